@@ -1,0 +1,317 @@
+/*
+ * tmm_oracle.c -- plain, slow, FP64 CPU statement of the Transport Matrix Method
+ * year map of Metos3D (Piwonski & Slawig, "The Idea and Concept of Metos3D",
+ * arXiv:1410.0204).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA library is checked
+ * against.  The library never links, loads or calls it, and it shares no code, header,
+ * table or constant with the library; only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark use it.
+ *
+ * What it computes, in the paper's order and notation:
+ *   Section 3:     y_{i+1} = A_imp,i ( A_exp,i y_i + q_i(y_i, u) ),  i = 0 .. n_step-1,
+ *                  with twelve monthly explicit and twelve monthly implicit matrices,
+ *                  linearly interpolated in time;
+ *   Section 4:     the year map phi, y(T) = phi(y(0)), n_step = 2880 steps per year;
+ *   Section 2.2.1: the PO4-DOP source-minus-sink term q (two tracers, here "N-DOP");
+ *   Section 5:     the per-water-column model interface bgc(...), column-local, 360-day
+ *                  year, tracer array y(nlayer, ntracer) with the layer index fastest.
+ *
+ * Readings taken where the paper is silent (each restated where it is used):
+ *   R1  the model returns the increment over one ocean step, dt * q for one internal
+ *       step, so that y_{i+1} = A_imp (A_exp y_i + dt q(y_i));
+ *   R2  with nsub internal model steps (the paper's runs use eight) the increment is
+ *       y^(nsub) - y^(0) of nsub explicit Euler steps of length dt/nsub, all using the
+ *       forcing passed for the start of the ocean step;
+ *   R3  monthly matrix m sits at mid-month, t = (m + 1/2)/12, wrapping from December to
+ *       January; both matrices and forcing are taken at the start of the step,
+ *       t_j = j / n_step;
+ *   R4  the stored monthly implicit matrices themselves are interpolated;
+ *   R5  remineralisation of the sinking flux is a source, (F(z_top) - F(z_bot)) / h;
+ *   R6  the export integral is the sum over the euphotic layers of f_k h_k; light is
+ *       evaluated at the layer centre depth d_k, the flux at layer interfaces;
+ *   R7  the flux reaching a column's bottom interface is deposited in its bottom layer
+ *       (F(z_bot) = 0 there); a column with no aphotic layer keeps its export in its
+ *       bottom layer;
+ *   R8  I_SWR is the daily-mean top-of-atmosphere insolation of a circular orbit,
+ *       sigma_PAR = 0.4, sigma_ice = 0;
+ *   R9  alpha is given per day (times 360 per year), lambda per year, time in years.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_MODEL_NONE 0
+#define ORACLE_MODEL_NDOP 2
+#define ORACLE_MAX_LAYER 256
+
+typedef struct {
+    int n;                      /* wet cells */
+    int ncol;                   /* water columns */
+    int nnz;                    /* nonzeros of one explicit matrix */
+    int nmonth;                 /* monthly matrices (12) */
+    int nstep;                  /* steps per model year (2880) */
+    const int *col_start;       /* [ncol+1] first cell of each column, surface first */
+    const double *h;            /* [n] layer thickness [m] */
+    const double *zc;           /* [n] depth of the layer centre [m] */
+    const double *lat;          /* [ncol] latitude [degrees] */
+    const int *rowptr;          /* [n+1] explicit matrices: CSR row pointers */
+    const int *colidx;          /* [nnz] column indices */
+    const double *exp_val;      /* [nmonth][nnz] values */
+    const long long *blk_off;   /* [ncol+1] implicit matrices: offset of each column block */
+    const double *imp_blk;      /* [nmonth][s_imp] dense row-major blocks */
+    long long s_imp;
+} oracle_problem;
+
+/* ---------------------------------------------------------------------------------
+ * Interpolation weights in time (Section 3; reading R3).
+ * Step j starts at t_j = j / nstep (fraction of a year).  With monthly matrices at
+ * mid-month, s = nmonth t_j - 1/2, m0 = floor(s) mod nmonth, m1 = m0 + 1 mod nmonth,
+ * w = s - floor(s), and the operator is (1 - w) M_m0 + w M_m1.  s is formed from
+ * integers, num / den with num = 2 nmonth j - nstep and den = 2 nstep, so that w is
+ * exactly 0 on the month centres.
+ * --------------------------------------------------------------------------------- */
+void oracle_month_weights(int j, int nstep, int nmonth, int *m0, int *m1, double *w)
+{
+    long long num = 2LL * nmonth * j - nstep;
+    long long den = 2LL * nstep;
+    long long k = num / den;
+    if (num % den != 0 && num < 0) k -= 1;          /* floor division */
+    long long r = num - k * den;                    /* 0 <= r < den */
+    int mk = (int)(((k % nmonth) + nmonth) % nmonth);
+    *m0 = mk;
+    *m1 = (mk + 1) % nmonth;
+    *w = (double)r / (double)den;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Short-wave radiation I_SWR (Section 2.2.1 names Paltridge & Platt without giving the
+ * formula; reading R8): daily-mean insolation at the top of the atmosphere,
+ *   Q = S0/pi (h0 sin(phi) sin(delta) + cos(phi) cos(delta) sin(h0)),
+ *   h0 = arccos(clamp(-tan(phi) tan(delta), -1, 1)),
+ *   delta = -23.44 deg cos(2 pi (t + 10/360)),  S0 = 1361 W/m^2,
+ * t the time as a fraction of the 360-day year.  *dayfrac = h0 / pi (daylight fraction).
+ * --------------------------------------------------------------------------------- */
+double oracle_insolation(double lat_deg, double t, double *dayfrac)
+{
+    const double pi = 3.14159265358979323846;
+    const double S0 = 1361.0;
+    double phi = lat_deg * (pi / 180.0);
+    double delta = -23.44 * (pi / 180.0) * cos(2.0 * pi * (t + 10.0 / 360.0));
+    double x = -tan(phi) * tan(delta);
+    if (x > 1.0) x = 1.0;
+    if (x < -1.0) x = -1.0;
+    double h0 = acos(x);
+    if (dayfrac) *dayfrac = h0 / pi;
+    return S0 / pi * (h0 * sin(phi) * sin(delta) + cos(phi) * cos(delta) * sin(h0));
+}
+
+/* ---------------------------------------------------------------------------------
+ * PO4-DOP source-minus-sink term (Section 2.2.1), one evaluation on one column.
+ * Tracers: y1 = N (phosphate), y2 = DOP.  Parameters u, in this order:
+ *   u[0] k_w   attenuation of water [1/m]           (K_H2O)
+ *   u[1] alpha maximum community production [1/d]
+ *   u[2] sigma fraction of production to DOP [-]     (sigma_2; sigma_bar = 1 - sigma)
+ *   u[3] lambda DOP remineralisation rate [1/yr]     (lambda'_2)
+ *   u[4] K_N   half saturation of PO4               (K_1)
+ *   u[5] K_I   half saturation of light [W/m^2]
+ *   u[6] b     Martin exponent [-]
+ * Euphotic zone Omega_1: the top min(2, nlayer) layers (Section 7: two euphotic layers).
+ *   I_k  = I_SWR sigma_PAR (1 - sigma_ice) exp(-d_k k_w)
+ *   f_k  = alpha N_k/(N_k + K_N) I_k/(I_k + K_I)
+ *   q1_k = -f_k + lambda DOP_k,   q2_k = sigma f_k - lambda DOP_k
+ * Export through the base z_eu of the euphotic zone: E = (1 - sigma) sum_k f_k h_k,
+ * flux F(z) = E (z / z_eu)^(-b)  (Martin et al.).
+ * Aphotic zone Omega_2:
+ *   q1_k = (F(z_top,k) - F(z_bot,k)) / h_k + lambda DOP_k,  q2_k = -lambda DOP_k
+ * with F(z_bot) = 0 in the bottom layer (R5-R7).  Rates are per year (R9).
+ * --------------------------------------------------------------------------------- */
+static void ndop_q(int nlayer, const double *h, const double *d, double insol, double ice,
+                   const double *N, const double *DOP, const double *u, double *qN, double *qD)
+{
+    const double sigma_par = 0.4;
+    double kw = u[0], alpha = u[1] * 360.0, sigma = u[2], lambda = u[3];
+    double KN = u[4], KI = u[5], b = u[6];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double E = 0.0;
+    double zeu = 0.0;
+    for (int k = 0; k < neu; k++) {
+        double I = insol * sigma_par * (1.0 - ice) * exp(-d[k] * kw);
+        double f = alpha * (N[k] / (N[k] + KN)) * (I / (I + KI));
+        qN[k] = -f + lambda * DOP[k];
+        qD[k] = sigma * f - lambda * DOP[k];
+        E += (1.0 - sigma) * f * h[k];
+        zeu += h[k];
+    }
+    double ztop = zeu;
+    for (int k = neu; k < nlayer; k++) {
+        double zbot = ztop + h[k];
+        double Ftop = E * pow(ztop / zeu, -b);
+        double Fbot = (k == nlayer - 1) ? 0.0 : E * pow(zbot / zeu, -b);
+        qN[k] = (Ftop - Fbot) / h[k] + lambda * DOP[k];
+        qD[k] = -lambda * DOP[k];
+        ztop = zbot;
+    }
+    if (nlayer <= neu)
+        qN[nlayer - 1] += E / h[nlayer - 1];
+}
+
+/* ---------------------------------------------------------------------------------
+ * The model interface of Section 5.2:
+ *   bgc(t, dt, lat, insol, dayfrac, ice, wind, ntracer, nlayer, h, d, salt, temp,
+ *       y, ybgc, nparam, u)
+ * y and ybgc are (nlayer, ntracer) arrays with the layer index fastest.  ybgc receives
+ * the increment over the ocean step dt (R1, R2): nsub explicit Euler steps of length
+ * dt / nsub with the same forcing.  lat, dayfrac, wind, salt and temp are part of the
+ * interface and unused by this model.  Returns 0, or -1 on bad arguments.
+ * --------------------------------------------------------------------------------- */
+int oracle_bgc(int model, double t, double dt, double lat, double insol, double dayfrac,
+               double ice, double wind, int ntracer, int nlayer, const double *h,
+               const double *d, const double *salt, const double *temp, const double *y,
+               double *ybgc, int nparam, const double *u, int nsub)
+{
+    (void)t; (void)lat; (void)dayfrac; (void)wind; (void)salt; (void)temp;
+    if (nlayer < 1 || nlayer > ORACLE_MAX_LAYER || nsub < 1) return -1;
+    if (model == ORACLE_MODEL_NONE) {
+        for (int i = 0; i < ntracer * nlayer; i++) ybgc[i] = 0.0;
+        return 0;
+    }
+    if (model != ORACLE_MODEL_NDOP || ntracer != 2 || nparam != 7) return -1;
+    double ys[2 * ORACLE_MAX_LAYER], qN[ORACLE_MAX_LAYER], qD[ORACLE_MAX_LAYER];
+    memcpy(ys, y, sizeof(double) * 2 * nlayer);
+    double ds = dt / nsub;
+    for (int s = 0; s < nsub; s++) {
+        ndop_q(nlayer, h, d, insol, ice, ys, ys + nlayer, u, qN, qD);
+        for (int k = 0; k < nlayer; k++) {
+            ys[k] += ds * qN[k];
+            ys[nlayer + k] += ds * qD[k];
+        }
+    }
+    for (int i = 0; i < 2 * nlayer; i++) ybgc[i] = ys[i] - y[i];
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------
+ * One TMM step (Section 3): y_out = A_imp(t_j) (A_exp(t_j) y + q_j(y, u)).
+ * State layout [ntracer][n]; cells ordered column by column, surface to bottom.
+ * work: caller-provided [ntracer][n] scratch.
+ * --------------------------------------------------------------------------------- */
+int oracle_step(const oracle_problem *P, int model, int ntracer, int j, const double *y,
+                double *y_out, const double *u, int nparam, int nsub, double *work)
+{
+    int n = P->n;
+    int m0, m1;
+    double w;
+    oracle_month_weights(j, P->nstep, P->nmonth, &m0, &m1, &w);
+    double t = (double)j / P->nstep;
+    double dt = 1.0 / P->nstep;
+    const double *a0 = P->exp_val + (size_t)m0 * P->nnz;
+    const double *a1 = P->exp_val + (size_t)m1 * P->nnz;
+    const double *b0 = P->imp_blk + (size_t)m0 * P->s_imp;
+    const double *b1 = P->imp_blk + (size_t)m1 * P->s_imp;
+    double *z = work;
+    int bad = 0;
+
+    /* explicit part: z = A_exp(t_j) y, A_exp(t_j) = (1 - w) A_m0 + w A_m1 */
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; i++) {
+        for (int tr = 0; tr < ntracer; tr++) {
+            double s = 0.0;
+            for (int p = P->rowptr[i]; p < P->rowptr[i + 1]; p++) {
+                double a = (1.0 - w) * a0[p] + w * a1[p];
+                s += a * y[(size_t)tr * n + P->colidx[p]];
+            }
+            z[(size_t)tr * n + i] = s;
+        }
+    }
+
+    /* per column: add q(y_j), then the implicit part y_out = A_imp(t_j) z */
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int c = 0; c < P->ncol; c++) {
+        int s0 = P->col_start[c];
+        int L = P->col_start[c + 1] - s0;
+        double ycol[ORACLE_MAX_LAYER * 4], dq[ORACLE_MAX_LAYER * 4];
+        if (L > ORACLE_MAX_LAYER || ntracer > 4) { bad |= 1; continue; }
+        for (int tr = 0; tr < ntracer; tr++)
+            for (int k = 0; k < L; k++) ycol[tr * L + k] = y[(size_t)tr * n + s0 + k];
+        double dayfrac;
+        double insol = oracle_insolation(P->lat[c], t, &dayfrac);
+        if (oracle_bgc(model, t, dt, P->lat[c], insol, dayfrac, 0.0, 0.0, ntracer, L,
+                       P->h + s0, P->zc + s0, NULL, NULL, ycol, dq, nparam, u, nsub) != 0) {
+            bad |= 1;
+            continue;
+        }
+        for (int tr = 0; tr < ntracer; tr++)
+            for (int k = 0; k < L; k++) z[(size_t)tr * n + s0 + k] += dq[tr * L + k];
+        const double *B0 = b0 + P->blk_off[c];
+        const double *B1 = b1 + P->blk_off[c];
+        for (int tr = 0; tr < ntracer; tr++) {
+            for (int r = 0; r < L; r++) {
+                double s = 0.0;
+                for (int k = 0; k < L; k++) {
+                    double bb = (1.0 - w) * B0[r * L + k] + w * B1[r * L + k];
+                    s += bb * z[(size_t)tr * n + s0 + k];
+                }
+                y_out[(size_t)tr * n + s0 + r] = s;
+            }
+        }
+    }
+    return bad ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------------------------
+ * The year map phi (Section 4): nstep steps from y0, result in y1.
+ * --------------------------------------------------------------------------------- */
+int oracle_year_map(const oracle_problem *P, int model, int ntracer, const double *y0,
+                    double *y1, const double *u, int nparam, int nsub)
+{
+    size_t len = (size_t)ntracer * P->n;
+    double *a = (double *)malloc(sizeof(double) * len);
+    double *b = (double *)malloc(sizeof(double) * len);
+    double *work = (double *)malloc(sizeof(double) * len);
+    if (!a || !b || !work) { free(a); free(b); free(work); return -2; }
+    memcpy(a, y0, sizeof(double) * len);
+    int rc = 0;
+    for (int j = 0; j < P->nstep && rc == 0; j++) {
+        rc = oracle_step(P, model, ntracer, j, a, b, u, nparam, nsub, work);
+        double *tmp = a; a = b; b = tmp;
+    }
+    memcpy(y1, a, sizeof(double) * len);
+    free(a); free(b); free(work);
+    return rc;
+}
+
+/* Run nsteps steps starting at step j0 (steps wrap around the year). */
+int oracle_steps(const oracle_problem *P, int model, int ntracer, int j0, int nsteps,
+                 const double *y0, double *y1, const double *u, int nparam, int nsub)
+{
+    size_t len = (size_t)ntracer * P->n;
+    double *a = (double *)malloc(sizeof(double) * len);
+    double *b = (double *)malloc(sizeof(double) * len);
+    double *work = (double *)malloc(sizeof(double) * len);
+    if (!a || !b || !work) { free(a); free(b); free(work); return -2; }
+    memcpy(a, y0, sizeof(double) * len);
+    int rc = 0;
+    for (int s = 0; s < nsteps && rc == 0; s++) {
+        rc = oracle_step(P, model, ntracer, (j0 + s) % P->nstep, a, b, u, nparam, nsub, work);
+        double *tmp = a; a = b; b = tmp;
+    }
+    memcpy(y1, a, sizeof(double) * len);
+    free(a); free(b); free(work);
+    return rc;
+}
+
+/* Threads used by the OpenMP loops above (1 when built without OpenMP). */
+int oracle_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}

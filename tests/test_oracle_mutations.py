@@ -1,0 +1,52 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (on the CPU only),
+builds it, and runs the pin suite against it: the suite must fail for every mutant.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "tmm_oracle.c")
+
+MUTANTS = {
+    "interp_weights_swapped": ("(1.0 - w) * a0[p] + w * a1[p]", "w * a0[p] + (1.0 - w) * a1[p]"),
+    "block_transposed": ("B0[r * L + k] + w * B1[r * L + k]", "B0[k * L + r] + w * B1[k * L + r]"),
+    "q_on_explicit_result": ("ycol[tr * L + k] = y[(size_t)tr * n + s0 + k]", "ycol[tr * L + k] = z[(size_t)tr * n + s0 + k]"),
+    "dop_remin_dropped_in_euphotic": ("qN[k] = -f + lambda * DOP[k];", "qN[k] = -f;"),
+    "martin_sign": ("(Ftop - Fbot) / h[k]", "(Fbot - Ftop) / h[k]"),
+    "export_fraction": ("E += (1.0 - sigma) * f * h[k];", "E += sigma * f * h[k];"),
+    "bottom_deposit_dropped": ("(k == nlayer - 1) ? 0.0 : E * pow(zbot / zeu, -b)", "E * pow(zbot / zeu, -b)"),
+    "light_at_wrong_depth": ("exp(-d[k] * kw)", "exp(-h[k] * kw)"),
+    "alpha_units": ("u[1] * 360.0", "u[1]"),
+    "insolation_term": ("cos(phi) * cos(delta) * sin(h0)", "cos(phi) * cos(delta) * cos(h0)"),
+    "month_index": ("*m1 = (mk + 1) % nmonth;", "*m1 = (mk + 2) % nmonth;"),
+    "forcing_time": ("double t = (double)j / P->nstep;", "double t = (double)(j + 1) / P->nstep;"),
+    "substep_length": ("double ds = dt / nsub;", "double ds = dt;"),
+    "csr_gather": ("y[(size_t)tr * n + P->colidx[p]]", "y[(size_t)tr * n + i]"),
+    "euphotic_layers": ("int neu = nlayer < 2 ? nlayer : 2;", "int neu = nlayer < 3 ? nlayer : 3;"),
+    "light_half_saturation": ("(I / (I + KI))", "(I / (I + KN))"),
+    "declination_phase": ("cos(2.0 * pi * (t + 10.0 / 360.0))", "cos(2.0 * pi * (t - 10.0 / 360.0))"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, "mutation site not found: %s" % name
+    mutated = tmp_path / "tmm_oracle_mut.c"
+    mutated.write_text(text.replace(old, new))
+    lib = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                           "-o", str(lib), str(mutated), "-lm"])
+    env = dict(os.environ, M3D_ORACLE_LIB=str(lib), M3D_ORACLE_THREADS="1",
+               OMP_NUM_THREADS="1", OMP_WAIT_POLICY="passive")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "the pins did not catch mutant %s:\n%s" % (name, r.stdout[-2000:])
