@@ -1,0 +1,309 @@
+"""Benchmark of the TMM year map (Metos3D, arXiv:1410.0204, Sections 3-4) on GB300.
+
+One benchmark step = one model year: the year map phi over 2880 TMM steps on the
+128 x 64 x 15 synthetic grid (52749 wet cells in 4448 columns, the size of the paper's
+2.8125 degree runs), PO4-DOP model (2 tracers), FP64, inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the FP64 C statement of the method the GPU path is
+checked against) on the host cores instead.  For N > 1 (torchrun) every rank runs its own
+replica of the year map (the method does not shard on one problem here; replicas only).
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import m3d_inputs as mi  # noqa: E402
+
+WORKLOAD = "ndop_128x64x15"
+METRIC = "model years/s & HBM roofline % of year map"
+UNIT = "model years/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, src = 6800.0, "fallback"
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        hbm, src = float(d["hbm_gbs"]), "measured"
+    except Exception:
+        pass
+    return hbm, src
+
+
+# FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz maximum SM clock.
+# (A DFMA throughput probe on this GPU measured 1.20 TFLOP/s, 1.92 FMA/clock/SM at the
+# clock it ran.)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def algorithmic_per_step(prob, ntr=2):
+    """Algorithmic bytes and FP64 flops of one TMM step.
+
+    bytes: explicit values of two months and their column indices, row pointers, the
+    implicit blocks of two months, and the state read and written once.
+    flops: one FMA to interpolate each matrix entry plus one FMA per tracer (explicit and
+    implicit), and the source term: ~20 flops per euphotic cell, ~8 per aphotic cell,
+    plus adding the increment to every tracer.
+    """
+    n, nnz, s_imp = prob.n, prob.nnz, prob.s_imp
+    bytes_ = nnz * (2 * 8 + 4) + 4 * (n + 1) + s_imp * 2 * 8 + ntr * n * (8 + 8)
+    L = prob.nlayer
+    n_eu = int(np.minimum(L, 2).sum())
+    flops = (nnz + s_imp) * (2 + 2 * ntr) + 20 * n_eu + 8 * (n - n_eu) + 2 * ntr * n
+    return bytes_, flops
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            self.f.seek(0)
+            rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        finally:
+            try:
+                os.unlink(self.f.name)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if len(r) > 2]
+        mx = [float(r[2]) for r in rows if len(r) > 2]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(prob, seconds=12.0, max_steps=2880):
+    """The CPU oracle as it stands, on all host cores, over a bounded sample of the year."""
+    import oracle
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    P = oracle.Problem(prob)
+    u = mi.default_params_ndop()
+    y = mi.initial_state(prob)
+    t0 = time.perf_counter()
+    steps = 0
+    chunk = 24
+    while steps < max_steps and time.perf_counter() - t0 < seconds:
+        y = oracle.steps(P, steps % prob.nstep, chunk, y, u)
+        steps += chunk
+    dt = time.perf_counter() - t0
+    oracle.set_threads(1)
+    years = steps / prob.nstep
+    return {"value": years / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of the 2880 TMM steps of the %s year map, FP64 C oracle, %d OpenMP threads, %.1f s"
+                      % (steps, WORKLOAD, threads, dt)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    prob = mi.make_problem(WORKLOAD)
+    import oracle
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    P = oracle.Problem(prob)
+    u = mi.default_params_ndop()
+    y = mi.initial_state(prob)
+    sample_steps = 288        # one tenth of a model year per benchmark step
+    for _ in range(args.warmup):
+        y = oracle.steps(P, 0, sample_steps, y, u)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        y = oracle.steps(P, (k * sample_steps) % prob.nstep, sample_steps, y, u)
+    dt = time.perf_counter() - t0
+    value = args.steps * sample_steps / prob.nstep / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + " year map, PO4-DOP, 2 tracers, 2880 steps/year",
+                       "sample": "each step: %d TMM steps (1/10 model year)" % sample_steps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d x %d TMM steps of the %s year map" % (args.steps, sample_steps, WORKLOAD)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    import paper_1410_0204_gb300 as m3d
+
+    prob = mi.make_problem(WORKLOAD)
+    u_h = mi.default_params_ndop()
+    y0_h = mi.initial_state(prob)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = m3d.Context.from_problem(prob, model=m3d.MODEL_NDOP, ntracer=2, nparam=7, stream=stream)
+        y0 = torch.from_numpy(y0_h).cuda()
+        u = torch.from_numpy(u_h).cuda()
+        ya = torch.empty_like(y0)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+        for _ in range(max(args.warmup, 0)):
+            ctx.year_map(y0, ya, u)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        times = []
+        launches = 0
+        with ClockSampler(local) as clocks:
+            for _ in range(args.steps):
+                flush.fill_(1.0)                       # L2 flushed between timed iterations
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.year_map(y0, ya, u)
+                e1.record(stream)
+                launches += ctx.last_launch_count()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        total = sum(times)
+        if pg:
+            t = torch.tensor([total], dtype=torch.float64, device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            total = float(t.item())
+        value = world * args.steps / total
+
+        # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+        y0_pin = torch.from_numpy(y0_h).pin_memory()
+        y1_pin = torch.empty_like(y0_pin).pin_memory()
+        u_pin = torch.from_numpy(u_h).pin_memory()
+        ctx.year_map_host_ptr(y0_pin.data_ptr(), y1_pin.data_ptr(), u_pin.data_ptr())
+        e2e_steps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.year_map_host_ptr(y0_pin.data_ptr(), y1_pin.data_ptr(), u_pin.data_ptr())
+        e2e_dt = time.perf_counter() - t0
+        e2e_value = world * e2e_steps / e2e_dt if world == 1 else None
+        if pg:
+            t = torch.tensor([e2e_dt], dtype=torch.float64, device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_value = world * e2e_steps / float(t.item())
+        ctx.close()
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+    hbm_peak, hbm_src = peaks()
+    bytes_step, flops_step = algorithmic_per_step(prob)
+    t_year = total / args.steps
+    flops_year = flops_step * prob.nstep
+    bytes_year = bytes_step * prob.nstep
+    achieved_tf = flops_year / t_year / 1e12
+    achieved_gbs = bytes_year / t_year / 1e9
+    clock = clocks.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_year, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " year map: PO4-DOP, 2 tracers, 2880 TMM steps per model year",
+                   "n": prob.n, "ncol": prob.ncol, "nnz": prob.nnz, "S_imp": prob.s_imp,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed iterations (256 MiB write); 12 months of matrices (~270 MB) exceed L2"},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_step (one launch per TMM step, whole year timed)",
+                     "peak_source": "FP64 units x max SM clock (152 SMs x 2 FMA/clk x 2.07 GHz)"},
+        "hbm_roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src,
+                         "bytes_per_step": bytes_step, "flops_per_step": flops_step},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y0_h.nbytes + u_h.nbytes),
+                "d2h_bytes_per_step": int(y0_h.nbytes)},
+        "gpu_launches": launches,
+        "clocks": clock,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob)
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

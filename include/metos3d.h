@@ -1,0 +1,182 @@
+/*
+ * metos3d.h -- C ABI of the GB300 (sm_103a) implementation of the Transport Matrix
+ * Method year map of Metos3D (Piwonski & Slawig, arXiv:1410.0204).
+ *
+ * The library advances marine biogeochemical tracers with the TMM time step of
+ * Section 3,
+ *     y_{j+1} = A_imp(t_j) ( A_exp(t_j) y_j + q_j(y_j, u) ),   j = 0 .. n_step - 1,
+ * where A_exp and A_imp are linear interpolations in time of twelve monthly explicit
+ * and implicit transport matrices, and iterates it over one model year (Section 4) as
+ * the year map phi, y(T) = phi(y(0)), whose fixed point is the periodic solution.
+ * q is the per-water-column source-minus-sink term of Section 5 (here the PO4-DOP
+ * model of Section 2.2.1).
+ *
+ * Conventions shared by every call:
+ *   - All arithmetic is IEEE FP64.
+ *   - A tracer state is a device array of ntracer * n doubles in the layout
+ *     [tracer][cell]; cells are ordered water column by water column, each column
+ *     from the surface down (the interface's y(nlayer, ntracer), layer fastest).
+ *   - State and parameter pointers passed to metos3d_step / metos3d_year_map are
+ *     caller-owned DEVICE pointers; the library never frees them.  Work is enqueued
+ *     on the context's stream; the calls return without waiting unless stated.
+ *   - Every call returns an m3d_status and never lets an exception cross the ABI.
+ *     metos3d_last_error(ctx) gives a message for the last failure on ctx
+ *     (metos3d_last_error(NULL) for a failed metos3d_init).
+ *   - A context is bound to one CUDA device (the current one at metos3d_init) and to
+ *     one stream; it is not thread-safe.
+ */
+#ifndef METOS3D_H
+#define METOS3D_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    M3D_OK = 0,
+    M3D_NOT_CONVERGED = 1,      /* an iterative solve stopped before its tolerance */
+    M3D_ERR_ARG = -1,           /* invalid argument or inconsistent input */
+    M3D_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+    M3D_ERR_NONFINITE = -3,     /* a non-finite value appeared in the state */
+    M3D_ERR_TIMEOUT = -4,       /* a bounded device-side wait ran out */
+    M3D_ERR_UNSUPPORTED = -5    /* a valid request this build does not implement */
+} m3d_status;
+
+/* Biogeochemical models (Section 2.2). */
+enum {
+    M3D_MODEL_NONE = 0,         /* q = 0: pure transport, any number of tracers */
+    M3D_MODEL_NDOP = 2          /* PO4-DOP (Section 2.2.1): 2 tracers, 7 parameters */
+};
+
+#define M3D_MAX_LAYERS 64       /* deepest water column accepted */
+#define M3D_MAX_TRACERS 8
+
+typedef struct m3d_ctx m3d_ctx;   /* opaque; owned by the library */
+
+/*
+ * Ocean grid (host pointers; copied at init).  Water column c holds cells
+ * col_start[c] .. col_start[c+1]-1, surface first; its layer count must not exceed
+ * M3D_MAX_LAYERS.
+ */
+typedef struct {
+    int n;                      /* wet cells */
+    int ncol;                   /* water columns */
+    const int *col_start;       /* [ncol+1], col_start[0] = 0, strictly increasing, col_start[ncol] = n */
+    const double *h;            /* [n] layer thickness [m], > 0 (the interface's h) */
+    const double *zc;           /* [n] depth of the layer centre [m] (the interface's d) */
+    const double *vol;          /* [n] cell volume [m^3] (mass diagnostics) */
+    const double *lat;          /* [ncol] latitude [degrees], in [-90, 90] */
+} m3d_grid;
+
+/*
+ * Monthly transport matrices (Section 3; host pointers; copied and re-laid out at init).
+ * Explicit: nmonth CSR matrices sharing one pattern (rows sorted, no duplicates).
+ * Implicit: block diagonal by water column; month m holds, for each column c in order,
+ * its dense L_c x L_c block in row-major order, s_imp = sum_c L_c^2 doubles per month.
+ * Month m is centred at t = (m + 1/2) / nmonth of the year; between centres the
+ * matrices are interpolated linearly, wrapping from the last month to the first.
+ */
+typedef struct {
+    int nmonth;                 /* monthly matrices, >= 1 (12 in the paper) */
+    int nnz;                    /* nonzeros of one explicit matrix */
+    const int *exp_rowptr;      /* [n+1] */
+    const int *exp_colidx;      /* [nnz] */
+    const double *exp_val;      /* [nmonth][nnz] */
+    long long s_imp;            /* sum over columns of L_c^2 */
+    const double *imp_blk;      /* [nmonth][s_imp] */
+} m3d_matrices;
+
+/* Model and time discretisation. */
+typedef struct {
+    int model_id;               /* M3D_MODEL_* */
+    int ntracer;                /* 2 for M3D_MODEL_NDOP; 1..M3D_MAX_TRACERS for M3D_MODEL_NONE */
+    int nparam;                 /* 7 for M3D_MODEL_NDOP (see metos3d_bgc) */
+    int nsub;                   /* internal model steps per ocean step, >= 1 (the paper's runs use 8) */
+    int nstep;                  /* ocean steps per model year (2880 in the paper) */
+} m3d_model;
+
+/*
+ * Create a context: validate and copy the grid, the matrices and the model onto the
+ * current CUDA device, build the device layouts and the insolation table, and bind
+ * the context to `stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Synchronous.  Returns M3D_ERR_ARG for inconsistent input (bad sizes, unsorted or
+ * out-of-range CSR indices, block sizes not matching col_start, non-finite values).
+ * On success *ctx must later be released with metos3d_free.
+ */
+m3d_status metos3d_init(m3d_ctx **ctx, const m3d_grid *grid, const m3d_matrices *mats,
+                        const m3d_model *model, void *stream);
+
+/* Rebind the context to another stream (a cudaStream_t). */
+m3d_status metos3d_set_stream(m3d_ctx *ctx, void *stream);
+
+/*
+ * One TMM step j (Section 3): y_out = A_imp(t_j) (A_exp(t_j) y_in + q(y_in, u)),
+ * t_j = j / nstep of the year, 0 <= j < nstep.  y_in, y_out: device [ntracer][n], must
+ * not overlap.  u: device [nparam] model parameters.  Asynchronous.
+ */
+m3d_status metos3d_step(m3d_ctx *ctx, int j, const double *y_in, double *y_out,
+                        const double *u);
+
+/*
+ * The year map phi (Section 4): nstep steps from y0, result in y1 (device [ntracer][n];
+ * y0 and y1 may be the same array).  u: device [nparam].  Asynchronous; the first call
+ * on a context builds its execution plan (do it before any stream capture).
+ * A non-finite value in the result is reported by metos3d_check_finite.
+ */
+m3d_status metos3d_year_map(m3d_ctx *ctx, const double *y0, double *y1, const double *u);
+
+/*
+ * The year map with HOST arrays: copies y0 and u to the device, runs metos3d_year_map
+ * and copies the result back into y1.  Synchronous.  Pinned host memory gives the
+ * fastest copies.
+ */
+m3d_status metos3d_year_map_host(m3d_ctx *ctx, const double *y0_host, double *y1_host,
+                                 const double *u_host);
+
+/*
+ * Diagnostics, synchronous, result on the host:
+ *   metos3d_mass:     sum over tracers and cells of vol_i y_{tr,i} (total tracer mass);
+ *   metos3d_residual: || a - b ||_2 over all ntracer * n entries (the paper's spin-up and
+ *                     Newton residual || y - phi(y) ||_2, Section 7);
+ *   metos3d_check_finite: M3D_OK, or M3D_ERR_NONFINITE if y holds a NaN or infinity.
+ */
+m3d_status metos3d_mass(m3d_ctx *ctx, const double *y, double *mass_host);
+m3d_status metos3d_residual(m3d_ctx *ctx, const double *a, const double *b, double *norm_host);
+m3d_status metos3d_check_finite(m3d_ctx *ctx, const double *y);
+
+/*
+ * The biogeochemical model interface of Section 5.2, evaluated by the library's device
+ * code on one water column, with HOST arrays (a check and debugging entry; the time
+ * step uses the same device code):
+ *   bgc(t, dt, lat, insol, dayfrac, ice, wind, ntracer, nlayer, h, d, salt, temp,
+ *       y, ybgc, nparam, u)
+ * y and ybgc are (nlayer, ntracer) arrays, layer index fastest.  ybgc receives the
+ * increment of the model over the ocean step dt: nsub explicit Euler steps of length
+ * dt / nsub with the forcing given.  For M3D_MODEL_NDOP, u = (k_w [1/m], alpha [1/d],
+ * sigma [-], lambda [1/yr], K_N [mmol P/m^3], K_I [W/m^2], b [-]) and time is in years.
+ * lat, dayfrac, wind, salt and temp are accepted and unused by this model; salt and
+ * temp may be NULL.  Synchronous.  Returns M3D_ERR_ARG for bad sizes.
+ */
+m3d_status metos3d_bgc(int model_id, double t, double dt, double lat, double insol,
+                       double dayfrac, double ice, double wind, int ntracer, int nlayer,
+                       const double *h, const double *d, const double *salt,
+                       const double *temp, const double *y, double *ybgc, int nparam,
+                       const double *u, int nsub);
+
+/* Sizes of a context: n, ncol, ntracer, nstep (any pointer may be NULL). */
+m3d_status metos3d_info(const m3d_ctx *ctx, int *n, int *ncol, int *ntracer, int *nstep);
+
+/* Number of kernel launches the last metos3d_year_map issued. */
+long long metos3d_last_launch_count(const m3d_ctx *ctx);
+
+/* Message for the last failure on ctx, or on metos3d_init when ctx is NULL. */
+const char *metos3d_last_error(const m3d_ctx *ctx);
+
+/* Release a context and all device memory it owns.  NULL is accepted. */
+void metos3d_free(m3d_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* METOS3D_H */

@@ -47,6 +47,7 @@
 #define ORACLE_MODEL_NONE 0
 #define ORACLE_MODEL_NDOP 2
 #define ORACLE_MAX_LAYER 256
+#define ORACLE_MAX_TRACER 8
 
 typedef struct {
     int n;                      /* wet cells */
@@ -233,8 +234,8 @@ int oracle_step(const oracle_problem *P, int model, int ntracer, int j, const do
     for (int c = 0; c < P->ncol; c++) {
         int s0 = P->col_start[c];
         int L = P->col_start[c + 1] - s0;
-        double ycol[ORACLE_MAX_LAYER * 4], dq[ORACLE_MAX_LAYER * 4];
-        if (L > ORACLE_MAX_LAYER || ntracer > 4) { bad |= 1; continue; }
+        double ycol[ORACLE_MAX_LAYER * ORACLE_MAX_TRACER], dq[ORACLE_MAX_LAYER * ORACLE_MAX_TRACER];
+        if (L > ORACLE_MAX_LAYER || ntracer > ORACLE_MAX_TRACER) { bad |= 1; continue; }
         for (int tr = 0; tr < ntracer; tr++)
             for (int k = 0; k < L; k++) ycol[tr * L + k] = y[(size_t)tr * n + s0 + k];
         double dayfrac;

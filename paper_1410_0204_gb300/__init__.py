@@ -1,0 +1,9 @@
+"""GB300-native (sm_103a, FP64) Transport Matrix Method year map of Metos3D (arXiv:1410.0204).
+
+The compute path is the CUDA library ``libmetos3d.so`` (C ABI in ``include/metos3d.h``);
+this package holds its sources (``csrc/``), its build (``build.py``) and a thin ctypes
+binding (``binding.py``) that passes torch CUDA tensors and streams to it.
+"""
+from .binding import (Context, Metos3dError, bgc, declared_symbols, load, library_path,  # noqa: F401
+                      MODEL_NONE, MODEL_NDOP, M3D_OK, M3D_ERR_ARG, M3D_ERR_CUDA, M3D_ERR_NONFINITE,
+                      M3D_ERR_TIMEOUT, M3D_ERR_UNSUPPORTED, M3D_NOT_CONVERGED)

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of libmetos3d.so (include/metos3d.h): argument marshalling only.
+
+Every step of the TMM year map runs in the library's CUDA kernels; this module converts
+numpy arrays and torch CUDA tensors into the pointers and sizes of the C ABI, passes the
+current torch stream, and turns status codes into exceptions.  There is no CPU path: if
+the library is missing the import of a context fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+M3D_OK = 0
+M3D_NOT_CONVERGED = 1
+M3D_ERR_ARG = -1
+M3D_ERR_CUDA = -2
+M3D_ERR_NONFINITE = -3
+M3D_ERR_TIMEOUT = -4
+M3D_ERR_UNSUPPORTED = -5
+
+MODEL_NONE = 0
+MODEL_NDOP = 2
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "metos3d.h")
+
+
+class Metos3dError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("metos3d status %d: %s" % (status, msg))
+        self.status = status
+
+
+class _Grid(C.Structure):
+    _fields_ = [("n", C.c_int), ("ncol", C.c_int), ("col_start", C.POINTER(C.c_int)),
+                ("h", C.POINTER(C.c_double)), ("zc", C.POINTER(C.c_double)),
+                ("vol", C.POINTER(C.c_double)), ("lat", C.POINTER(C.c_double))]
+
+
+class _Matrices(C.Structure):
+    _fields_ = [("nmonth", C.c_int), ("nnz", C.c_int), ("exp_rowptr", C.POINTER(C.c_int)),
+                ("exp_colidx", C.POINTER(C.c_int)), ("exp_val", C.POINTER(C.c_double)),
+                ("s_imp", C.c_longlong), ("imp_blk", C.POINTER(C.c_double))]
+
+
+class _Model(C.Structure):
+    _fields_ = [("model_id", C.c_int), ("ntracer", C.c_int), ("nparam", C.c_int),
+                ("nsub", C.c_int), ("nstep", C.c_int)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libmetos3d.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError("libmetos3d.so is not built: run __graft_entry__.build() "
+                               "or python -m paper_1410_0204_gb300.build")
+    L = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+    L.metos3d_init.argtypes = [C.POINTER(vp), C.POINTER(_Grid), C.POINTER(_Matrices), C.POINTER(_Model), vp]
+    L.metos3d_set_stream.argtypes = [vp, vp]
+    L.metos3d_step.argtypes = [vp, C.c_int, vp, vp, vp]
+    L.metos3d_year_map.argtypes = [vp, vp, vp, vp]
+    L.metos3d_year_map_host.argtypes = [vp, dp, dp, dp]
+    L.metos3d_mass.argtypes = [vp, vp, dp]
+    L.metos3d_residual.argtypes = [vp, vp, vp, dp]
+    L.metos3d_check_finite.argtypes = [vp, vp]
+    L.metos3d_bgc.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                              C.c_double, C.c_double, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp,
+                              C.c_int, dp, C.c_int]
+    L.metos3d_info.argtypes = [vp, ip, ip, ip, ip]
+    L.metos3d_last_launch_count.argtypes = [vp]
+    L.metos3d_last_launch_count.restype = C.c_longlong
+    L.metos3d_last_error.argtypes = [vp]
+    L.metos3d_last_error.restype = C.c_char_p
+    L.metos3d_free.argtypes = [vp]
+    L.metos3d_free.restype = None
+    for name in declared_symbols():
+        fn = getattr(L, name)
+        if name not in ("metos3d_last_error", "metos3d_free", "metos3d_last_launch_count"):
+            fn.restype = C.c_int
+    _lib = L
+    return L
+
+
+def declared_symbols():
+    """Names of the functions include/metos3d.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(metos3d_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status, ctx=None):
+    if status != M3D_OK:
+        msg = load().metos3d_last_error(ctx).decode(errors="replace")
+        raise Metos3dError(status, msg)
+    return status
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_ptr(t, numel, name, writable=False):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError("%s must be a contiguous float64 tensor of %d elements" % (name, numel))
+    return C.c_void_p(t.data_ptr())
+
+
+def bgc(y, h, d, u, t=0.0, dt=1.0 / 2880, lat=0.0, insol=0.0, dayfrac=0.5, ice=0.0, wind=0.0,
+        model=MODEL_NDOP, nsub=1):
+    """The model interface of Section 5.2 on one column, on the GPU (host arrays)."""
+    L = load()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    ntr, nl = y.shape
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros_like(y)
+    _check(L.metos3d_bgc(model, t, dt, lat, insol, dayfrac, ice, wind, ntr, nl, _dp(h), _dp(d),
+                         None, None, _dp(y), _dp(out), u.shape[0], _dp(u), nsub))
+    return out
+
+
+class Context:
+    """A metos3d context on the current CUDA device (host inputs are copied at init)."""
+
+    def __init__(self, *, col_start, h, zc, vol, lat, exp_rowptr, exp_colidx, exp_val, imp_blk,
+                 model=MODEL_NDOP, ntracer=2, nparam=7, nsub=1, nstep=2880, stream=None):
+        torch = _torch()
+        L = load()
+        self._L = L
+        cs = np.ascontiguousarray(col_start, dtype=np.int32)
+        self.n = int(cs[-1])
+        self.ncol = int(cs.shape[0] - 1)
+        self.ntracer = int(ntracer)
+        self.nparam = int(nparam)
+        self.nstep = int(nstep)
+        h, zc, vol, lat = (np.ascontiguousarray(a, dtype=np.float64) for a in (h, zc, vol, lat))
+        rp = np.ascontiguousarray(exp_rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(exp_colidx, dtype=np.int32)
+        ev = np.ascontiguousarray(exp_val, dtype=np.float64)
+        ib = np.ascontiguousarray(imp_blk, dtype=np.float64)
+        nmonth = ev.shape[0]
+        g = _Grid(self.n, self.ncol, _ip(cs), _dp(h), _dp(zc), _dp(vol), _dp(lat))
+        m = _Matrices(nmonth, ci.shape[0], _ip(rp), _ip(ci), _dp(ev), ib.shape[1], _dp(ib))
+        md = _Model(model, self.ntracer, self.nparam, nsub, self.nstep)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        ctx = C.c_void_p()
+        _check(L.metos3d_init(C.byref(ctx), C.byref(g), C.byref(m), C.byref(md), C.c_void_p(stream.cuda_stream)))
+        self._ctx = ctx
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        return cls(col_start=prob.col_start, h=prob.h, zc=prob.zc, vol=prob.vol, lat=prob.lat,
+                   exp_rowptr=prob.exp_rowptr, exp_colidx=prob.exp_colidx, exp_val=prob.exp_val,
+                   imp_blk=prob.imp_blk, nstep=prob.nstep, **kw)
+
+    # ---- helpers
+    def _sync_stream(self):
+        torch = _torch()
+        s = torch.cuda.current_stream()
+        if s.cuda_stream != self._stream.cuda_stream:
+            self._stream = s
+            _check(self._L.metos3d_set_stream(self._ctx, C.c_void_p(s.cuda_stream)), self._ctx)
+
+    @property
+    def numel(self):
+        return self.ntracer * self.n
+
+    def new_state(self):
+        torch = _torch()
+        return torch.empty((self.ntracer, self.n), dtype=torch.float64, device="cuda")
+
+    # ---- the C ABI
+    def step(self, j, y_in, y_out, u):
+        self._sync_stream()
+        _check(self._L.metos3d_step(self._ctx, int(j), _dev_ptr(y_in, self.numel, "y_in"),
+                                    _dev_ptr(y_out, self.numel, "y_out", True),
+                                    _dev_ptr(u, self.nparam, "u") if self.nparam else None), self._ctx)
+        return y_out
+
+    def year_map(self, y0, y1, u):
+        self._sync_stream()
+        _check(self._L.metos3d_year_map(self._ctx, _dev_ptr(y0, self.numel, "y0"),
+                                        _dev_ptr(y1, self.numel, "y1", True),
+                                        _dev_ptr(u, self.nparam, "u") if self.nparam else None), self._ctx)
+        return y1
+
+    def year_map_host(self, y0, u, out=None):
+        self._sync_stream()
+        y0 = np.ascontiguousarray(y0, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        if out is None:
+            out = np.empty_like(y0)
+        if y0.size != self.numel or out.size != self.numel:
+            raise ValueError("state must hold ntracer * n values")
+        _check(self._L.metos3d_year_map_host(self._ctx, _dp(y0), _dp(out), _dp(u)), self._ctx)
+        return out
+
+    def year_map_host_ptr(self, y0_ptr, y1_ptr, u_ptr):
+        """Year map on raw host pointers (e.g. pinned torch CPU tensors)."""
+        self._sync_stream()
+        dp = C.POINTER(C.c_double)
+        _check(self._L.metos3d_year_map_host(self._ctx, C.cast(y0_ptr, dp), C.cast(y1_ptr, dp),
+                                             C.cast(u_ptr, dp)), self._ctx)
+
+    def mass(self, y):
+        self._sync_stream()
+        out = C.c_double()
+        _check(self._L.metos3d_mass(self._ctx, _dev_ptr(y, self.numel, "y"), C.byref(out)), self._ctx)
+        return out.value
+
+    def residual(self, a, b):
+        self._sync_stream()
+        out = C.c_double()
+        _check(self._L.metos3d_residual(self._ctx, _dev_ptr(a, self.numel, "a"), _dev_ptr(b, self.numel, "b"),
+                                        C.byref(out)), self._ctx)
+        return out.value
+
+    def check_finite(self, y):
+        self._sync_stream()
+        return self._L.metos3d_check_finite(self._ctx, _dev_ptr(y, self.numel, "y"))
+
+    def last_launch_count(self):
+        return int(self._L.metos3d_last_launch_count(self._ctx))
+
+    def last_error(self):
+        return self._L.metos3d_last_error(self._ctx).decode(errors="replace")
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._L.metos3d_free(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,774 @@
+// metos3d.cu -- the C ABI of include/metos3d.h: context set-up (validation and device
+// layouts), the TMM step and year map (Metos3D, arXiv:1410.0204, Sections 3 and 4),
+// diagnostics and the model-interface entry of Section 5.2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "metos3d.h"
+#include "tmm_kernels.cuh"
+
+using m3d::StepParams;
+using m3d::Tile;
+
+// ------------------------------------------------------------------------------ kernels
+namespace {
+
+template <int NTR, int MODEL>
+__global__ void __launch_bounds__(m3d::kThreads) k_step(StepParams P, int j, const double *y,
+                                                        double *yn)
+{
+    extern __shared__ double smem[];
+    m3d::step_tile<NTR, MODEL, false>(P, blockIdx.x, j, y, yn, smem);
+}
+
+// Per-call tables of the PO4-DOP model that depend on the parameters u:
+// atten = sigma_PAR exp(-k_w d) on euphotic cells, mfrac = Martin profile on aphotic cells.
+__global__ void k_ndop_prologue(int n, const int *cell_kl, const double *h, const double *zc,
+                                const double *u, double *atten, double *mfrac)
+{
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= n) return;
+    int kl = cell_kl[cell];
+    int k = kl & 0xff, L = kl >> 8;
+    double kw = u[0], b = u[6];
+    bool euphotic = (L <= m3d::kEuphotic) || (k < m3d::kEuphotic);
+    atten[cell] = euphotic ? m3d::kSigmaPar * exp(-zc[cell] * kw) : 0.0;
+    mfrac[cell] = euphotic ? 0.0 : m3d::martin_fraction(h + cell - k, k, L, b);
+}
+
+// Insolation table I0[j][ulat] at the start of every step.
+__global__ void k_insolation_table(int nstep, int nulat, const double *ulat, double *I0)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)nstep * nulat) return;
+    int j = (int)(i / nulat), l = (int)(i % nulat);
+    I0[i] = m3d::insolation(ulat[l], (double)j / nstep);
+}
+
+// Deterministic FP64 reductions: fixed grid, per-block partials, one final ordered sum.
+constexpr int kRedBlocks = 512;
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double ws[m3d::kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += ws[i];
+    return s;
+}
+
+// mode 0: sum vol[i mod n] a[i]; mode 1: sum (a[i] - b[i])^2; mode 2: count non-finite a[i]
+__global__ void __launch_bounds__(m3d::kThreads) k_reduce(int mode, long long len, int n,
+                                                          const double *a, const double *b,
+                                                          const double *vol, double *part)
+{
+    double v = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x) {
+        double x = a[i];
+        if (mode == 0) v += vol[i % n] * x;
+        else if (mode == 1) { double d = x - b[i]; v += d * d; }
+        else v += isfinite(x) ? 0.0 : 1.0;
+    }
+    double s = block_sum(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_reduce_final(int nblocks, const double *part, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nblocks; i++) s += part[i];
+        out[0] = s;
+    }
+}
+
+// The model interface of Section 5.2 on one column (one thread per layer).
+__global__ void k_bgc_column(int model, double dt, double insol, double ice, int nlayer,
+                             const double *h, const double *d, const double *y, double *ybgc,
+                             const double *u, int nsub)
+{
+    __shared__ double ek[M3D_MAX_LAYERS];
+    int k = threadIdx.x;
+    if (model == m3d::kModelNone) {
+        for (int i = k; i < 2 * nlayer; i += blockDim.x) ybgc[i] = 0.0;
+        return;
+    }
+    const double kw = u[0], alpha = u[1] * 360.0, sigma = u[2], lambda = u[3], KN = u[4];
+    const double KI = u[5], b = u[6];
+    const double ds = dt / nsub;
+    const int L = nlayer;
+    const double Isurf = insol * m3d::kSigmaPar * (1.0 - ice);
+    if (L <= m3d::kEuphotic) {
+        if (k == 0) {
+            double I[m3d::kEuphotic], dN[m3d::kEuphotic], dD[m3d::kEuphotic];
+            for (int kk = 0; kk < L; kk++) I[kk] = Isurf * exp(-d[kk] * kw);
+            m3d::ndop_shallow_column(L, h, y, y + L, I, alpha, sigma, lambda, KN, KI, ds, nsub, dN, dD);
+            for (int kk = 0; kk < L; kk++) { ybgc[kk] = dN[kk]; ybgc[L + kk] = dD[kk]; }
+        }
+        return;
+    }
+    if (k < m3d::kEuphotic) {
+        double dN, dD, fsum;
+        m3d::ndop_euphotic(y[k], y[L + k], Isurf * exp(-d[k] * kw), alpha, sigma, lambda, KN, KI,
+                           ds, nsub, dN, dD, fsum);
+        ybgc[k] = dN;
+        ybgc[L + k] = dD;
+        ek[k] = (1.0 - sigma) * fsum * h[k];
+    }
+    __syncthreads();
+    if (k >= m3d::kEuphotic && k < L) {
+        double dN, dD;
+        m3d::ndop_aphotic(y[L + k], ek[0] + ek[1], m3d::martin_fraction(h, k, L, b), lambda, ds,
+                          nsub, dN, dD);
+        ybgc[k] = dN;
+        ybgc[L + k] = dD;
+    }
+}
+
+typedef void (*step_kernel_t)(StepParams, int, const double *, double *);
+
+step_kernel_t pick_step_kernel(int model, int ntr)
+{
+    if (model == m3d::kModelNdop) return ntr == 2 ? k_step<2, m3d::kModelNdop> : nullptr;
+    switch (ntr) {
+    case 1: return k_step<1, m3d::kModelNone>;
+    case 2: return k_step<2, m3d::kModelNone>;
+    case 3: return k_step<3, m3d::kModelNone>;
+    case 4: return k_step<4, m3d::kModelNone>;
+    case 5: return k_step<5, m3d::kModelNone>;
+    case 6: return k_step<6, m3d::kModelNone>;
+    case 7: return k_step<7, m3d::kModelNone>;
+    case 8: return k_step<8, m3d::kModelNone>;
+    default: return nullptr;
+    }
+}
+
+thread_local std::string g_init_error;
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ context
+struct m3d_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n = 0, ncol = 0, ntr = 0, nparam = 0, nsub = 1, nstep = 0, nmonth = 0, model = 0;
+    int ntiles = 0, zmax = 0, nulat = 0;
+    size_t smem_bytes = 0;
+    std::vector<void *> allocs;
+    StepParams P{};
+    step_kernel_t step_kernel = nullptr;
+    double *u_dev = nullptr;
+    double *ybuf[2] = {nullptr, nullptr};
+    double *atten = nullptr, *mfrac = nullptr;
+    double *vol = nullptr, *h = nullptr, *zc = nullptr;
+    int *cell_kl = nullptr;
+    double *red_part = nullptr, *red_out = nullptr, *red_host = nullptr;
+    cudaGraphExec_t year_graph = nullptr;
+    int year_result_buf = 0;
+    long long last_launches = 0;
+    std::string err;
+};
+
+namespace {
+
+m3d_status fail(m3d_ctx *c, m3d_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_init_error = buf;
+    return s;
+}
+
+#define CUDA_OR_FAIL(ctx, call)                                                              \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), M3D_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+cudaError_t upload(m3d_ctx *c, T **dst, const T *src, size_t count)
+{
+    *dst = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * count);
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(*dst);
+    if (src) return cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t upload_vec(m3d_ctx *c, const T **dst, const std::vector<T> &v)
+{
+    T *p = nullptr;
+    cudaError_t e = upload(c, &p, v.empty() ? nullptr : v.data(), v.size());
+    *dst = p;
+    return e;
+}
+
+void release(m3d_ctx *c)
+{
+    if (!c) return;
+    if (c->year_graph) cudaGraphExecDestroy(c->year_graph);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->red_host) cudaFreeHost(c->red_host);
+    c->allocs.clear();
+}
+
+bool all_finite(const double *p, size_t count)
+{
+    for (size_t i = 0; i < count; i++)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Contiguous partition of the water columns into tiles of about equal FP64 work.
+std::vector<int> partition_columns(const m3d_grid *g, const int *rowptr, int ntr, int ntiles)
+{
+    std::vector<double> work(g->ncol);
+    for (int c = 0; c < g->ncol; c++) {
+        int s = g->col_start[c], e = g->col_start[c + 1], L = e - s;
+        double nnz = rowptr[e] - rowptr[s];
+        work[c] = (1.0 + ntr) * (nnz + (double)L * L) + 8.0 * L;
+    }
+    double total = std::accumulate(work.begin(), work.end(), 0.0);
+    std::vector<int> bounds{0};
+    double acc = 0.0;
+    for (int c = 0; c < g->ncol; c++) {
+        acc += work[c];
+        int t = (int)bounds.size();
+        if (t < ntiles && acc >= total * t / ntiles && c + 1 < g->ncol) bounds.push_back(c + 1);
+    }
+    bounds.push_back(g->ncol);
+    return bounds;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *metos3d_last_error(const m3d_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+m3d_status metos3d_info(const m3d_ctx *ctx, int *n, int *ncol, int *ntracer, int *nstep)
+{
+    if (!ctx) return fail(nullptr, M3D_ERR_ARG, "metos3d_info: null context");
+    if (n) *n = ctx->n;
+    if (ncol) *ncol = ctx->ncol;
+    if (ntracer) *ntracer = ctx->ntr;
+    if (nstep) *nstep = ctx->nstep;
+    return M3D_OK;
+}
+
+long long metos3d_last_launch_count(const m3d_ctx *ctx) { return ctx ? ctx->last_launches : -1; }
+
+void metos3d_free(m3d_ctx *ctx)
+{
+    if (!ctx) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    release(ctx);
+    cudaSetDevice(prev);
+    delete ctx;
+}
+
+m3d_status metos3d_set_stream(m3d_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(nullptr, M3D_ERR_ARG, "metos3d_set_stream: null context");
+    ctx->stream = (cudaStream_t)stream;
+    return M3D_OK;
+}
+
+m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt,
+                        const m3d_model *md, void *stream)
+{
+    if (!out) return fail(nullptr, M3D_ERR_ARG, "metos3d_init: out is null");
+    *out = nullptr;
+    if (!g || !mt || !md) return fail(nullptr, M3D_ERR_ARG, "metos3d_init: null grid, matrices or model");
+    // ---- validation
+    if (g->n <= 0 || g->ncol <= 0 || !g->col_start || !g->h || !g->zc || !g->vol || !g->lat)
+        return fail(nullptr, M3D_ERR_ARG, "grid: bad sizes or null arrays");
+    if (g->col_start[0] != 0 || g->col_start[g->ncol] != g->n)
+        return fail(nullptr, M3D_ERR_ARG, "grid: col_start must run from 0 to n");
+    long long s_imp = 0;
+    for (int c = 0; c < g->ncol; c++) {
+        int L = g->col_start[c + 1] - g->col_start[c];
+        if (L < 1 || L > M3D_MAX_LAYERS)
+            return fail(nullptr, M3D_ERR_ARG, "grid: column %d has %d layers (1..%d allowed)", c, L, M3D_MAX_LAYERS);
+        if (!(g->lat[c] >= -90.0 && g->lat[c] <= 90.0))
+            return fail(nullptr, M3D_ERR_ARG, "grid: latitude of column %d out of range", c);
+        s_imp += (long long)L * L;
+    }
+    for (int i = 0; i < g->n; i++)
+        if (!(g->h[i] > 0.0) || !std::isfinite(g->h[i]) || !std::isfinite(g->zc[i]) || !std::isfinite(g->vol[i]))
+            return fail(nullptr, M3D_ERR_ARG, "grid: bad h, zc or vol at cell %d", i);
+    if (md->nstep <= 0 || md->nsub < 1)
+        return fail(nullptr, M3D_ERR_ARG, "model: nstep and nsub must be positive");
+    if (md->model_id == M3D_MODEL_NDOP) {
+        if (md->ntracer != 2 || md->nparam != 7)
+            return fail(nullptr, M3D_ERR_ARG, "model: PO4-DOP needs 2 tracers and 7 parameters");
+    } else if (md->model_id == M3D_MODEL_NONE) {
+        if (md->ntracer < 1 || md->ntracer > M3D_MAX_TRACERS || md->nparam < 0)
+            return fail(nullptr, M3D_ERR_ARG, "model: 1..%d tracers for the transport-only model", M3D_MAX_TRACERS);
+    } else {
+        return fail(nullptr, M3D_ERR_UNSUPPORTED, "model: unknown model_id %d", md->model_id);
+    }
+    if (mt->nmonth < 1 || mt->nnz < g->n || !mt->exp_rowptr || !mt->exp_colidx || !mt->exp_val || !mt->imp_blk)
+        return fail(nullptr, M3D_ERR_ARG, "matrices: bad sizes or null arrays");
+    if (mt->s_imp != s_imp)
+        return fail(nullptr, M3D_ERR_ARG, "matrices: s_imp is %lld, the columns need %lld", mt->s_imp, s_imp);
+    const int *rp = mt->exp_rowptr, *ci = mt->exp_colidx;
+    if (rp[0] != 0 || rp[g->n] != mt->nnz)
+        return fail(nullptr, M3D_ERR_ARG, "matrices: rowptr must run from 0 to nnz");
+    for (int i = 0; i < g->n; i++) {
+        if (rp[i + 1] < rp[i]) return fail(nullptr, M3D_ERR_ARG, "matrices: rowptr decreases at row %d", i);
+        for (int p = rp[i]; p < rp[i + 1]; p++) {
+            if (ci[p] < 0 || ci[p] >= g->n)
+                return fail(nullptr, M3D_ERR_ARG, "matrices: column index out of range in row %d", i);
+            if (p > rp[i] && ci[p] <= ci[p - 1])
+                return fail(nullptr, M3D_ERR_ARG, "matrices: row %d is not sorted or has duplicates", i);
+        }
+    }
+    if (!all_finite(mt->exp_val, (size_t)mt->nmonth * mt->nnz) || !all_finite(mt->imp_blk, (size_t)mt->nmonth * s_imp))
+        return fail(nullptr, M3D_ERR_ARG, "matrices: non-finite values");
+
+    m3d_ctx *c = new (std::nothrow) m3d_ctx();
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "out of host memory");
+    auto bail = [&](m3d_status s) {
+        g_init_error = c->err;
+        release(c);
+        delete c;
+        return s;
+    };
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)stream;
+    c->n = g->n;
+    c->ncol = g->ncol;
+    c->ntr = md->ntracer;
+    c->nparam = md->nparam;
+    c->nsub = md->nsub;
+    c->nstep = md->nstep;
+    c->nmonth = mt->nmonth;
+    c->model = md->model_id;
+    c->step_kernel = pick_step_kernel(c->model, c->ntr);
+    if (!c->step_kernel) {
+        fail(c, M3D_ERR_UNSUPPORTED, "no step kernel for model %d with %d tracers", c->model, c->ntr);
+        return bail(M3D_ERR_UNSUPPORTED);
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
+        fail(c, M3D_ERR_CUDA, "cudaGetDeviceProperties failed");
+        return bail(M3D_ERR_CUDA);
+    }
+
+    // ---- tiles of whole columns
+    int ntarget = std::min(g->ncol, 2 * prop.multiProcessorCount);
+    std::vector<int> bounds = partition_columns(g, rp, c->ntr, ntarget);
+    int ntiles = (int)bounds.size() - 1;
+    c->ntiles = ntiles;
+
+    std::vector<Tile> tiles(ntiles);
+    std::vector<int> sp_len, sp_off, sp_row, sp_col;
+    std::vector<int> bk_len, bk_off, bk_row, bk_cb, bk_L;
+    int sp_slots = 0, bk_slots = 0, zmax = 0;
+    // first pass: the slice structure; values are filled per month afterwards
+    struct SliceRef { int tile_cell0; std::vector<int> rows; };
+    std::vector<int> sp_rows_flat, bk_rows_flat;   // global row per (slice, lane), -1 if empty
+    for (int t = 0; t < ntiles; t++) {
+        int c0 = bounds[t], c1 = bounds[t + 1];
+        int cell0 = g->col_start[c0], cell1 = g->col_start[c1];
+        int nc = cell1 - cell0;
+        zmax = std::max(zmax, nc);
+        Tile &T = tiles[t];
+        T.cell0 = cell0;
+        T.ncell = nc;
+        T.pad0 = T.pad1 = 0;
+        // explicit slices: rows by decreasing nonzero count
+        std::vector<int> rows(nc);
+        std::iota(rows.begin(), rows.end(), cell0);
+        std::stable_sort(rows.begin(), rows.end(), [&](int a, int b) {
+            return (rp[a + 1] - rp[a]) > (rp[b + 1] - rp[b]);
+        });
+        T.sp0 = (int)sp_len.size();
+        for (int s0 = 0; s0 < nc; s0 += 32) {
+            int len = 0;
+            for (int l = 0; l < 32; l++) {
+                int r = s0 + l < nc ? rows[s0 + l] : -1;
+                sp_rows_flat.push_back(r);
+                sp_row.push_back(r >= 0 ? r - cell0 : -1);
+                if (r >= 0) len = std::max(len, rp[r + 1] - rp[r]);
+            }
+            sp_len.push_back(len);
+            sp_off.push_back(sp_slots);
+            sp_slots += len;
+        }
+        T.sp1 = (int)sp_len.size();
+        // implicit slices: rows by decreasing column depth
+        std::vector<int> colL(nc), colB(nc);
+        for (int cc = c0; cc < c1; cc++)
+            for (int i = g->col_start[cc]; i < g->col_start[cc + 1]; i++) {
+                colL[i - cell0] = g->col_start[cc + 1] - g->col_start[cc];
+                colB[i - cell0] = g->col_start[cc] - cell0;
+            }
+        std::vector<int> brow(nc);
+        std::iota(brow.begin(), brow.end(), 0);
+        std::stable_sort(brow.begin(), brow.end(), [&](int a, int b) { return colL[a] > colL[b]; });
+        T.bk0 = (int)bk_len.size();
+        for (int s0 = 0; s0 < nc; s0 += 32) {
+            int len = 0;
+            for (int l = 0; l < 32; l++) {
+                int r = s0 + l < nc ? brow[s0 + l] : -1;
+                bk_rows_flat.push_back(r >= 0 ? r + cell0 : -1);
+                bk_row.push_back(r);
+                bk_cb.push_back(r >= 0 ? colB[r] : 0);
+                bk_L.push_back(r >= 0 ? colL[r] : 0);
+                if (r >= 0) len = std::max(len, colL[r]);
+            }
+            bk_len.push_back(len);
+            bk_off.push_back(bk_slots);
+            bk_slots += len;
+        }
+        T.bk1 = (int)bk_len.size();
+    }
+    c->zmax = zmax;
+
+    // column block offsets and per-cell tables
+    std::vector<long long> blk_off(g->ncol + 1, 0);
+    for (int cc = 0; cc < g->ncol; cc++) {
+        long long L = g->col_start[cc + 1] - g->col_start[cc];
+        blk_off[cc + 1] = blk_off[cc] + L * L;
+    }
+    std::vector<int> cell_col(g->n), cell_kl(g->n), cell_ulat(g->n);
+    std::vector<double> ulat(g->lat, g->lat + g->ncol);
+    std::sort(ulat.begin(), ulat.end());
+    ulat.erase(std::unique(ulat.begin(), ulat.end()), ulat.end());
+    c->nulat = (int)ulat.size();
+    for (int cc = 0; cc < g->ncol; cc++) {
+        int L = g->col_start[cc + 1] - g->col_start[cc];
+        int li = (int)(std::lower_bound(ulat.begin(), ulat.end(), g->lat[cc]) - ulat.begin());
+        for (int k = 0; k < L; k++) {
+            int i = g->col_start[cc] + k;
+            cell_col[i] = cc;
+            cell_kl[i] = k | (L << 8);
+            cell_ulat[i] = li;
+        }
+    }
+
+    // values in slice layout, month by month: A_m and A_{m+1} - A_m
+    const long long spn = (long long)sp_slots * 32, bkn = (long long)bk_slots * 32;
+    std::vector<double> sp_a((size_t)(spn * c->nmonth), 0.0), sp_d((size_t)(spn * c->nmonth), 0.0);
+    sp_col.assign((size_t)spn, 0);
+    for (size_t s = 0; s < sp_len.size(); s++)
+        for (int l = 0; l < 32; l++) {
+            int r = sp_rows_flat[s * 32 + l];
+            for (int q = 0; q < sp_len[s]; q++) {
+                size_t idx = ((size_t)sp_off[s] + q) * 32 + l;
+                if (r < 0) { sp_col[idx] = 0; continue; }
+                int nr = rp[r + 1] - rp[r];
+                int p = rp[r] + std::min(q, nr - 1);
+                sp_col[idx] = ci[p];
+                for (int m = 0; m < c->nmonth; m++) {
+                    double a0 = q < nr ? mt->exp_val[(size_t)m * mt->nnz + p] : 0.0;
+                    double a1 = q < nr ? mt->exp_val[(size_t)((m + 1) % c->nmonth) * mt->nnz + p] : 0.0;
+                    sp_a[(size_t)m * spn + idx] = a0;
+                    sp_d[(size_t)m * spn + idx] = a1 - a0;
+                }
+            }
+        }
+    std::vector<double> bk_b((size_t)(bkn * c->nmonth), 0.0), bk_d((size_t)(bkn * c->nmonth), 0.0);
+    for (size_t s = 0; s < bk_len.size(); s++)
+        for (int l = 0; l < 32; l++) {
+            int r = bk_rows_flat[s * 32 + l];
+            if (r < 0) continue;
+            int cc = cell_col[r];
+            int L = g->col_start[cc + 1] - g->col_start[cc];
+            int rr = r - g->col_start[cc];
+            for (int k = 0; k < L; k++) {
+                size_t idx = ((size_t)bk_off[s] + k) * 32 + l;
+                size_t src = (size_t)blk_off[cc] + (size_t)rr * L + k;
+                for (int m = 0; m < c->nmonth; m++) {
+                    double b0 = mt->imp_blk[(size_t)m * s_imp + src];
+                    double b1 = mt->imp_blk[(size_t)((m + 1) % c->nmonth) * s_imp + src];
+                    bk_b[(size_t)m * bkn + idx] = b0;
+                    bk_d[(size_t)m * bkn + idx] = b1 - b0;
+                }
+            }
+        }
+
+    // ---- upload
+    StepParams &P = c->P;
+    P.n = c->n;
+    P.nstep = c->nstep;
+    P.nmonth = c->nmonth;
+    P.nsub = c->nsub;
+    P.nulat = c->nulat;
+    P.zmax = c->zmax;
+    P.sp_mstride = spn;
+    P.bk_mstride = bkn;
+    cudaError_t e = cudaSuccess;
+#define UP(...) do { e = (__VA_ARGS__); if (e != cudaSuccess) { fail(c, M3D_ERR_CUDA, "device upload: %s", cudaGetErrorString(e)); return bail(M3D_ERR_CUDA); } } while (0)
+    UP(upload_vec(c, &P.tiles, tiles));
+    UP(upload_vec(c, &P.sp_len, sp_len));
+    UP(upload_vec(c, &P.sp_off, sp_off));
+    UP(upload_vec(c, &P.sp_row, sp_row));
+    UP(upload_vec(c, &P.sp_col, sp_col));
+    UP(upload_vec(c, &P.sp_a, sp_a));
+    UP(upload_vec(c, &P.sp_d, sp_d));
+    UP(upload_vec(c, &P.bk_len, bk_len));
+    UP(upload_vec(c, &P.bk_off, bk_off));
+    UP(upload_vec(c, &P.bk_row, bk_row));
+    UP(upload_vec(c, &P.bk_cb, bk_cb));
+    UP(upload_vec(c, &P.bk_L, bk_L));
+    UP(upload_vec(c, &P.bk_b, bk_b));
+    UP(upload_vec(c, &P.bk_d, bk_d));
+    UP(upload_vec(c, &P.cell_kl, cell_kl));
+    UP(upload_vec(c, &P.cell_ulat, cell_ulat));
+    c->cell_kl = const_cast<int *>(P.cell_kl);
+    UP(upload(c, &c->h, g->h, (size_t)c->n));
+    UP(upload(c, &c->zc, g->zc, (size_t)c->n));
+    UP(upload(c, &c->vol, g->vol, (size_t)c->n));
+    P.h = c->h;
+    UP(upload(c, &c->atten, (const double *)nullptr, (size_t)c->n));
+    UP(upload(c, &c->mfrac, (const double *)nullptr, (size_t)c->n));
+    P.atten = c->atten;
+    P.mfrac = c->mfrac;
+    UP(upload(c, &c->u_dev, (const double *)nullptr, (size_t)std::max(1, c->nparam)));
+    P.u = c->u_dev;
+    UP(upload(c, &c->ybuf[0], (const double *)nullptr, (size_t)c->ntr * c->n));
+    UP(upload(c, &c->ybuf[1], (const double *)nullptr, (size_t)c->ntr * c->n));
+    UP(upload(c, &c->red_part, (const double *)nullptr, (size_t)kRedBlocks));
+    UP(upload(c, &c->red_out, (const double *)nullptr, (size_t)1));
+    UP(cudaMallocHost((void **)&c->red_host, sizeof(double)));
+    UP(cudaMemset(c->atten, 0, sizeof(double) * c->n));
+    UP(cudaMemset(c->mfrac, 0, sizeof(double) * c->n));
+    UP(cudaMemset(c->u_dev, 0, sizeof(double) * std::max(1, c->nparam)));
+    // insolation table at the start of every step
+    double *ulat_dev = nullptr, *I0 = nullptr;
+    UP(upload(c, &ulat_dev, ulat.data(), ulat.size()));
+    UP(upload(c, &I0, (const double *)nullptr, (size_t)c->nstep * c->nulat));
+    {
+        long long tot = (long long)c->nstep * c->nulat;
+        k_insolation_table<<<(unsigned)((tot + 255) / 256), 256>>>(c->nstep, c->nulat, ulat_dev, I0);
+        UP(cudaGetLastError());
+        UP(cudaDeviceSynchronize());
+    }
+    P.I0tab = I0;
+    c->smem_bytes = sizeof(double) * (size_t)(c->ntr + 1) * c->zmax;
+    if (c->smem_bytes > 48 * 1024) {
+        UP(cudaFuncSetAttribute((const void *)c->step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)c->smem_bytes));
+    }
+#undef UP
+    *out = c;
+    return M3D_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+m3d_status launch_prologue(m3d_ctx *c, const double *u)
+{
+    if (c->model != M3D_MODEL_NDOP) return M3D_OK;
+    k_ndop_prologue<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->n, c->cell_kl, c->h, c->zc, u,
+                                                               c->atten, c->mfrac);
+    CUDA_OR_FAIL(c, cudaGetLastError());
+    return M3D_OK;
+}
+
+m3d_status launch_step(m3d_ctx *c, int j, const double *y, double *yn)
+{
+    c->step_kernel<<<c->ntiles, m3d::kThreads, c->smem_bytes, c->stream>>>(c->P, j, y, yn);
+    CUDA_OR_FAIL(c, cudaGetLastError());
+    return M3D_OK;
+}
+
+m3d_status build_year_graph(m3d_ctx *c)
+{
+    cudaStream_t s = c->stream;
+    bool own = false;
+    if (!s) {
+        // capture needs a non-legacy stream
+        CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        own = true;
+    }
+    cudaStream_t saved = c->stream;
+    c->stream = s;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    m3d_status st = M3D_OK;
+    if (e == cudaSuccess) {
+        st = launch_prologue(c, c->u_dev);
+        for (int j = 0; j < c->nstep && st == M3D_OK; j++)
+            st = launch_step(c, j, c->ybuf[j & 1], c->ybuf[(j + 1) & 1]);
+        e = cudaStreamEndCapture(s, &graph);
+    }
+    c->stream = saved;
+    if (own) cudaStreamDestroy(s);
+    if (st != M3D_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) return fail(c, M3D_ERR_CUDA, "year graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->year_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, M3D_ERR_CUDA, "year graph instantiate: %s", cudaGetErrorString(e));
+    c->year_result_buf = c->nstep & 1;
+    return M3D_OK;
+}
+
+m3d_status reduce(m3d_ctx *c, int mode, const double *a, const double *b, double *out)
+{
+    long long len = (long long)c->ntr * c->n;
+    k_reduce<<<kRedBlocks, m3d::kThreads, 0, c->stream>>>(mode, len, c->n, a, b, c->vol, c->red_part);
+    CUDA_OR_FAIL(c, cudaGetLastError());
+    k_reduce_final<<<1, 32, 0, c->stream>>>(kRedBlocks, c->red_part, c->red_out);
+    CUDA_OR_FAIL(c, cudaGetLastError());
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->red_host, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    *out = *c->red_host;
+    return M3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+m3d_status metos3d_step(m3d_ctx *c, int j, const double *y_in, double *y_out, const double *u)
+{
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_step: null context");
+    if (j < 0 || j >= c->nstep) return fail(c, M3D_ERR_ARG, "metos3d_step: j = %d outside [0, %d)", j, c->nstep);
+    if (!y_in || !y_out || (c->nparam > 0 && !u)) return fail(c, M3D_ERR_ARG, "metos3d_step: null pointer");
+    size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    const char *a = (const char *)y_in, *b = (const char *)y_out;
+    if (a < b + len && b < a + len) return fail(c, M3D_ERR_ARG, "metos3d_step: y_in and y_out overlap");
+    if (c->nparam > 0)
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_dev, u, sizeof(double) * c->nparam, cudaMemcpyDeviceToDevice, c->stream));
+    m3d_status st = launch_prologue(c, c->u_dev);
+    if (st != M3D_OK) return st;
+    return launch_step(c, j, y_in, y_out);
+}
+
+m3d_status metos3d_year_map(m3d_ctx *c, const double *y0, double *y1, const double *u)
+{
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_map: null context");
+    if (!y0 || !y1 || (c->nparam > 0 && !u)) return fail(c, M3D_ERR_ARG, "metos3d_year_map: null pointer");
+    if (!c->year_graph) {
+        m3d_status st = build_year_graph(c);
+        if (st != M3D_OK) return st;
+    }
+    size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    if (c->nparam > 0)
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_dev, u, sizeof(double) * c->nparam, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], y0, len, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaGraphLaunch(c->year_graph, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(y1, c->ybuf[c->year_result_buf], len, cudaMemcpyDeviceToDevice, c->stream));
+    c->last_launches = (c->model == M3D_MODEL_NDOP ? 1 : 0) + c->nstep;
+    return M3D_OK;
+}
+
+m3d_status metos3d_year_map_host(m3d_ctx *c, const double *y0_host, double *y1_host, const double *u_host)
+{
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_map_host: null context");
+    if (!y0_host || !y1_host || (c->nparam > 0 && !u_host))
+        return fail(c, M3D_ERR_ARG, "metos3d_year_map_host: null pointer");
+    if (!c->year_graph) {
+        m3d_status st = build_year_graph(c);
+        if (st != M3D_OK) return st;
+    }
+    size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    if (c->nparam > 0)
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_dev, u_host, sizeof(double) * c->nparam, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], y0_host, len, cudaMemcpyHostToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaGraphLaunch(c->year_graph, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(y1_host, c->ybuf[c->year_result_buf], len, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    c->last_launches = (c->model == M3D_MODEL_NDOP ? 1 : 0) + c->nstep;
+    return M3D_OK;
+}
+
+m3d_status metos3d_mass(m3d_ctx *c, const double *y, double *mass)
+{
+    if (!c || !y || !mass) return fail(c, M3D_ERR_ARG, "metos3d_mass: null argument");
+    return reduce(c, 0, y, nullptr, mass);
+}
+
+m3d_status metos3d_residual(m3d_ctx *c, const double *a, const double *b, double *norm)
+{
+    if (!c || !a || !b || !norm) return fail(c, M3D_ERR_ARG, "metos3d_residual: null argument");
+    double s = 0.0;
+    m3d_status st = reduce(c, 1, a, b, &s);
+    if (st == M3D_OK) *norm = std::sqrt(s);
+    return st;
+}
+
+m3d_status metos3d_check_finite(m3d_ctx *c, const double *y)
+{
+    if (!c || !y) return fail(c, M3D_ERR_ARG, "metos3d_check_finite: null argument");
+    double bad = 0.0;
+    m3d_status st = reduce(c, 2, y, nullptr, &bad);
+    if (st != M3D_OK) return st;
+    if (bad != 0.0) return fail(c, M3D_ERR_NONFINITE, "state holds %.0f non-finite values", bad);
+    return M3D_OK;
+}
+
+m3d_status metos3d_bgc(int model_id, double t, double dt, double lat, double insol, double dayfrac,
+                       double ice, double wind, int ntracer, int nlayer, const double *h,
+                       const double *d, const double *salt, const double *temp, const double *y,
+                       double *ybgc, int nparam, const double *u, int nsub)
+{
+    (void)t; (void)lat; (void)dayfrac; (void)wind; (void)salt; (void)temp;
+    if (nlayer < 1 || nlayer > M3D_MAX_LAYERS || nsub < 1 || !h || !d || !y || !ybgc)
+        return fail(nullptr, M3D_ERR_ARG, "metos3d_bgc: bad sizes or null arrays");
+    if (model_id == M3D_MODEL_NDOP) {
+        if (ntracer != 2 || nparam != 7 || !u) return fail(nullptr, M3D_ERR_ARG, "metos3d_bgc: PO4-DOP needs 2 tracers, 7 parameters");
+    } else if (model_id == M3D_MODEL_NONE) {
+        if (ntracer < 1 || ntracer > M3D_MAX_TRACERS) return fail(nullptr, M3D_ERR_ARG, "metos3d_bgc: bad tracer count");
+    } else {
+        return fail(nullptr, M3D_ERR_UNSUPPORTED, "metos3d_bgc: unknown model %d", model_id);
+    }
+    size_t ny = (size_t)ntracer * nlayer;
+    double *buf = nullptr;
+    size_t tot = 2 * (size_t)nlayer + 2 * ny + 8;
+    if (cudaMalloc((void **)&buf, sizeof(double) * tot) != cudaSuccess)
+        return fail(nullptr, M3D_ERR_CUDA, "metos3d_bgc: cudaMalloc failed");
+    double *dh = buf, *dd = buf + nlayer, *dy = buf + 2 * nlayer, *dyb = dy + ny, *du = dyb + ny;
+    cudaError_t e = cudaMemcpy(dh, h, sizeof(double) * nlayer, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dd, d, sizeof(double) * nlayer, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dy, y, sizeof(double) * ny, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && model_id == M3D_MODEL_NDOP) e = cudaMemcpy(du, u, sizeof(double) * 7, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        if (model_id == M3D_MODEL_NONE) e = cudaMemset(dyb, 0, sizeof(double) * ny);
+        else {
+            k_bgc_column<<<1, M3D_MAX_LAYERS>>>(model_id, dt, insol, ice, nlayer, dh, dd, dy, dyb, du, nsub);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ybgc, dyb, sizeof(double) * ny, cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(nullptr, M3D_ERR_CUDA, "metos3d_bgc: %s", cudaGetErrorString(e));
+    return M3D_OK;
+}
+
+}  // extern "C"

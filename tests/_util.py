@@ -1,0 +1,10 @@
+"""Helpers shared by the tests."""
+import numpy as np
+
+
+def rel_err(got, want, floor=1e-6):
+    """max_i |g_i - o_i| / max(|o_i|, floor * max|o|): the parity measure of the year map."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    scale = np.maximum(np.abs(want), floor * np.abs(want).max())
+    return float(np.max(np.abs(got - want) / scale))

@@ -1,0 +1,40 @@
+"""The C ABI library loads and exports every function include/metos3d.h declares (no GPU needed)."""
+import ctypes
+import os
+
+import pytest
+
+import paper_1410_0204_gb300 as m3d
+from paper_1410_0204_gb300 import build as b
+
+
+@pytest.fixture(scope="module")
+def lib():
+    b.build()
+    return ctypes.CDLL(b.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = m3d.declared_symbols()
+    for required in ("metos3d_init", "metos3d_step", "metos3d_year_map", "metos3d_year_map_host",
+                     "metos3d_mass", "metos3d_residual", "metos3d_bgc", "metos3d_free", "metos3d_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in m3d.declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_loads(lib):
+    L = m3d.load()
+    assert L is not None
+    assert os.path.exists(m3d.library_path())
+
+
+def test_init_rejects_bad_grid_without_gpu_work(lib):
+    # argument validation happens before any device call
+    L = m3d.load()
+    ctx = ctypes.c_void_p()
+    assert L.metos3d_init(ctypes.byref(ctx), None, None, None, None) == m3d.M3D_ERR_ARG
+    assert b"null" in L.metos3d_last_error(None)
