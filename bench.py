@@ -292,6 +292,24 @@ def run_ours(args):
     return 0
 
 
+def run_profile_steps(nsteps):
+    """A short run for profilers: set up the benchmark workload and run nsteps single TMM steps."""
+    import torch
+    import paper_1410_0204_gb300 as m3d
+    prob = mi.make_problem(WORKLOAD)
+    ctx = m3d.Context.from_problem(prob, model=m3d.MODEL_NDOP, ntracer=2, nparam=7)
+    y = torch.from_numpy(mi.initial_state(prob)).cuda()
+    u = torch.from_numpy(mi.default_params_ndop()).cuda()
+    yn = torch.empty_like(y)
+    for j in range(nsteps):
+        ctx.step(j, y, yn, u)
+        y, yn = yn, y
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"profile_steps": nsteps, "workload": WORKLOAD}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,7 +317,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only run this many single TMM steps of the workload (for profilers)")
     args = ap.parse_args()
+    if args.profile_steps:
+        return run_profile_steps(args.profile_steps)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
