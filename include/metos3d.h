@@ -163,6 +163,27 @@ m3d_status metos3d_bgc(int model_id, double t, double dt, double lat, double ins
                        const double *temp, const double *y, double *ybgc, int nparam,
                        const double *u, int nsub);
 
+/*
+ * || a - b ||_2 over len doubles (device arrays a, b), written to the device double
+ * *norm_dev, without allocating anything.  The paper has no counterpart: this is the
+ * metos3d_residual reduction for callers that cannot call cudaMalloc when they need the
+ * norm (for example while a stream is being captured into a CUDA graph, or when another
+ * allocator owns all device memory), and it needs no context.
+ * Its per-block partial sums live in one static device array of
+ * M3D_RESIDUAL_STATIC_MAX_BLOCKS doubles (512 KiB), which every GPU that loads the
+ * library keeps until the process exits; len may be at most
+ * M3D_RESIDUAL_STATIC_MAX_BLOCKS * 2048 (about 134 million doubles), larger sizes
+ * return M3D_ERR_ARG.  Asynchronous on `stream` (a cudaStream_t).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array, so calls that overlap on
+ * the GPU (on different streams) race; calls on one stream are ordered and safe.
+ * The message of the last failure is metos3d_residual_static_error().
+ */
+#define M3D_RESIDUAL_STATIC_MAX_BLOCKS 65536
+m3d_status metos3d_residual_static(const double *a, const double *b, long long len, double *norm_dev,
+                                   void *stream);
+const char *metos3d_residual_static_error(void);
+
 /* Sizes of a context: n, ncol, ntracer, nstep (any pointer may be NULL). */
 m3d_status metos3d_info(const m3d_ctx *ctx, int *n, int *ncol, int *ntracer, int *nstep);
 

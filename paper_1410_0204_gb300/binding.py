@@ -91,9 +91,13 @@ def load(build_if_missing: bool = False):
     L.metos3d_last_error.restype = C.c_char_p
     L.metos3d_free.argtypes = [vp]
     L.metos3d_free.restype = None
+    L.metos3d_residual_static.argtypes = [vp, vp, C.c_longlong, vp, vp]
+    L.metos3d_residual_static_error.argtypes = []
+    L.metos3d_residual_static_error.restype = C.c_char_p
     for name in declared_symbols():
         fn = getattr(L, name)
-        if name not in ("metos3d_last_error", "metos3d_free", "metos3d_last_launch_count"):
+        if name not in ("metos3d_last_error", "metos3d_free", "metos3d_last_launch_count",
+                        "metos3d_residual_static_error"):
             fn.restype = C.c_int
     _lib = L
     return L
