@@ -184,10 +184,41 @@ m3d_status metos3d_residual_static(const double *a, const double *b, long long l
                                    void *stream);
 const char *metos3d_residual_static_error(void);
 
+/*
+ * Wait for the context's stream and report a failure of the last year map that can only be
+ * seen on the device: M3D_ERR_TIMEOUT if the persistent year kernel gave up a bounded
+ * wait (its tiles wait only for neighbouring tiles, at most the configured timeout; on
+ * time-out they stop and the result is not valid).
+ */
+m3d_status metos3d_sync(m3d_ctx *ctx);
+
+/*
+ * Execution options (tuning and checks; the defaults need no setting):
+ *   M3D_OPT_YEAR_PLAN: M3D_PLAN_PERSISTENT (default when all tiles fit on the GPU at once):
+ *       the year map is one cooperative launch whose tiles synchronise with their
+ *       neighbours through per-tile step counters; M3D_PLAN_GRAPH: one kernel launch per
+ *       step, captured in a CUDA graph.
+ *   M3D_OPT_WAIT_TIMEOUT_NS: bound of every device-side wait of the persistent kernel
+ *       (default 2 s).
+ *   M3D_OPT_TEST_WITHHOLD_TILE: for tests of the timeout path only: the given tile never
+ *       announces its progress, so its neighbours' waits run out (-1: off, the default).
+ *   M3D_OPT_NTILES (read only): number of tiles (CTAs) of a step.
+ * metos3d_get_option returns -1 for an unknown option.
+ */
+enum {
+    M3D_OPT_YEAR_PLAN = 1,
+    M3D_OPT_WAIT_TIMEOUT_NS = 2,
+    M3D_OPT_TEST_WITHHOLD_TILE = 3,
+    M3D_OPT_NTILES = 4
+};
+enum { M3D_PLAN_PERSISTENT = 0, M3D_PLAN_GRAPH = 1 };
+m3d_status metos3d_set_option(m3d_ctx *ctx, int option, long long value);
+long long metos3d_get_option(const m3d_ctx *ctx, int option);
+
 /* Sizes of a context: n, ncol, ntracer, nstep (any pointer may be NULL). */
 m3d_status metos3d_info(const m3d_ctx *ctx, int *n, int *ncol, int *ntracer, int *nstep);
 
-/* Number of kernel launches the last metos3d_year_map issued. */
+/* Number of kernel launches the last metos3d_year_map issued (prologue included). */
 long long metos3d_last_launch_count(const m3d_ctx *ctx);
 
 /* Message for the last failure on ctx, or on metos3d_init when ctx is NULL. */

@@ -23,6 +23,13 @@ M3D_ERR_NONFINITE = -3
 M3D_ERR_TIMEOUT = -4
 M3D_ERR_UNSUPPORTED = -5
 
+OPT_YEAR_PLAN = 1
+OPT_WAIT_TIMEOUT_NS = 2
+OPT_TEST_WITHHOLD_TILE = 3
+OPT_NTILES = 4
+PLAN_PERSISTENT = 0
+PLAN_GRAPH = 1
+
 MODEL_NONE = 0
 MODEL_NDOP = 2
 
@@ -91,13 +98,17 @@ def load(build_if_missing: bool = False):
     L.metos3d_last_error.restype = C.c_char_p
     L.metos3d_free.argtypes = [vp]
     L.metos3d_free.restype = None
+    L.metos3d_sync.argtypes = [vp]
+    L.metos3d_set_option.argtypes = [vp, C.c_int, C.c_longlong]
+    L.metos3d_get_option.argtypes = [vp, C.c_int]
+    L.metos3d_get_option.restype = C.c_longlong
     L.metos3d_residual_static.argtypes = [vp, vp, C.c_longlong, vp, vp]
     L.metos3d_residual_static_error.argtypes = []
     L.metos3d_residual_static_error.restype = C.c_char_p
     for name in declared_symbols():
         fn = getattr(L, name)
         if name not in ("metos3d_last_error", "metos3d_free", "metos3d_last_launch_count",
-                        "metos3d_residual_static_error"):
+                        "metos3d_residual_static_error", "metos3d_get_option"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -255,6 +266,16 @@ class Context:
     def check_finite(self, y):
         self._sync_stream()
         return self._L.metos3d_check_finite(self._ctx, _dev_ptr(y, self.numel, "y"))
+
+    def sync(self):
+        """Wait for the stream; raises Metos3dError(M3D_ERR_TIMEOUT) if the last year map timed out."""
+        _check(self._L.metos3d_sync(self._ctx), self._ctx)
+
+    def set_option(self, option, value):
+        _check(self._L.metos3d_set_option(self._ctx, int(option), int(value)), self._ctx)
+
+    def get_option(self, option):
+        return int(self._L.metos3d_get_option(self._ctx, int(option)))
 
     def last_launch_count(self):
         return int(self._L.metos3d_last_launch_count(self._ctx))

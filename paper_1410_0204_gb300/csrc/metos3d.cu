@@ -30,12 +30,28 @@ __global__ void __launch_bounds__(m3d::kThreads) k_step(StepParams P, int j, con
     m3d::step_tile<NTR, MODEL, false>(P, blockIdx.x, j, y, yn, smem);
 }
 
+template <int NTR, int MODEL>
+__global__ void __launch_bounds__(m3d::kThreads) k_year(StepParams P, m3d::SyncParams S, double *buf0,
+                                                        double *buf1, int j0, int nsteps)
+{
+    extern __shared__ double smem[];
+    m3d::year_persistent<NTR, MODEL>(P, S, buf0, buf1, j0, nsteps, smem);
+}
+
 // Per-call tables of the PO4-DOP model that depend on the parameters u:
 // atten = sigma_PAR exp(-k_w d) on euphotic cells, mfrac = Martin profile on aphotic cells.
 __global__ void k_ndop_prologue(int n, const int *cell_kl, const double *h, const double *zc,
-                                const double *u, double *atten, double *mfrac)
+                                const double *u, double *atten, double *mfrac, double *qpar)
 {
     int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell == 0) {
+        qpar[m3d::kQAlpha] = u[1] * 360.0;       // alpha is given per day; time is in years
+        qpar[m3d::kQSigma] = u[2];
+        qpar[m3d::kQLambda] = u[3];
+        qpar[m3d::kQKN] = u[4];
+        qpar[m3d::kQKI] = u[5];
+        qpar[m3d::kQOneMinusSigma] = 1.0 - u[2];
+    }
     if (cell >= n) return;
     int kl = cell_kl[cell];
     int k = kl & 0xff, L = kl >> 8;
@@ -139,6 +155,23 @@ __global__ void k_bgc_column(int model, double dt, double insol, double ice, int
 }
 
 typedef void (*step_kernel_t)(StepParams, int, const double *, double *);
+typedef void (*year_kernel_t)(StepParams, m3d::SyncParams, double *, double *, int, int);
+
+year_kernel_t pick_year_kernel(int model, int ntr)
+{
+    if (model == m3d::kModelNdop) return ntr == 2 ? k_year<2, m3d::kModelNdop> : nullptr;
+    switch (ntr) {
+    case 1: return k_year<1, m3d::kModelNone>;
+    case 2: return k_year<2, m3d::kModelNone>;
+    case 3: return k_year<3, m3d::kModelNone>;
+    case 4: return k_year<4, m3d::kModelNone>;
+    case 5: return k_year<5, m3d::kModelNone>;
+    case 6: return k_year<6, m3d::kModelNone>;
+    case 7: return k_year<7, m3d::kModelNone>;
+    case 8: return k_year<8, m3d::kModelNone>;
+    default: return nullptr;
+    }
+}
 
 step_kernel_t pick_step_kernel(int model, int ntr)
 {
@@ -169,7 +202,13 @@ struct m3d_ctx {
     size_t smem_bytes = 0;
     std::vector<void *> allocs;
     StepParams P{};
+    m3d::SyncParams S{};
     step_kernel_t step_kernel = nullptr;
+    year_kernel_t year_kernel = nullptr;
+    int plan = 0;                       // 0: persistent year kernel, 1: graph of step launches
+    int persistent_ok = 0;              // all tiles fit on the GPU at once
+    int *status_host = nullptr;         // pinned copy of S.status
+    double *qpar = nullptr;
     double *u_dev = nullptr;
     double *ybuf[2] = {nullptr, nullptr};
     double *atten = nullptr, *mfrac = nullptr;
@@ -230,6 +269,7 @@ void release(m3d_ctx *c)
     if (c->year_graph) cudaGraphExecDestroy(c->year_graph);
     for (void *p : c->allocs) cudaFree(p);
     if (c->red_host) cudaFreeHost(c->red_host);
+    if (c->status_host) cudaFreeHost(c->status_host);
     c->allocs.clear();
 }
 
@@ -375,7 +415,8 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     c->nmonth = mt->nmonth;
     c->model = md->model_id;
     c->step_kernel = pick_step_kernel(c->model, c->ntr);
-    if (!c->step_kernel) {
+    c->year_kernel = pick_year_kernel(c->model, c->ntr);
+    if (!c->step_kernel || !c->year_kernel) {
         fail(c, M3D_ERR_UNSUPPORTED, "no step kernel for model %d with %d tracers", c->model, c->ntr);
         return bail(M3D_ERR_UNSUPPORTED);
     }
@@ -394,6 +435,7 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     std::vector<Tile> tiles(ntiles);
     std::vector<int> sp_len, sp_off, sp_row, sp_col;
     std::vector<int> bk_len, bk_off, bk_row, bk_cb, bk_L;
+    std::vector<int> eu_list, ap_list;
     int sp_slots = 0, bk_slots = 0, zmax = 0;
     // first pass: the slice structure; values are filled per month afterwards
     struct SliceRef { int tile_cell0; std::vector<int> rows; };
@@ -453,8 +495,52 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
             bk_slots += len;
         }
         T.bk1 = (int)bk_len.size();
+        // source-term work lists: euphotic cells of deep columns and the first cell of each
+        // shallow column (which then runs whole on one thread); aphotic cells
+        T.eu0 = (int)eu_list.size();
+        T.ap0 = (int)ap_list.size();
+        for (int cc = c0; cc < c1; cc++) {
+            int L = g->col_start[cc + 1] - g->col_start[cc];
+            int base = g->col_start[cc] - cell0;
+            if (L <= m3d::kEuphotic) {
+                eu_list.push_back(base);
+            } else {
+                for (int k = 0; k < m3d::kEuphotic; k++) eu_list.push_back(base + k);
+            }
+        }
+        for (int cc = c0; cc < c1; cc++) {
+            int L = g->col_start[cc + 1] - g->col_start[cc];
+            int base = g->col_start[cc] - cell0;
+            for (int k = m3d::kEuphotic; k < L; k++) ap_list.push_back(base + k);
+        }
+        T.eu1 = (int)eu_list.size();
+        T.ap1 = (int)ap_list.size();
     }
     c->zmax = zmax;
+
+    // neighbour tiles: those this tile reads from and those that read from it
+    std::vector<int> cell_tile(g->n);
+    for (int t = 0; t < ntiles; t++)
+        for (int i = tiles[t].cell0; i < tiles[t].cell0 + tiles[t].ncell; i++) cell_tile[i] = t;
+    std::vector<std::vector<int>> nbr(ntiles);
+    for (int t = 0; t < ntiles; t++)
+        for (int r = tiles[t].cell0; r < tiles[t].cell0 + tiles[t].ncell; r++)
+            for (int p = rp[r]; p < rp[r + 1]; p++) {
+                int o = cell_tile[ci[p]];
+                if (o != t) { nbr[t].push_back(o); nbr[o].push_back(t); }
+            }
+    std::vector<int> dep_off(ntiles + 1, 0), dep_idx;
+    for (int t = 0; t < ntiles; t++) {
+        std::sort(nbr[t].begin(), nbr[t].end());
+        nbr[t].erase(std::unique(nbr[t].begin(), nbr[t].end()), nbr[t].end());
+        dep_idx.insert(dep_idx.end(), nbr[t].begin(), nbr[t].end());
+        dep_off[t + 1] = (int)dep_idx.size();
+    }
+
+    // month and weight of every step (the weight needs a division: do it once here)
+    std::vector<int> m0tab(c->nstep);
+    std::vector<double> wtab(c->nstep);
+    for (int j = 0; j < c->nstep; j++) m3d::month_weights(j, c->nstep, c->nmonth, m0tab[j], wtab[j]);
 
     // column block offsets and per-cell tables
     std::vector<long long> blk_off(g->ncol + 1, 0);
@@ -529,6 +615,7 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     P.zmax = c->zmax;
     P.sp_mstride = spn;
     P.bk_mstride = bkn;
+    P.ds = (1.0 / c->nstep) / c->nsub;
     cudaError_t e = cudaSuccess;
 #define UP(...) do { e = (__VA_ARGS__); if (e != cudaSuccess) { fail(c, M3D_ERR_CUDA, "device upload: %s", cudaGetErrorString(e)); return bail(M3D_ERR_CUDA); } } while (0)
     UP(upload_vec(c, &P.tiles, tiles));
@@ -545,6 +632,27 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     UP(upload_vec(c, &P.bk_L, bk_L));
     UP(upload_vec(c, &P.bk_b, bk_b));
     UP(upload_vec(c, &P.bk_d, bk_d));
+    UP(upload_vec(c, &P.m0tab, m0tab));
+    UP(upload_vec(c, &P.wtab, wtab));
+    UP(upload_vec(c, &P.eu_list, eu_list));
+    UP(upload_vec(c, &P.ap_list, ap_list));
+    {
+        const int *p_off = nullptr, *p_idx = nullptr;
+        UP(upload_vec(c, &p_off, dep_off));
+        UP(upload_vec(c, &p_idx, dep_idx));
+        c->S.dep_off = p_off;
+        c->S.dep_idx = p_idx;
+        UP(upload(c, &c->S.flags, (const int *)nullptr, (size_t)ntiles));
+        UP(upload(c, &c->S.status, (const int *)nullptr, (size_t)4));
+        UP(cudaMemset(c->S.status, 0, 4 * sizeof(int)));
+        UP(cudaMallocHost((void **)&c->status_host, 4 * sizeof(int)));
+        memset(c->status_host, 0, 4 * sizeof(int));
+        c->S.timeout_ns = 2000000000ULL;      // 2 s; one step takes microseconds
+        c->S.withhold_tile = -1;
+    }
+    UP(upload(c, &c->qpar, (const double *)nullptr, (size_t)m3d::kQCount));
+    UP(cudaMemset(c->qpar, 0, sizeof(double) * m3d::kQCount));
+    P.qpar = c->qpar;
     UP(upload_vec(c, &P.cell_kl, cell_kl));
     UP(upload_vec(c, &P.cell_ulat, cell_ulat));
     c->cell_kl = const_cast<int *>(P.cell_kl);
@@ -557,7 +665,6 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     P.atten = c->atten;
     P.mfrac = c->mfrac;
     UP(upload(c, &c->u_dev, (const double *)nullptr, (size_t)std::max(1, c->nparam)));
-    P.u = c->u_dev;
     UP(upload(c, &c->ybuf[0], (const double *)nullptr, (size_t)c->ntr * c->n));
     UP(upload(c, &c->ybuf[1], (const double *)nullptr, (size_t)c->ntr * c->n));
     UP(upload(c, &c->red_part, (const double *)nullptr, (size_t)kRedBlocks));
@@ -581,6 +688,17 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     if (c->smem_bytes > 48 * 1024) {
         UP(cudaFuncSetAttribute((const void *)c->step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)c->smem_bytes));
+        UP(cudaFuncSetAttribute((const void *)c->year_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)c->smem_bytes));
+    }
+    {
+        // the persistent year kernel needs every tile resident at once
+        int per_sm = 0, coop = 0;
+        UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)c->year_kernel, m3d::kThreads,
+                                                         c->smem_bytes));
+        UP(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+        c->persistent_ok = coop && (long long)per_sm * prop.multiProcessorCount >= ntiles;
+        c->plan = c->persistent_ok ? 0 : 1;
     }
 #undef UP
     *out = c;
@@ -595,7 +713,7 @@ m3d_status launch_prologue(m3d_ctx *c, const double *u)
 {
     if (c->model != M3D_MODEL_NDOP) return M3D_OK;
     k_ndop_prologue<<<(c->n + 255) / 256, 256, 0, c->stream>>>(c->n, c->cell_kl, c->h, c->zc, u,
-                                                               c->atten, c->mfrac);
+                                                               c->atten, c->mfrac, c->qpar);
     CUDA_OR_FAIL(c, cudaGetLastError());
     return M3D_OK;
 }
@@ -604,6 +722,21 @@ m3d_status launch_step(m3d_ctx *c, int j, const double *y, double *yn)
 {
     c->step_kernel<<<c->ntiles, m3d::kThreads, c->smem_bytes, c->stream>>>(c->P, j, y, yn);
     CUDA_OR_FAIL(c, cudaGetLastError());
+    return M3D_OK;
+}
+
+// One cooperative launch for nsteps steps from step j0: y in buf[0], result in buf[nsteps & 1].
+m3d_status launch_year_persistent(m3d_ctx *c, int j0, int nsteps)
+{
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.flags, 0, sizeof(int) * c->ntiles, c->stream));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.status, 0, sizeof(int) * 4, c->stream));
+    StepParams P = c->P;
+    m3d::SyncParams S = c->S;
+    double *b0 = c->ybuf[0], *b1 = c->ybuf[1];
+    void *args[] = {&P, &S, &b0, &b1, &j0, &nsteps};
+    CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)c->year_kernel, dim3(c->ntiles), dim3(m3d::kThreads),
+                                                args, c->smem_bytes, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
     return M3D_OK;
 }
 
@@ -635,6 +768,25 @@ m3d_status build_year_graph(m3d_ctx *c)
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(c, M3D_ERR_CUDA, "year graph instantiate: %s", cudaGetErrorString(e));
     c->year_result_buf = c->nstep & 1;
+    return M3D_OK;
+}
+
+// Run the year from ybuf[0] (u already in u_dev) and copy the result to `out`.
+m3d_status run_year_from_ybuf(m3d_ctx *c, double *out, cudaMemcpyKind kind)
+{
+    size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    if (c->plan == 0) {
+        m3d_status st = launch_prologue(c, c->u_dev);
+        if (st != M3D_OK) return st;
+        st = launch_year_persistent(c, 0, c->nstep);
+        if (st != M3D_OK) return st;
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(out, c->ybuf[c->nstep & 1], len, kind, c->stream));
+        c->last_launches = (c->model == M3D_MODEL_NDOP ? 1 : 0) + 1;
+    } else {
+        CUDA_OR_FAIL(c, cudaGraphLaunch(c->year_graph, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(out, c->ybuf[c->year_result_buf], len, kind, c->stream));
+        c->last_launches = (c->model == M3D_MODEL_NDOP ? 1 : 0) + c->nstep;
+    }
     return M3D_OK;
 }
 
@@ -674,18 +826,15 @@ m3d_status metos3d_year_map(m3d_ctx *c, const double *y0, double *y1, const doub
 {
     if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_map: null context");
     if (!y0 || !y1 || (c->nparam > 0 && !u)) return fail(c, M3D_ERR_ARG, "metos3d_year_map: null pointer");
-    if (!c->year_graph) {
+    size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    if (c->plan == 1 && !c->year_graph) {
         m3d_status st = build_year_graph(c);
         if (st != M3D_OK) return st;
     }
-    size_t len = sizeof(double) * (size_t)c->ntr * c->n;
     if (c->nparam > 0)
         CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_dev, u, sizeof(double) * c->nparam, cudaMemcpyDeviceToDevice, c->stream));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], y0, len, cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_OR_FAIL(c, cudaGraphLaunch(c->year_graph, c->stream));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(y1, c->ybuf[c->year_result_buf], len, cudaMemcpyDeviceToDevice, c->stream));
-    c->last_launches = (c->model == M3D_MODEL_NDOP ? 1 : 0) + c->nstep;
-    return M3D_OK;
+    return run_year_from_ybuf(c, y1, cudaMemcpyDeviceToDevice);
 }
 
 m3d_status metos3d_year_map_host(m3d_ctx *c, const double *y0_host, double *y1_host, const double *u_host)
@@ -693,19 +842,64 @@ m3d_status metos3d_year_map_host(m3d_ctx *c, const double *y0_host, double *y1_h
     if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_map_host: null context");
     if (!y0_host || !y1_host || (c->nparam > 0 && !u_host))
         return fail(c, M3D_ERR_ARG, "metos3d_year_map_host: null pointer");
-    if (!c->year_graph) {
+    size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    if (c->plan == 1 && !c->year_graph) {
         m3d_status st = build_year_graph(c);
         if (st != M3D_OK) return st;
     }
-    size_t len = sizeof(double) * (size_t)c->ntr * c->n;
     if (c->nparam > 0)
         CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_dev, u_host, sizeof(double) * c->nparam, cudaMemcpyHostToDevice, c->stream));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], y0_host, len, cudaMemcpyHostToDevice, c->stream));
-    CUDA_OR_FAIL(c, cudaGraphLaunch(c->year_graph, c->stream));
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(y1_host, c->ybuf[c->year_result_buf], len, cudaMemcpyDeviceToHost, c->stream));
+    m3d_status st = run_year_from_ybuf(c, y1_host, cudaMemcpyDeviceToHost);
+    if (st != M3D_OK) return st;
+    return metos3d_sync(c);
+}
+
+m3d_status metos3d_sync(m3d_ctx *c)
+{
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_sync: null context");
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
-    c->last_launches = (c->model == M3D_MODEL_NDOP ? 1 : 0) + c->nstep;
+    if (c->status_host[0] != 0) {
+        int tile = c->status_host[1], step = c->status_host[2];
+        c->status_host[0] = 0;
+        return fail(c, M3D_ERR_TIMEOUT, "year map: tile %d gave up waiting for its neighbours at step %d", tile, step);
+    }
     return M3D_OK;
+}
+
+m3d_status metos3d_set_option(m3d_ctx *c, int option, long long value)
+{
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_set_option: null context");
+    switch (option) {
+    case M3D_OPT_YEAR_PLAN:
+        if (value == M3D_PLAN_PERSISTENT && !c->persistent_ok)
+            return fail(c, M3D_ERR_UNSUPPORTED, "the persistent year kernel does not fit on this GPU");
+        if (value != M3D_PLAN_PERSISTENT && value != M3D_PLAN_GRAPH) return fail(c, M3D_ERR_ARG, "bad plan");
+        c->plan = (int)value;
+        return M3D_OK;
+    case M3D_OPT_WAIT_TIMEOUT_NS:
+        if (value <= 0) return fail(c, M3D_ERR_ARG, "timeout must be positive");
+        c->S.timeout_ns = (unsigned long long)value;
+        return M3D_OK;
+    case M3D_OPT_TEST_WITHHOLD_TILE:
+        if (value < -1 || value >= c->ntiles) return fail(c, M3D_ERR_ARG, "tile out of range");
+        c->S.withhold_tile = (int)value;
+        return M3D_OK;
+    default:
+        return fail(c, M3D_ERR_ARG, "unknown option %d", option);
+    }
+}
+
+long long metos3d_get_option(const m3d_ctx *c, int option)
+{
+    if (!c) return -1;
+    switch (option) {
+    case M3D_OPT_YEAR_PLAN: return c->plan;
+    case M3D_OPT_WAIT_TIMEOUT_NS: return (long long)c->S.timeout_ns;
+    case M3D_OPT_TEST_WITHHOLD_TILE: return c->S.withhold_tile;
+    case M3D_OPT_NTILES: return c->ntiles;
+    default: return -1;
+    }
 }
 
 m3d_status metos3d_mass(m3d_ctx *c, const double *y, double *mass)

@@ -1,12 +1,14 @@
 // tmm_kernels.cuh -- device code of the TMM step (Metos3D, arXiv:1410.0204, Section 3):
 //     y_{j+1} = A_imp(t_j) ( A_exp(t_j) y_j + q_j(y_j, u) ),
-// fused into one pass per tile of water columns.  FP64 throughout.
+// fused into one pass per tile of water columns, and the year map of Section 4 as one
+// persistent launch.  FP64 throughout.
 //
-// GB300 facts that shape this code: the FP64 pipe retires about one warp-wide DFMA every
-// 16 clocks per SM (measured 1.2 TFLOP/s for the whole GPU, 64x below FP32), and a warp
-// instruction costs the same whether 1 or 32 lanes are active.  So the year map is bound
-// by FP64 instruction issue, not by HBM: every FP64 instruction here is laid out so that
-// all 32 lanes do useful work, and transcendentals are hoisted out of the step into
+// GB300 facts that shape this code: the FP64 pipe retires one warp-wide DFMA every 16
+// clocks per SM (2 lanes per clock; measured 1.2 TFLOP/s for the GPU, 64x below FP32), and
+// a warp instruction costs the same whether 1 or 32 lanes are active.  The year map is
+// therefore bound by FP64 instruction issue, not by HBM.  Every FP64 instruction here is
+// laid out so that all 32 lanes do useful work; scalars that need a division (the month
+// weight, the internal step length) come precomputed; transcendentals are hoisted into
 // per-init (insolation) and per-call (light attenuation, Martin profile) tables.
 #pragma once
 
@@ -21,17 +23,25 @@ constexpr int kModelNdop = 2;
 constexpr double kSigmaPar = 0.4;    // photosynthetically available fraction of I_SWR
 constexpr int kEuphotic = 2;         // euphotic layers (Section 7: two)
 
+// Scalars of the PO4-DOP model computed once per call from u (prologue kernel).
+enum { kQAlpha = 0, kQSigma, kQLambda, kQKN, kQKI, kQOneMinusSigma, kQCount = 8 };
+
 // One tile: a contiguous range of whole water columns, processed by one CTA.
 struct Tile {
     int cell0, ncell;                // cells [cell0, cell0 + ncell)
     int sp0, sp1;                    // explicit-matrix warp slices [sp0, sp1)
     int bk0, bk1;                    // implicit-block warp slices [bk0, bk1)
+    int eu0, eu1;                    // entries of eu_list: euphotic cells / shallow columns
+    int ap0, ap1;                    // entries of ap_list: aphotic cells
     int pad0, pad1;
 };
 
 // Everything one step reads, as device pointers owned by the context.
 struct StepParams {
     int n, nstep, nmonth, nsub, nulat, zmax;
+    double ds;                             // internal model step, (1/nstep)/nsub
+    const int *m0tab;                      // [nstep] first month of step j
+    const double *wtab;                    // [nstep] interpolation weight of step j
     const Tile *tiles;
     // explicit matrices in warp-slice layout: slice s covers 32 rows (one per lane) and
     // sp_len[s] slots; element (slot q, lane l) of slice s sits at (sp_off[s] + q) * 32 + l.
@@ -46,19 +56,21 @@ struct StepParams {
     const double *bk_b, *bk_d;             // [nmonth][...]: B_m and B_{m+1} - B_m
     long long bk_mstride;
     // biogeochemistry
+    const int *eu_list, *ap_list;          // tile-local cells, grouped per tile
     const int *cell_kl;                    // layer k | (column layers L << 8)
     const int *cell_ulat;                  // index of the cell's latitude in the insolation table
     const double *h;                       // [n] layer thickness
     const double *atten;                   // [n] sigma_PAR exp(-k_w d) (euphotic cells; per call)
     const double *mfrac;                   // [n] Martin deposition profile (aphotic cells; per call)
     const double *I0tab;                   // [nstep][nulat] daily-mean I_SWR at t_j
-    const double *u;                       // [nparam] model parameters
+    const double *qpar;                    // [kQCount] model scalars (per call)
 };
 
 // Month weights (Section 3): month m is centred at t = (m + 1/2)/nmonth; t_j = j/nstep.
 // s = nmonth t_j - 1/2 = num/den with num = 2 nmonth j - nstep, den = 2 nstep;
 // m0 = floor(s) mod nmonth, w = s - floor(s) in [0, 1); the operator is M_m0 + w (M_m1 - M_m0).
-__device__ __forceinline__ void month_weights(int j, int nstep, int nmonth, int &m0, double &w)
+// Evaluated once per step at set-up into m0tab/wtab.
+__host__ __device__ inline void month_weights(int j, int nstep, int nmonth, int &m0, double &w)
 {
     long long num = 2LL * nmonth * j - nstep;
     long long den = 2LL * nstep;
@@ -86,12 +98,21 @@ __device__ __forceinline__ double insolation(double lat_deg, double t)
 
 // PO4-DOP euphotic cell over nsub internal steps (Section 2.2.1), light I fixed:
 //   f = alpha N/(N+K_N) I/(I+K_I),  dN = -f + lambda DOP,  dDOP = sigma f - lambda DOP.
-// Returns the increments and the production summed over the internal steps.
+// Returns the increments and the production summed over the internal steps.  With one
+// internal step the two Michaelis-Menten quotients share one division.
 __device__ __forceinline__ void ndop_euphotic(double N, double D, double I, double alpha,
                                               double sigma, double lambda, double KN, double KI,
                                               double ds, int nsub, double &dN, double &dD,
                                               double &fsum)
 {
+    if (nsub == 1) {
+        double f = (alpha * N * I) / ((N + KN) * (I + KI));
+        double lD = lambda * D;
+        dN = ds * (lD - f);
+        dD = ds * (sigma * f - lD);
+        fsum = f;
+        return;
+    }
     double aLF = alpha * (I / (I + KI));
     double N0 = N, D0 = D;
     fsum = 0.0;
@@ -107,10 +128,16 @@ __device__ __forceinline__ void ndop_euphotic(double N, double D, double I, doub
 }
 
 // Aphotic PO4-DOP cell: DOP remineralises at lambda; the sinking flux deposits
-// Esum * mfrac per unit of production-time (Esum = sum over internal steps of the export).
+// Esum * mfrac, Esum being the export summed over the internal steps.
 __device__ __forceinline__ void ndop_aphotic(double D, double Esum, double mfrac, double lambda,
                                              double ds, int nsub, double &dN, double &dD)
 {
+    if (nsub == 1) {
+        double lD = lambda * D;
+        dN = ds * (lD + mfrac * Esum);
+        dD = ds * (-lD);
+        return;
+    }
     double D0 = D, Dsum = 0.0;
     for (int s = 0; s < nsub; s++) {
         Dsum += D;
@@ -136,11 +163,10 @@ __device__ __forceinline__ double martin_fraction(const double *hcol, int k, int
 
 // A whole shallow column (L <= number of euphotic layers) on one thread, with the export
 // kept in its bottom layer inside every internal step.
-__device__ __forceinline__ void ndop_shallow_column(int L, const double *hcol, const double *N0,
-                                                    const double *D0, const double *I, double alpha,
-                                                    double sigma, double lambda, double KN,
-                                                    double KI, double ds, int nsub, double *dN,
-                                                    double *dD)
+__device__ __noinline__ void ndop_shallow_column(int L, const double *hcol, const double *N0,
+                                                 const double *D0, const double *I, double alpha,
+                                                 double sigma, double lambda, double KN, double KI,
+                                                 double ds, int nsub, double *dN, double *dD)
 {
     double N[kEuphotic], D[kEuphotic];
     for (int k = 0; k < L; k++) { N[k] = N0[k]; D[k] = D0[k]; }
@@ -184,9 +210,8 @@ __device__ __forceinline__ void step_tile(const StepParams &P, int tile, int j,
     double *z = smem;                 // [NTR][zmax] A_exp y + dq, tile-local cells
     double *ek = smem + NTR * zmax;   // [zmax] export contributions of euphotic cells
 
-    int m0;
-    double w;
-    month_weights(j, P.nstep, P.nmonth, m0, w);
+    const int m0 = __ldg(P.m0tab + j);
+    const double w = __ldg(P.wtab + j);
 
     // ---- explicit part: z = (A_m0 + w (A_m1 - A_m0)) y, all tracers per matrix read
     {
@@ -218,54 +243,53 @@ __device__ __forceinline__ void step_tile(const StepParams &P, int tile, int j,
 
     // ---- source-minus-sink term q on y_j (Section 2.2.1), added as its increment
     if (MODEL == kModelNdop) {
-        const double alpha = __ldg(P.u + 1) * 360.0, sigma = __ldg(P.u + 2);
-        const double lambda = __ldg(P.u + 3), KN = __ldg(P.u + 4), KI = __ldg(P.u + 5);
+        const double alpha = __ldg(P.qpar + kQAlpha), sigma = __ldg(P.qpar + kQSigma);
+        const double lambda = __ldg(P.qpar + kQLambda), KN = __ldg(P.qpar + kQKN);
+        const double KI = __ldg(P.qpar + kQKI), oms = __ldg(P.qpar + kQOneMinusSigma);
         const int nsub = P.nsub;
-        const double ds = (1.0 / P.nstep) / nsub;
+        const double ds = P.ds;
         const double *I0row = P.I0tab + (size_t)j * P.nulat;
-        for (int i = threadIdx.x; i < T.ncell; i += blockDim.x) {
+        // euphotic cells of deep columns, and whole shallow columns
+        for (int e = T.eu0 + (int)threadIdx.x; e < T.eu1; e += blockDim.x) {
+            const int i = __ldg(P.eu_list + e);
             const int cell = T.cell0 + i;
             const int kl = __ldg(P.cell_kl + cell);
-            const int k = kl & 0xff, L = kl >> 8;
+            const int L = kl >> 8;
+            const double I0 = __ldg(I0row + __ldg(P.cell_ulat + cell));
             if (L <= kEuphotic) {
-                if (k == 0) {
-                    double N0[kEuphotic], D0[kEuphotic], I[kEuphotic], dN[kEuphotic], dD[kEuphotic];
-                    const double I0 = __ldg(I0row + __ldg(P.cell_ulat + cell));
-                    for (int kk = 0; kk < L; kk++) {
-                        N0[kk] = load_state<COHERENT>(y + cell + kk);
-                        D0[kk] = load_state<COHERENT>(y + n + cell + kk);
-                        I[kk] = I0 * __ldg(P.atten + cell + kk);
-                    }
-                    ndop_shallow_column(L, P.h + cell, N0, D0, I, alpha, sigma, lambda, KN, KI,
-                                        ds, nsub, dN, dD);
-                    for (int kk = 0; kk < L; kk++) {
-                        z[i + kk] += dN[kk];
-                        z[zmax + i + kk] += dD[kk];
-                    }
+                double N0[kEuphotic], D0[kEuphotic], I[kEuphotic], dN[kEuphotic], dD[kEuphotic];
+                for (int kk = 0; kk < L; kk++) {
+                    N0[kk] = load_state<COHERENT>(y + cell + kk);
+                    D0[kk] = load_state<COHERENT>(y + n + cell + kk);
+                    I[kk] = I0 * __ldg(P.atten + cell + kk);
                 }
-            } else if (k < kEuphotic) {
-                const double I = __ldg(I0row + __ldg(P.cell_ulat + cell)) * __ldg(P.atten + cell);
+                ndop_shallow_column(L, P.h + cell, N0, D0, I, alpha, sigma, lambda, KN, KI, ds,
+                                    nsub, dN, dD);
+                for (int kk = 0; kk < L; kk++) {
+                    z[i + kk] += dN[kk];
+                    z[zmax + i + kk] += dD[kk];
+                }
+            } else {
                 double dN, dD, fsum;
-                ndop_euphotic(load_state<COHERENT>(y + cell), load_state<COHERENT>(y + n + cell), I,
-                              alpha, sigma, lambda, KN, KI, ds, nsub, dN, dD, fsum);
+                ndop_euphotic(load_state<COHERENT>(y + cell), load_state<COHERENT>(y + n + cell),
+                              I0 * __ldg(P.atten + cell), alpha, sigma, lambda, KN, KI, ds, nsub,
+                              dN, dD, fsum);
                 z[i] += dN;
                 z[zmax + i] += dD;
-                ek[i] = (1.0 - sigma) * fsum * __ldg(P.h + cell);
+                ek[i] = oms * fsum * __ldg(P.h + cell);
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < T.ncell; i += blockDim.x) {
+        for (int a = T.ap0 + (int)threadIdx.x; a < T.ap1; a += blockDim.x) {
+            const int i = __ldg(P.ap_list + a);
             const int cell = T.cell0 + i;
-            const int kl = __ldg(P.cell_kl + cell);
-            const int k = kl & 0xff, L = kl >> 8;
-            if (L > kEuphotic && k >= kEuphotic) {
-                const double Esum = ek[i - k] + ek[i - k + 1];
-                double dN, dD;
-                ndop_aphotic(load_state<COHERENT>(y + n + cell), Esum, __ldg(P.mfrac + cell), lambda,
-                             ds, nsub, dN, dD);
-                z[i] += dN;
-                z[zmax + i] += dD;
-            }
+            const int k = __ldg(P.cell_kl + cell) & 0xff;
+            const double Esum = ek[i - k] + ek[i - k + 1];
+            double dN, dD;
+            ndop_aphotic(load_state<COHERENT>(y + n + cell), Esum, __ldg(P.mfrac + cell), lambda, ds,
+                         nsub, dN, dD);
+            z[i] += dN;
+            z[zmax + i] += dD;
         }
         __syncthreads();
     }
@@ -295,6 +319,98 @@ __device__ __forceinline__ void step_tile(const StepParams &P, int tile, int j,
 #pragma unroll
                 for (int t = 0; t < NTR; t++) yn[(size_t)t * n + T.cell0 + row] = acc[t];
             }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Persistent year map: one cooperative launch, one CTA per tile, all tiles co-resident.
+// Before step s a tile waits until every tile it reads from, or that reads from it, has
+// finished step s-1 (per-tile counters, release/acquire at GPU scope).  That makes y_s
+// complete where this tile reads it, and makes the buffer it overwrites (y_{s-1}) no longer
+// read by anyone.  Every wait is bounded: after timeout_ns the tile records the failure in
+// status[] and returns, and the others stop at their next wait.
+
+struct SyncParams {
+    int *flags;                 // [ntiles] steps completed (0 at launch)
+    const int *dep_off;         // [ntiles+1]
+    const int *dep_idx;         // neighbour tiles
+    int *status;                // [4]: 0 ok / 1 timeout; tile; step; unused
+    unsigned long long timeout_ns;
+    int withhold_tile;          // test hook: this tile never publishes its counter (-1: none)
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int load_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void store_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Warp 0 waits for the neighbours of `tile` to reach `target`; returns false on abort.
+__device__ __forceinline__ bool wait_neighbours(const SyncParams &S, int tile, int target, int step)
+{
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    const int d0 = __ldg(S.dep_off + tile), d1 = __ldg(S.dep_off + tile + 1);
+    for (int d = d0 + lane; d < d1 && ok; d += 32) {
+        const int nb = __ldg(S.dep_idx + d);
+        if (load_acquire(S.flags + nb) >= target) continue;
+        const unsigned long long t0 = global_ns();
+        while (true) {
+            if (load_acquire(S.flags + nb) >= target) break;
+            if (*(volatile int *)S.status != 0) { ok = false; break; }
+            if (global_ns() - t0 > S.timeout_ns) {
+                if (atomicCAS(S.status, 0, 1) == 0) {
+                    S.status[1] = tile;
+                    S.status[2] = step;
+                }
+                ok = false;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+template <int NTR, int MODEL>
+__device__ __forceinline__ void year_persistent(const StepParams &P, const SyncParams &S,
+                                                double *buf0, double *buf1, int j0, int nsteps,
+                                                double *smem)
+{
+    __shared__ int abort_flag;
+    const int tile = blockIdx.x;
+    for (int s = 0; s < nsteps; s++) {
+        const int j = (j0 + s) % P.nstep;
+        const double *y = (s & 1) ? buf1 : buf0;
+        double *yn = (s & 1) ? buf0 : buf1;
+        if (s > 0) {
+            if (threadIdx.x < 32) {
+                bool ok = wait_neighbours(S, tile, s, s);
+                __threadfence();
+                if (threadIdx.x == 0) abort_flag = ok ? 0 : 1;
+            }
+            __syncthreads();
+            if (abort_flag) return;
+        }
+        step_tile<NTR, MODEL, true>(P, tile, j, y, yn, smem);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (tile != S.withhold_tile) store_release(S.flags + tile, s + 1);
         }
     }
 }

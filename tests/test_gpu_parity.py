@@ -100,20 +100,24 @@ def test_step_transport_only_many_tracers(m3d):
 
 
 # ------------------------------------------------------------------ year maps
+@pytest.mark.parametrize("plan", ["persistent", "graph"])
 @pytest.mark.parametrize("name,nsub", [("tiny_4x3x3", 1), ("tiny_6x4x4", 8), ("ndop_64x32x8", 1)])
-def test_year_map_matches_oracle(m3d, name, nsub):
+def test_year_map_matches_oracle(m3d, name, nsub, plan):
     p, P = problem(name)
     u = mi.default_params_ndop()
     ctx = ctx_for(m3d, p, nsub=nsub)
+    if plan == "graph":
+        ctx.set_option(m3d.OPT_YEAR_PLAN, m3d.PLAN_GRAPH)
+    assert ctx.get_option(m3d.OPT_YEAR_PLAN) == (m3d.PLAN_GRAPH if plan == "graph" else m3d.PLAN_PERSISTENT)
     y0 = mi.initial_state(p)
     yd, ud = cuda(y0), cuda(u)
     y1 = torch.empty_like(yd)
     ctx.year_map(yd, y1, ud)
-    torch.cuda.synchronize()
+    ctx.sync()
     got = y1.cpu().numpy()
     want = oracle.year_map(P, y0, u, nsub=nsub)
     assert rel_err(got, want) < YEAR_TOL
-    assert ctx.last_launch_count() == 2881
+    assert ctx.last_launch_count() == (2881 if plan == "graph" else 2)
     # mass is conserved on the device too (Section 3 matrices conserve V^T y; q is column-conservative)
     m0 = math.fsum((p.vol * y0).ravel())
     assert abs(ctx.mass(y1) - m0) / m0 < 1e-12
@@ -136,6 +140,47 @@ def test_year_map_paper_grid_matches_oracle(m3d):
     finally:
         oracle.set_threads(1)
     assert rel_err(y1.cpu().numpy(), want) < YEAR_TOL
+    ctx.close()
+
+
+def test_persistent_and_graph_plans_agree_bitwise(m3d):
+    """Both plans run the same per-tile step in the same order: identical results."""
+    p, _ = problem("ndop_64x32x8")
+    u = cuda(mi.default_params_ndop())
+    y0 = cuda(mi.random_state(p))
+    a = torch.empty_like(y0)
+    b = torch.empty_like(y0)
+    ctx = ctx_for(m3d, p)
+    ctx.year_map(y0, a, u)
+    ctx.set_option(m3d.OPT_YEAR_PLAN, m3d.PLAN_GRAPH)
+    ctx.year_map(y0, b, u)
+    ctx.sync()
+    assert torch.equal(a, b)
+    ctx.close()
+
+
+def test_persistent_wait_timeout_is_reported_and_recoverable(m3d):
+    """A tile that never announces its progress makes its neighbours' bounded waits run out:
+    the kernel stops, metos3d_sync reports M3D_ERR_TIMEOUT, and the context stays usable."""
+    p, P = problem("ndop_64x32x8")
+    u_h = mi.default_params_ndop()
+    u = cuda(u_h)
+    y0_h = mi.initial_state(p)
+    y0 = cuda(y0_h)
+    y1 = torch.empty_like(y0)
+    ctx = ctx_for(m3d, p)
+    assert ctx.get_option(m3d.OPT_NTILES) > 1
+    ctx.set_option(m3d.OPT_WAIT_TIMEOUT_NS, 50_000_000)      # 50 ms
+    ctx.set_option(m3d.OPT_TEST_WITHHOLD_TILE, 0)
+    ctx.year_map(y0, y1, u)
+    with pytest.raises(m3d.Metos3dError) as e:
+        ctx.sync()
+    assert e.value.status == m3d.M3D_ERR_TIMEOUT
+    ctx.set_option(m3d.OPT_TEST_WITHHOLD_TILE, -1)
+    ctx.set_option(m3d.OPT_WAIT_TIMEOUT_NS, 2_000_000_000)
+    ctx.year_map(y0, y1, u)
+    ctx.sync()
+    assert rel_err(y1.cpu().numpy(), oracle.year_map(P, y0_h, u_h)) < YEAR_TOL
     ctx.close()
 
 
