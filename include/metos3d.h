@@ -194,10 +194,14 @@ m3d_status metos3d_sync(m3d_ctx *ctx);
 
 /*
  * Execution options (tuning and checks; the defaults need no setting):
- *   M3D_OPT_YEAR_PLAN: M3D_PLAN_PERSISTENT (default when all tiles fit on the GPU at once):
- *       the year map is one cooperative launch whose tiles synchronise with their
- *       neighbours through per-tile step counters; M3D_PLAN_GRAPH: one kernel launch per
- *       step, captured in a CUDA graph.
+ *   M3D_OPT_YEAR_PLAN:
+ *       M3D_PLAN_RESIDENT (default when it fits): the year map is one cooperative launch;
+ *       each tile of water columns keeps its month of matrices in shared memory, reloads
+ *       them when the month changes, and synchronises with its neighbouring tiles through
+ *       per-tile step counters;
+ *       M3D_PLAN_PERSISTENT: the same launch with the matrices read from global memory
+ *       every step (default when the matrices do not fit in shared memory);
+ *       M3D_PLAN_GRAPH: one kernel launch per step, captured in a CUDA graph.
  *   M3D_OPT_WAIT_TIMEOUT_NS: bound of every device-side wait of the persistent kernel
  *       (default 2 s).
  *   M3D_OPT_TEST_WITHHOLD_TILE: for tests of the timeout path only: the given tile never
@@ -211,7 +215,7 @@ enum {
     M3D_OPT_TEST_WITHHOLD_TILE = 3,
     M3D_OPT_NTILES = 4
 };
-enum { M3D_PLAN_PERSISTENT = 0, M3D_PLAN_GRAPH = 1 };
+enum { M3D_PLAN_PERSISTENT = 0, M3D_PLAN_GRAPH = 1, M3D_PLAN_RESIDENT = 2 };
 m3d_status metos3d_set_option(m3d_ctx *ctx, int option, long long value);
 long long metos3d_get_option(const m3d_ctx *ctx, int option);
 

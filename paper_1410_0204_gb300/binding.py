@@ -29,6 +29,7 @@ OPT_TEST_WITHHOLD_TILE = 3
 OPT_NTILES = 4
 PLAN_PERSISTENT = 0
 PLAN_GRAPH = 1
+PLAN_RESIDENT = 2
 
 MODEL_NONE = 0
 MODEL_NDOP = 2

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -15,6 +16,7 @@
 
 #include "metos3d.h"
 #include "tmm_kernels.cuh"
+#include "tmm_resident.cuh"
 
 using m3d::StepParams;
 using m3d::Tile;
@@ -23,7 +25,7 @@ using m3d::Tile;
 namespace {
 
 template <int NTR, int MODEL>
-__global__ void __launch_bounds__(m3d::kThreads) k_step(StepParams P, int j, const double *y,
+__global__ void __launch_bounds__(m3d::kThreads, 1) k_step(StepParams P, int j, const double *y,
                                                         double *yn)
 {
     extern __shared__ double smem[];
@@ -31,11 +33,19 @@ __global__ void __launch_bounds__(m3d::kThreads) k_step(StepParams P, int j, con
 }
 
 template <int NTR, int MODEL>
-__global__ void __launch_bounds__(m3d::kThreads) k_year(StepParams P, m3d::SyncParams S, double *buf0,
+__global__ void __launch_bounds__(m3d::kThreads, 1) k_year(StepParams P, m3d::SyncParams S, double *buf0,
                                                         double *buf1, int j0, int nsteps)
 {
     extern __shared__ double smem[];
     m3d::year_persistent<NTR, MODEL>(P, S, buf0, buf1, j0, nsteps, smem);
+}
+
+template <int NTR, int MODEL>
+__global__ void __launch_bounds__(m3d::kThreads, 1) k_year_resident(StepParams P, m3d::ResidentParams R,
+                                                                 m3d::SyncParams S, double *buf0, double *buf1,
+                                                                 int j0, int nsteps)
+{
+    m3d::year_resident<NTR, MODEL>(P, R, S, buf0, buf1, j0, nsteps);
 }
 
 // Per-call tables of the PO4-DOP model that depend on the parameters u:
@@ -173,6 +183,36 @@ year_kernel_t pick_year_kernel(int model, int ntr)
     }
 }
 
+typedef void (*resident_kernel_t)(StepParams, m3d::ResidentParams, m3d::SyncParams, double *, double *, int, int);
+typedef void (*layout_kernel_t)(int, const double *, double *);
+
+struct ResidentKernels {
+    resident_kernel_t year;
+    layout_kernel_t to_interleaved, from_interleaved;
+};
+
+template <int NTR, int MODEL>
+ResidentKernels resident_kernels()
+{
+    return {k_year_resident<NTR, MODEL>, m3d::k_interleave<NTR>, m3d::k_deinterleave<NTR>};
+}
+
+ResidentKernels pick_resident_kernels(int model, int ntr)
+{
+    if (model == m3d::kModelNdop) return ntr == 2 ? resident_kernels<2, m3d::kModelNdop>() : ResidentKernels{};
+    switch (ntr) {
+    case 1: return resident_kernels<1, m3d::kModelNone>();
+    case 2: return resident_kernels<2, m3d::kModelNone>();
+    case 3: return resident_kernels<3, m3d::kModelNone>();
+    case 4: return resident_kernels<4, m3d::kModelNone>();
+    case 5: return resident_kernels<5, m3d::kModelNone>();
+    case 6: return resident_kernels<6, m3d::kModelNone>();
+    case 7: return resident_kernels<7, m3d::kModelNone>();
+    case 8: return resident_kernels<8, m3d::kModelNone>();
+    default: return ResidentKernels{};
+    }
+}
+
 step_kernel_t pick_step_kernel(int model, int ntr)
 {
     if (model == m3d::kModelNdop) return ntr == 2 ? k_step<2, m3d::kModelNdop> : nullptr;
@@ -205,8 +245,12 @@ struct m3d_ctx {
     m3d::SyncParams S{};
     step_kernel_t step_kernel = nullptr;
     year_kernel_t year_kernel = nullptr;
-    int plan = 0;                       // 0: persistent year kernel, 1: graph of step launches
-    int persistent_ok = 0;              // all tiles fit on the GPU at once
+    int plan = 0;                       // M3D_PLAN_*
+    int persistent_ok = 0;              // all tiles fit on the GPU at once (streaming plan)
+    int resident_ok = 0;                // ... with their month of matrices in shared memory
+    m3d::ResidentParams R{};
+    ResidentKernels rk{};
+    size_t resident_smem = 0;
     int *status_host = nullptr;         // pinned copy of S.status
     double *qpar = nullptr;
     double *u_dev = nullptr;
@@ -287,7 +331,10 @@ std::vector<int> partition_columns(const m3d_grid *g, const int *rowptr, int ntr
     for (int c = 0; c < g->ncol; c++) {
         int s = g->col_start[c], e = g->col_start[c + 1], L = e - s;
         double nnz = rowptr[e] - rowptr[s];
-        work[c] = (1.0 + ntr) * (nnz + (double)L * L) + 8.0 * L;
+        // FP64 lane-operations: interpolation plus one FMA per tracer for every matrix entry,
+        // about 32 per euphotic cell (a division is about 10) and 6 per aphotic cell
+        int neu = std::min(L, 2);
+        work[c] = (1.0 + ntr) * (nnz + (double)L * L) + 32.0 * neu + 6.0 * (L - neu);
     }
     double total = std::accumulate(work.begin(), work.end(), 0.0);
     std::vector<int> bounds{0};
@@ -416,6 +463,7 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     c->model = md->model_id;
     c->step_kernel = pick_step_kernel(c->model, c->ntr);
     c->year_kernel = pick_year_kernel(c->model, c->ntr);
+    c->rk = pick_resident_kernels(c->model, c->ntr);
     if (!c->step_kernel || !c->year_kernel) {
         fail(c, M3D_ERR_UNSUPPORTED, "no step kernel for model %d with %d tracers", c->model, c->ntr);
         return bail(M3D_ERR_UNSUPPORTED);
@@ -427,7 +475,10 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     }
 
     // ---- tiles of whole columns
-    int ntarget = std::min(g->ncol, 2 * prop.multiProcessorCount);
+    // one tile (CTA of 16 warps) per SM by default; METOS3D_TILES_PER_SM overrides it for tuning
+    int tiles_per_sm = 1;
+    if (const char *env = getenv("METOS3D_TILES_PER_SM")) tiles_per_sm = std::max(1, std::min(8, atoi(env)));
+    int ntarget = std::min(g->ncol, tiles_per_sm * prop.multiProcessorCount);
     std::vector<int> bounds = partition_columns(g, rp, c->ntr, ntarget);
     int ntiles = (int)bounds.size() - 1;
     c->ntiles = ntiles;
@@ -435,7 +486,7 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     std::vector<Tile> tiles(ntiles);
     std::vector<int> sp_len, sp_off, sp_row, sp_col;
     std::vector<int> bk_len, bk_off, bk_row, bk_cb, bk_L;
-    std::vector<int> eu_list, ap_list;
+    std::vector<int> eu_list, ap_list, sh_list;
     int sp_slots = 0, bk_slots = 0, zmax = 0;
     // first pass: the slice structure; values are filled per month afterwards
     struct SliceRef { int tile_cell0; std::vector<int> rows; };
@@ -448,7 +499,6 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
         Tile &T = tiles[t];
         T.cell0 = cell0;
         T.ncell = nc;
-        T.pad0 = T.pad1 = 0;
         // explicit slices: rows by decreasing nonzero count
         std::vector<int> rows(nc);
         std::iota(rows.begin(), rows.end(), cell0);
@@ -499,13 +549,15 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
         // shallow column (which then runs whole on one thread); aphotic cells
         T.eu0 = (int)eu_list.size();
         T.ap0 = (int)ap_list.size();
+        T.sh0 = (int)sh_list.size();
         for (int cc = c0; cc < c1; cc++) {
             int L = g->col_start[cc + 1] - g->col_start[cc];
             int base = g->col_start[cc] - cell0;
-            if (L <= m3d::kEuphotic) {
-                eu_list.push_back(base);
+            if (L <= m3d::kEuphotic && md->nsub > 1) {
+                eu_list.push_back(base);                 // the whole column on one thread
             } else {
-                for (int k = 0; k < m3d::kEuphotic; k++) eu_list.push_back(base + k);
+                for (int k = 0; k < std::min(L, m3d::kEuphotic); k++) eu_list.push_back(base + k);
+                if (L <= m3d::kEuphotic) sh_list.push_back(base + L - 1);
             }
         }
         for (int cc = c0; cc < c1; cc++) {
@@ -515,6 +567,7 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
         }
         T.eu1 = (int)eu_list.size();
         T.ap1 = (int)ap_list.size();
+        T.sh1 = (int)sh_list.size();
     }
     c->zmax = zmax;
 
@@ -636,6 +689,7 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     UP(upload_vec(c, &P.wtab, wtab));
     UP(upload_vec(c, &P.eu_list, eu_list));
     UP(upload_vec(c, &P.ap_list, ap_list));
+    UP(upload_vec(c, &P.sh_list, sh_list));
     {
         const int *p_off = nullptr, *p_idx = nullptr;
         UP(upload_vec(c, &p_off, dep_off));
@@ -692,13 +746,45 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
                                 (int)c->smem_bytes));
     }
     {
-        // the persistent year kernel needs every tile resident at once
+        // the persistent year kernels need every tile resident at once
         int per_sm = 0, coop = 0;
         UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)c->year_kernel, m3d::kThreads,
                                                          c->smem_bytes));
         UP(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
         c->persistent_ok = coop && (long long)per_sm * prop.multiProcessorCount >= ntiles;
-        c->plan = c->persistent_ok ? 0 : 1;
+        // resident plan: the tile's month of matrices in shared memory
+        std::vector<m3d::ResidentTile> rt(ntiles);
+        int sp_max = 0, bk_max = 0;
+        for (int t = 0; t < ntiles; t++) {
+            const Tile &T = tiles[t];
+            int sp_first = T.sp0 < T.sp1 ? sp_off[T.sp0] : 0, sp_slots = 0;
+            for (int q = T.sp0; q < T.sp1; q++) sp_slots += sp_len[q];
+            int bk_first = T.bk0 < T.bk1 ? bk_off[T.bk0] : 0, bk_slots_t = 0;
+            for (int q = T.bk0; q < T.bk1; q++) bk_slots_t += bk_len[q];
+            rt[t].sp_base = (long long)sp_first * 32;
+            rt[t].sp_n = sp_slots * 32;
+            rt[t].bk_base = (long long)bk_first * 32;
+            rt[t].bk_n = bk_slots_t * 32;
+            rt[t].pad0 = rt[t].pad1 = 0;
+            sp_max = std::max(sp_max, rt[t].sp_n);
+            bk_max = std::max(bk_max, rt[t].bk_n);
+        }
+        m3d::ResidentLayout Ly = m3d::resident_layout(c->ntr, sp_max, bk_max, c->zmax);
+        c->resident_smem = (size_t)Ly.total;
+        const m3d::ResidentTile *rt_dev = nullptr;
+        UP(upload_vec(c, &rt_dev, rt));
+        c->R.rt = rt_dev;
+        c->R.sp_max = sp_max;
+        c->R.bk_max = bk_max;
+        if (coop && c->rk.year && c->resident_smem <= (size_t)prop.sharedMemPerBlockOptin) {
+            UP(cudaFuncSetAttribute((const void *)c->rk.year, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)c->resident_smem));
+            int rps = 0;
+            UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rps, (const void *)c->rk.year, m3d::kThreads,
+                                                             c->resident_smem));
+            c->resident_ok = (long long)rps * prop.multiProcessorCount >= ntiles;
+        }
+        c->plan = c->resident_ok ? M3D_PLAN_RESIDENT : (c->persistent_ok ? M3D_PLAN_PERSISTENT : M3D_PLAN_GRAPH);
     }
 #undef UP
     *out = c;
@@ -775,7 +861,39 @@ m3d_status build_year_graph(m3d_ctx *c)
 m3d_status run_year_from_ybuf(m3d_ctx *c, double *out, cudaMemcpyKind kind)
 {
     size_t len = sizeof(double) * (size_t)c->ntr * c->n;
-    if (c->plan == 0) {
+    if (c->plan == M3D_PLAN_RESIDENT) {
+        m3d_status st = launch_prologue(c, c->u_dev);
+        if (st != M3D_OK) return st;
+        const int nb = (c->n + 255) / 256;
+        // the year runs on the interleaved state: start in ybuf[1]
+        c->rk.to_interleaved<<<nb, 256, 0, c->stream>>>(c->n, c->ybuf[0], c->ybuf[1]);
+        CUDA_OR_FAIL(c, cudaGetLastError());
+        CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.flags, 0, sizeof(int) * c->ntiles, c->stream));
+        CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.status, 0, sizeof(int) * 4, c->stream));
+        StepParams P = c->P;
+        m3d::ResidentParams R = c->R;
+        m3d::SyncParams S = c->S;
+        double *b0 = c->ybuf[1], *b1 = c->ybuf[0];
+        int j0 = 0, nsteps = c->nstep;
+        void *args[] = {&P, &R, &S, &b0, &b1, &j0, &nsteps};
+        CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)c->rk.year, dim3(c->ntiles), dim3(m3d::kThreads),
+                                                    args, c->resident_smem, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost,
+                                        c->stream));
+        double *res = (nsteps & 1) ? b1 : b0;
+        double *other = (nsteps & 1) ? b0 : b1;
+        if (kind == cudaMemcpyDeviceToDevice) {
+            c->rk.from_interleaved<<<nb, 256, 0, c->stream>>>(c->n, res, out);
+            CUDA_OR_FAIL(c, cudaGetLastError());
+        } else {
+            c->rk.from_interleaved<<<nb, 256, 0, c->stream>>>(c->n, res, other);
+            CUDA_OR_FAIL(c, cudaGetLastError());
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(out, other, len, kind, c->stream));
+        }
+        c->last_launches = (c->model == M3D_MODEL_NDOP ? 1 : 0) + 3;
+        return M3D_OK;
+    }
+    if (c->plan == M3D_PLAN_PERSISTENT) {
         m3d_status st = launch_prologue(c, c->u_dev);
         if (st != M3D_OK) return st;
         st = launch_year_persistent(c, 0, c->nstep);
@@ -874,7 +992,10 @@ m3d_status metos3d_set_option(m3d_ctx *c, int option, long long value)
     case M3D_OPT_YEAR_PLAN:
         if (value == M3D_PLAN_PERSISTENT && !c->persistent_ok)
             return fail(c, M3D_ERR_UNSUPPORTED, "the persistent year kernel does not fit on this GPU");
-        if (value != M3D_PLAN_PERSISTENT && value != M3D_PLAN_GRAPH) return fail(c, M3D_ERR_ARG, "bad plan");
+        if (value == M3D_PLAN_RESIDENT && !c->resident_ok)
+            return fail(c, M3D_ERR_UNSUPPORTED, "the tiles' matrices do not fit in shared memory");
+        if (value != M3D_PLAN_PERSISTENT && value != M3D_PLAN_GRAPH && value != M3D_PLAN_RESIDENT)
+            return fail(c, M3D_ERR_ARG, "bad plan");
         c->plan = (int)value;
         return M3D_OK;
     case M3D_OPT_WAIT_TIMEOUT_NS:

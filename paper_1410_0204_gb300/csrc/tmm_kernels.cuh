@@ -17,7 +17,7 @@
 
 namespace m3d {
 
-constexpr int kThreads = 256;        // threads per tile CTA
+constexpr int kThreads = 512;        // threads per tile CTA (16 warps: 4 per SM sub-partition)
 constexpr int kModelNone = 0;
 constexpr int kModelNdop = 2;
 constexpr double kSigmaPar = 0.4;    // photosynthetically available fraction of I_SWR
@@ -33,7 +33,7 @@ struct Tile {
     int bk0, bk1;                    // implicit-block warp slices [bk0, bk1)
     int eu0, eu1;                    // entries of eu_list: euphotic cells / shallow columns
     int ap0, ap1;                    // entries of ap_list: aphotic cells
-    int pad0, pad1;
+    int sh0, sh1;                    // entries of sh_list: bottom cells of shallow columns (nsub = 1)
 };
 
 // Everything one step reads, as device pointers owned by the context.
@@ -57,6 +57,7 @@ struct StepParams {
     long long bk_mstride;
     // biogeochemistry
     const int *eu_list, *ap_list;          // tile-local cells, grouped per tile
+    const int *sh_list;                    // tile-local bottom cells of shallow columns (nsub = 1)
     const int *cell_kl;                    // layer k | (column layers L << 8)
     const int *cell_ulat;                  // index of the cell's latitude in the insolation table
     const double *h;                       // [n] layer thickness
@@ -163,7 +164,7 @@ __device__ __forceinline__ double martin_fraction(const double *hcol, int k, int
 
 // A whole shallow column (L <= number of euphotic layers) on one thread, with the export
 // kept in its bottom layer inside every internal step.
-__device__ __noinline__ void ndop_shallow_column(int L, const double *hcol, const double *N0,
+__device__ __forceinline__ void ndop_shallow_column(int L, const double *hcol, const double *N0,
                                                  const double *D0, const double *I, double alpha,
                                                  double sigma, double lambda, double KN, double KI,
                                                  double ds, int nsub, double *dN, double *dD)
@@ -195,7 +196,112 @@ __device__ __forceinline__ double load_state(const double *p)
     return __ldg(p);
 }
 
+// Read access to a state vector: [tracer][cell] (the caller's layout) or [cell][tracer]
+// (interleaved, used inside the resident year kernel so one gather serves all tracers).
+template <int NTR, bool INTERLEAVED, bool COHERENT>
+struct StateView {
+    const double *y;
+    int n;
+    __device__ __forceinline__ double get(int cell, int t) const
+    {
+        const double *p = INTERLEAVED ? y + (size_t)cell * NTR + t : y + (size_t)t * n + cell;
+        return load_state<COHERENT>(p);
+    }
+    __device__ __forceinline__ void gather(int cell, double *v) const
+    {
+        if (INTERLEAVED && NTR % 2 == 0) {
+            const double *p = y + (size_t)cell * NTR;
+#pragma unroll
+            for (int t = 0; t < NTR; t += 2) {
+                double2 q = COHERENT ? __ldcg(reinterpret_cast<const double2 *>(p + t))
+                                     : __ldg(reinterpret_cast<const double2 *>(p + t));
+                v[t] = q.x;
+                v[t + 1] = q.y;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < NTR; t++) v[t] = get(cell, t);
+        }
+    }
+};
+
+// Barrier over the first kThreads - 32 threads of the CTA (named barrier 1), or the whole CTA.
+__device__ __forceinline__ void barrier_sub(int id)
+{
+    if (id == 0) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" :: "n"(kThreads - 32) : "memory");
+}
+
+// The source-minus-sink increment of the PO4-DOP model (Section 2.2.1) for every cell of a
+// tile, computed from y_j and written to dq[t * zmax + i].  Reads only the tile's own cells.
+// Run by threads [0, nthr) of the CTA, which synchronise on named barrier `bar`:
+// euphotic cells first, then aphotic cells (which need their column's export) and the
+// export kept in the bottom layer of shallow columns.  With several internal steps a
+// shallow column runs whole on one thread, since its cells then couple at every step.
+template <int NTR, class SV>
+__device__ __forceinline__ void ndop_source_tile(const StepParams &P, const Tile &T, int j, const SV &Y,
+                                                 double *dq, double *ek, int nthr, int bar)
+{
+    const int tid = threadIdx.x;
+    const int zmax = P.zmax;
+    const double alpha = __ldg(P.qpar + kQAlpha), sigma = __ldg(P.qpar + kQSigma);
+    const double lambda = __ldg(P.qpar + kQLambda), KN = __ldg(P.qpar + kQKN);
+    const double KI = __ldg(P.qpar + kQKI), oms = __ldg(P.qpar + kQOneMinusSigma);
+    const int nsub = P.nsub;
+    const double ds = P.ds;
+    const double *I0row = P.I0tab + (size_t)j * P.nulat;
+    for (int e = T.eu0 + tid; e < T.eu1; e += nthr) {
+        const int i = __ldg(P.eu_list + e);
+        const int cell = T.cell0 + i;
+        const int L = __ldg(P.cell_kl + cell) >> 8;
+        const double I0 = __ldg(I0row + __ldg(P.cell_ulat + cell));
+        if (L <= kEuphotic && nsub > 1) {
+            double N0[kEuphotic], D0[kEuphotic], I[kEuphotic], dN[kEuphotic], dD[kEuphotic];
+            for (int kk = 0; kk < L; kk++) {
+                N0[kk] = Y.get(cell + kk, 0);
+                D0[kk] = Y.get(cell + kk, 1);
+                I[kk] = I0 * __ldg(P.atten + cell + kk);
+            }
+            ndop_shallow_column(L, P.h + cell, N0, D0, I, alpha, sigma, lambda, KN, KI, ds, nsub, dN, dD);
+            for (int kk = 0; kk < L; kk++) {
+                dq[i + kk] = dN[kk];
+                dq[zmax + i + kk] = dD[kk];
+            }
+        } else {
+            double v[NTR];
+            Y.gather(cell, v);
+            double dN, dD, fsum;
+            ndop_euphotic(v[0], v[1], I0 * __ldg(P.atten + cell), alpha, sigma, lambda, KN, KI, ds, nsub,
+                          dN, dD, fsum);
+            dq[i] = dN;
+            dq[zmax + i] = dD;
+            ek[i] = oms * fsum * __ldg(P.h + cell);
+        }
+    }
+    barrier_sub(bar);
+    for (int a = T.ap0 + tid; a < T.ap1; a += nthr) {
+        const int i = __ldg(P.ap_list + a);
+        const int cell = T.cell0 + i;
+        const int k = __ldg(P.cell_kl + cell) & 0xff;
+        const double Esum = ek[i - k] + ek[i - k + 1];
+        double dN, dD;
+        ndop_aphotic(Y.get(cell, 1), Esum, __ldg(P.mfrac + cell), lambda, ds, nsub, dN, dD);
+        dq[i] = dN;
+        dq[zmax + i] = dD;
+    }
+    // shallow columns (one internal step): the export stays in the bottom layer
+    for (int b = T.sh0 + tid; b < T.sh1; b += nthr) {
+        const int i = __ldg(P.sh_list + b);
+        const int cell = T.cell0 + i;
+        const int k = __ldg(P.cell_kl + cell) & 0xff;
+        const double Esum = (k == 0) ? ek[i] : ek[i - 1] + ek[i];
+        dq[i] += ds * (Esum / __ldg(P.h + cell));
+    }
+}
+
 // One TMM step on one tile.  smem: (NTR + 1) * zmax doubles.
+// Order: q increment of the tile's own cells into z (no neighbour data needed), then
+// z += A_exp(t_j) y_j, then y_{j+1} = A_imp(t_j) z.
 template <int NTR, int MODEL, bool COHERENT>
 __device__ __forceinline__ void step_tile(const StepParams &P, int tile, int j,
                                           const double *__restrict__ y, double *__restrict__ yn,
@@ -207,13 +313,20 @@ __device__ __forceinline__ void step_tile(const StepParams &P, int tile, int j,
     const int nwarps = blockDim.x >> 5;
     const int n = P.n;
     const int zmax = P.zmax;
-    double *z = smem;                 // [NTR][zmax] A_exp y + dq, tile-local cells
+    double *z = smem;                 // [NTR][zmax] dq, then A_exp y + dq, tile-local cells
     double *ek = smem + NTR * zmax;   // [zmax] export contributions of euphotic cells
 
     const int m0 = __ldg(P.m0tab + j);
     const double w = __ldg(P.wtab + j);
 
-    // ---- explicit part: z = (A_m0 + w (A_m1 - A_m0)) y, all tracers per matrix read
+    // ---- source-minus-sink increment on y_j (Section 2.2.1)
+    if (MODEL == kModelNdop) {
+        StateView<NTR, false, COHERENT> Y{y, n};
+        ndop_source_tile<NTR>(P, T, j, Y, z, ek, blockDim.x, 0);
+        __syncthreads();
+    }
+
+    // ---- explicit part: z += (A_m0 + w (A_m1 - A_m0)) y, all tracers per matrix read
     {
         const double *__restrict__ a0 = P.sp_a + (long long)m0 * P.sp_mstride;
         const double *__restrict__ d0 = P.sp_d + (long long)m0 * P.sp_mstride;
@@ -235,64 +348,12 @@ __device__ __forceinline__ void step_tile(const StepParams &P, int tile, int j,
             }
             if (row >= 0) {
 #pragma unroll
-                for (int t = 0; t < NTR; t++) z[t * zmax + row] = acc[t];
+                for (int t = 0; t < NTR; t++)
+                    z[t * zmax + row] = (MODEL == kModelNdop) ? acc[t] + z[t * zmax + row] : acc[t];
             }
         }
     }
     __syncthreads();
-
-    // ---- source-minus-sink term q on y_j (Section 2.2.1), added as its increment
-    if (MODEL == kModelNdop) {
-        const double alpha = __ldg(P.qpar + kQAlpha), sigma = __ldg(P.qpar + kQSigma);
-        const double lambda = __ldg(P.qpar + kQLambda), KN = __ldg(P.qpar + kQKN);
-        const double KI = __ldg(P.qpar + kQKI), oms = __ldg(P.qpar + kQOneMinusSigma);
-        const int nsub = P.nsub;
-        const double ds = P.ds;
-        const double *I0row = P.I0tab + (size_t)j * P.nulat;
-        // euphotic cells of deep columns, and whole shallow columns
-        for (int e = T.eu0 + (int)threadIdx.x; e < T.eu1; e += blockDim.x) {
-            const int i = __ldg(P.eu_list + e);
-            const int cell = T.cell0 + i;
-            const int kl = __ldg(P.cell_kl + cell);
-            const int L = kl >> 8;
-            const double I0 = __ldg(I0row + __ldg(P.cell_ulat + cell));
-            if (L <= kEuphotic) {
-                double N0[kEuphotic], D0[kEuphotic], I[kEuphotic], dN[kEuphotic], dD[kEuphotic];
-                for (int kk = 0; kk < L; kk++) {
-                    N0[kk] = load_state<COHERENT>(y + cell + kk);
-                    D0[kk] = load_state<COHERENT>(y + n + cell + kk);
-                    I[kk] = I0 * __ldg(P.atten + cell + kk);
-                }
-                ndop_shallow_column(L, P.h + cell, N0, D0, I, alpha, sigma, lambda, KN, KI, ds,
-                                    nsub, dN, dD);
-                for (int kk = 0; kk < L; kk++) {
-                    z[i + kk] += dN[kk];
-                    z[zmax + i + kk] += dD[kk];
-                }
-            } else {
-                double dN, dD, fsum;
-                ndop_euphotic(load_state<COHERENT>(y + cell), load_state<COHERENT>(y + n + cell),
-                              I0 * __ldg(P.atten + cell), alpha, sigma, lambda, KN, KI, ds, nsub,
-                              dN, dD, fsum);
-                z[i] += dN;
-                z[zmax + i] += dD;
-                ek[i] = oms * fsum * __ldg(P.h + cell);
-            }
-        }
-        __syncthreads();
-        for (int a = T.ap0 + (int)threadIdx.x; a < T.ap1; a += blockDim.x) {
-            const int i = __ldg(P.ap_list + a);
-            const int cell = T.cell0 + i;
-            const int k = __ldg(P.cell_kl + cell) & 0xff;
-            const double Esum = ek[i - k] + ek[i - k + 1];
-            double dN, dD;
-            ndop_aphotic(load_state<COHERENT>(y + n + cell), Esum, __ldg(P.mfrac + cell), lambda, ds,
-                         nsub, dN, dD);
-            z[i] += dN;
-            z[zmax + i] += dD;
-        }
-        __syncthreads();
-    }
 
     // ---- implicit part: y_{j+1} = (B_m0 + w (B_m1 - B_m0)) z, column by column
     {
@@ -400,18 +461,15 @@ __device__ __forceinline__ void year_persistent(const StepParams &P, const SyncP
         if (s > 0) {
             if (threadIdx.x < 32) {
                 bool ok = wait_neighbours(S, tile, s, s);
-                __threadfence();
                 if (threadIdx.x == 0) abort_flag = ok ? 0 : 1;
             }
             __syncthreads();
             if (abort_flag) return;
         }
         step_tile<NTR, MODEL, true>(P, tile, j, y, yn, smem);
+        // the CTA barrier orders every thread's stores of y_{j+1} before thread 0's release
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            if (tile != S.withhold_tile) store_release(S.flags + tile, s + 1);
-        }
+        if (threadIdx.x == 0 && tile != S.withhold_tile) store_release(S.flags + tile, s + 1);
     }
 }
 

@@ -100,15 +100,18 @@ def test_step_transport_only_many_tracers(m3d):
 
 
 # ------------------------------------------------------------------ year maps
-@pytest.mark.parametrize("plan", ["persistent", "graph"])
+PLANS = {"resident": 2, "persistent": 0, "graph": 1}
+LAUNCHES = {"resident": 4, "persistent": 2, "graph": 2881}
+
+
+@pytest.mark.parametrize("plan", list(PLANS))
 @pytest.mark.parametrize("name,nsub", [("tiny_4x3x3", 1), ("tiny_6x4x4", 8), ("ndop_64x32x8", 1)])
 def test_year_map_matches_oracle(m3d, name, nsub, plan):
     p, P = problem(name)
     u = mi.default_params_ndop()
     ctx = ctx_for(m3d, p, nsub=nsub)
-    if plan == "graph":
-        ctx.set_option(m3d.OPT_YEAR_PLAN, m3d.PLAN_GRAPH)
-    assert ctx.get_option(m3d.OPT_YEAR_PLAN) == (m3d.PLAN_GRAPH if plan == "graph" else m3d.PLAN_PERSISTENT)
+    assert ctx.get_option(m3d.OPT_YEAR_PLAN) == m3d.PLAN_RESIDENT      # the default where it fits
+    ctx.set_option(m3d.OPT_YEAR_PLAN, PLANS[plan])
     y0 = mi.initial_state(p)
     yd, ud = cuda(y0), cuda(u)
     y1 = torch.empty_like(yd)
@@ -117,7 +120,7 @@ def test_year_map_matches_oracle(m3d, name, nsub, plan):
     got = y1.cpu().numpy()
     want = oracle.year_map(P, y0, u, nsub=nsub)
     assert rel_err(got, want) < YEAR_TOL
-    assert ctx.last_launch_count() == (2881 if plan == "graph" else 2)
+    assert ctx.last_launch_count() == LAUNCHES[plan]
     # mass is conserved on the device too (Section 3 matrices conserve V^T y; q is column-conservative)
     m0 = math.fsum((p.vol * y0).ravel())
     assert abs(ctx.mass(y1) - m0) / m0 < 1e-12
@@ -143,19 +146,21 @@ def test_year_map_paper_grid_matches_oracle(m3d):
     ctx.close()
 
 
-def test_persistent_and_graph_plans_agree_bitwise(m3d):
-    """Both plans run the same per-tile step in the same order: identical results."""
-    p, _ = problem("ndop_64x32x8")
+@pytest.mark.parametrize("name", ["ndop_64x32x8", "ndop_128x64x15"])
+def test_all_plans_agree_bitwise(m3d, name):
+    """All plans run the same per-tile arithmetic in the same order: identical results."""
+    p, _ = problem(name)
     u = cuda(mi.default_params_ndop())
     y0 = cuda(mi.random_state(p))
-    a = torch.empty_like(y0)
-    b = torch.empty_like(y0)
     ctx = ctx_for(m3d, p)
-    ctx.year_map(y0, a, u)
-    ctx.set_option(m3d.OPT_YEAR_PLAN, m3d.PLAN_GRAPH)
-    ctx.year_map(y0, b, u)
+    out = {}
+    for plan, code in PLANS.items():
+        ctx.set_option(m3d.OPT_YEAR_PLAN, code)
+        out[plan] = torch.empty_like(y0)
+        ctx.year_map(y0, out[plan], u)
     ctx.sync()
-    assert torch.equal(a, b)
+    assert torch.equal(out["resident"], out["graph"])
+    assert torch.equal(out["persistent"], out["graph"])
     ctx.close()
 
 
@@ -172,10 +177,13 @@ def test_persistent_wait_timeout_is_reported_and_recoverable(m3d):
     assert ctx.get_option(m3d.OPT_NTILES) > 1
     ctx.set_option(m3d.OPT_WAIT_TIMEOUT_NS, 50_000_000)      # 50 ms
     ctx.set_option(m3d.OPT_TEST_WITHHOLD_TILE, 0)
-    ctx.year_map(y0, y1, u)
-    with pytest.raises(m3d.Metos3dError) as e:
-        ctx.sync()
-    assert e.value.status == m3d.M3D_ERR_TIMEOUT
+    for plan in (m3d.PLAN_RESIDENT, m3d.PLAN_PERSISTENT):
+        ctx.set_option(m3d.OPT_YEAR_PLAN, plan)
+        ctx.year_map(y0, y1, u)
+        with pytest.raises(m3d.Metos3dError) as e:
+            ctx.sync()
+        assert e.value.status == m3d.M3D_ERR_TIMEOUT
+    ctx.set_option(m3d.OPT_YEAR_PLAN, m3d.PLAN_RESIDENT)
     ctx.set_option(m3d.OPT_TEST_WITHHOLD_TILE, -1)
     ctx.set_option(m3d.OPT_WAIT_TIMEOUT_NS, 2_000_000_000)
     ctx.year_map(y0, y1, u)
