@@ -207,14 +207,22 @@ m3d_status metos3d_sync(m3d_ctx *ctx);
  *   M3D_OPT_TEST_WITHHOLD_TILE: for tests of the timeout path only: the given tile never
  *       announces its progress, so its neighbours' waits run out (-1: off, the default).
  *   M3D_OPT_NTILES (read only): number of tiles (CTAs) of a step.
+ *   M3D_OPT_IMPLICIT_FORM (resident plan): M3D_IMPLICIT_TRIDIAGONAL (default when every
+ *       monthly implicit block is, to 1e-11 relative, the inverse of a tridiagonal matrix,
+ *       as a vertical diffusion (I - dt K)^{-1} is): the interpolated implicit part is
+ *       applied as z0 + w (z1 - z0) with z_h solved by Thomas' algorithm from the two
+ *       monthly tridiagonal factors, which equals the interpolated dense product up to
+ *       rounding at a third of its FP64 work; M3D_IMPLICIT_DENSE: the dense blocks.
  * metos3d_get_option returns -1 for an unknown option.
  */
 enum {
     M3D_OPT_YEAR_PLAN = 1,
     M3D_OPT_WAIT_TIMEOUT_NS = 2,
     M3D_OPT_TEST_WITHHOLD_TILE = 3,
-    M3D_OPT_NTILES = 4
+    M3D_OPT_NTILES = 4,
+    M3D_OPT_IMPLICIT_FORM = 5
 };
+enum { M3D_IMPLICIT_DENSE = 0, M3D_IMPLICIT_TRIDIAGONAL = 1 };
 enum { M3D_PLAN_PERSISTENT = 0, M3D_PLAN_GRAPH = 1, M3D_PLAN_RESIDENT = 2 };
 m3d_status metos3d_set_option(m3d_ctx *ctx, int option, long long value);
 long long metos3d_get_option(const m3d_ctx *ctx, int option);

@@ -27,6 +27,9 @@ OPT_YEAR_PLAN = 1
 OPT_WAIT_TIMEOUT_NS = 2
 OPT_TEST_WITHHOLD_TILE = 3
 OPT_NTILES = 4
+OPT_IMPLICIT_FORM = 5
+IMPLICIT_DENSE = 0
+IMPLICIT_TRIDIAGONAL = 1
 PLAN_PERSISTENT = 0
 PLAN_GRAPH = 1
 PLAN_RESIDENT = 2

@@ -40,12 +40,12 @@ __global__ void __launch_bounds__(m3d::kThreads, 1) k_year(StepParams P, m3d::Sy
     m3d::year_persistent<NTR, MODEL>(P, S, buf0, buf1, j0, nsteps, smem);
 }
 
-template <int NTR, int MODEL>
+template <int NTR, int MODEL, bool TRI>
 __global__ void __launch_bounds__(m3d::kThreads, 1) k_year_resident(StepParams P, m3d::ResidentParams R,
                                                                  m3d::SyncParams S, double *buf0, double *buf1,
                                                                  int j0, int nsteps)
 {
-    m3d::year_resident<NTR, MODEL>(P, R, S, buf0, buf1, j0, nsteps);
+    m3d::year_resident<NTR, MODEL, TRI>(P, R, S, buf0, buf1, j0, nsteps);
 }
 
 // Per-call tables of the PO4-DOP model that depend on the parameters u:
@@ -187,14 +187,15 @@ typedef void (*resident_kernel_t)(StepParams, m3d::ResidentParams, m3d::SyncPara
 typedef void (*layout_kernel_t)(int, const double *, double *);
 
 struct ResidentKernels {
-    resident_kernel_t year;
+    resident_kernel_t year, year_tri;
     layout_kernel_t to_interleaved, from_interleaved;
 };
 
 template <int NTR, int MODEL>
 ResidentKernels resident_kernels()
 {
-    return {k_year_resident<NTR, MODEL>, m3d::k_interleave<NTR>, m3d::k_deinterleave<NTR>};
+    return {k_year_resident<NTR, MODEL, false>, k_year_resident<NTR, MODEL, true>, m3d::k_interleave<NTR>,
+            m3d::k_deinterleave<NTR>};
 }
 
 ResidentKernels pick_resident_kernels(int model, int ntr)
@@ -248,9 +249,12 @@ struct m3d_ctx {
     int plan = 0;                       // M3D_PLAN_*
     int persistent_ok = 0;              // all tiles fit on the GPU at once (streaming plan)
     int resident_ok = 0;                // ... with their month of matrices in shared memory
+    int tri_ok = 0;                     // every implicit block is the inverse of a tridiagonal matrix
+    int tri_resident_ok = 0;            // ... and the tridiagonal resident kernel fits
+    int implicit_form = 0;              // M3D_IMPLICIT_DENSE or M3D_IMPLICIT_TRIDIAGONAL (resident plan)
     m3d::ResidentParams R{};
     ResidentKernels rk{};
-    size_t resident_smem = 0;
+    size_t resident_smem = 0, resident_tri_smem = 0;
     int *status_host = nullptr;         // pinned copy of S.status
     double *qpar = nullptr;
     double *u_dev = nullptr;
@@ -346,6 +350,82 @@ std::vector<int> partition_columns(const m3d_grid *g, const int *rowptr, int ntr
     }
     bounds.push_back(g->ncol);
     return bounds;
+}
+
+// If the L x L row-major block B is the inverse of a tridiagonal matrix M (to 1e-11 relative),
+// write the Thomas factors of M: nl[k] = -l_k, rd[k] = 1/d_k, ne[k] = -e_k, and return true.
+bool tridiagonal_factors(const double *B, int L, double *nl, double *rd, double *ne)
+{
+    std::vector<double> a(B, B + (size_t)L * L), inv((size_t)L * L, 0.0);
+    for (int i = 0; i < L; i++) inv[(size_t)i * L + i] = 1.0;
+    for (int col = 0; col < L; col++) {            // Gauss-Jordan with partial pivoting
+        int piv = col;
+        for (int r = col + 1; r < L; r++)
+            if (std::fabs(a[(size_t)r * L + col]) > std::fabs(a[(size_t)piv * L + col])) piv = r;
+        if (a[(size_t)piv * L + col] == 0.0) return false;
+        if (piv != col)
+            for (int k = 0; k < L; k++) {
+                std::swap(a[(size_t)piv * L + k], a[(size_t)col * L + k]);
+                std::swap(inv[(size_t)piv * L + k], inv[(size_t)col * L + k]);
+            }
+        double p = a[(size_t)col * L + col];
+        for (int k = 0; k < L; k++) { a[(size_t)col * L + k] /= p; inv[(size_t)col * L + k] /= p; }
+        for (int r = 0; r < L; r++) {
+            if (r == col) continue;
+            double f = a[(size_t)r * L + col];
+            if (f == 0.0) continue;
+            for (int k = 0; k < L; k++) {
+                a[(size_t)r * L + k] -= f * a[(size_t)col * L + k];
+                inv[(size_t)r * L + k] -= f * inv[(size_t)col * L + k];
+            }
+        }
+    }
+    for (int i = 0; i < L; i++) {
+        double rowmax = 0.0;
+        for (int k = 0; k < L; k++) rowmax = std::max(rowmax, std::fabs(inv[(size_t)i * L + k]));
+        for (int k = 0; k < L; k++)
+            if (std::abs(i - k) > 1 && std::fabs(inv[(size_t)i * L + k]) > 1e-11 * rowmax) return false;
+    }
+    double dprev = 0.0;
+    for (int k = 0; k < L; k++) {
+        double l = k > 0 ? inv[(size_t)k * L + k - 1] / dprev : 0.0;
+        double d = inv[(size_t)k * L + k] - (k > 0 ? l * inv[(size_t)(k - 1) * L + k] : 0.0);
+        if (!(d > 0.0) || !std::isfinite(d)) return false;
+        nl[k] = -l;
+        rd[k] = 1.0 / d;
+        ne[k] = k + 1 < L ? -inv[(size_t)k * L + k + 1] * rd[k] : 0.0;
+        dprev = d;
+    }
+    return true;
+}
+
+// Deal the slices [s0, s1) (cost = slot count) to the warps of one tile: longest first to
+// the least loaded SM sub-partition (warp w sits on sub-partition w mod 4), round robin over
+// that sub-partition's warps.  Appends to wlist and woff (nwarps + 1 offsets).
+void deal_slices(int s0, int s1, const std::vector<int> &len, int nwarps, std::vector<int> &wlist,
+                 std::vector<int> &woff)
+{
+    std::vector<int> order;
+    for (int s = s0; s < s1; s++) order.push_back(s);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return len[a] > len[b]; });
+    const int nsub = 4;
+    std::vector<long long> load(nsub, 0);
+    std::vector<int> next(nsub, 0);
+    std::vector<std::vector<int>> per_warp(nwarps);
+    for (int s : order) {
+        int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[g] += len[s];
+        int w = g + nsub * (next[g] % (nwarps / nsub));
+        next[g]++;
+        per_warp[w].push_back(s);
+    }
+    int base = (int)wlist.size();
+    for (int w = 0; w < nwarps; w++) {
+        woff.push_back(base);
+        wlist.insert(wlist.end(), per_warp[w].begin(), per_warp[w].end());
+        base = (int)wlist.size();
+    }
+    woff.push_back(base);
 }
 
 }  // namespace
@@ -683,6 +763,18 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     UP(upload_vec(c, &P.bk_row, bk_row));
     UP(upload_vec(c, &P.bk_cb, bk_cb));
     UP(upload_vec(c, &P.bk_L, bk_L));
+    {
+        std::vector<int> spw, spwo, bkw, bkwo;
+        const int nwarps = m3d::kThreads / 32;
+        for (int t = 0; t < ntiles; t++) {
+            deal_slices(tiles[t].sp0, tiles[t].sp1, sp_len, nwarps, spw, spwo);
+            deal_slices(tiles[t].bk0, tiles[t].bk1, bk_len, nwarps, bkw, bkwo);
+        }
+        UP(upload_vec(c, &P.sp_wlist, spw));
+        UP(upload_vec(c, &P.sp_woff, spwo));
+        UP(upload_vec(c, &P.bk_wlist, bkw));
+        UP(upload_vec(c, &P.bk_woff, bkwo));
+    }
     UP(upload_vec(c, &P.bk_b, bk_b));
     UP(upload_vec(c, &P.bk_d, bk_d));
     UP(upload_vec(c, &P.m0tab, m0tab));
@@ -769,13 +861,54 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
             sp_max = std::max(sp_max, rt[t].sp_n);
             bk_max = std::max(bk_max, rt[t].bk_n);
         }
-        m3d::ResidentLayout Ly = m3d::resident_layout(c->ntr, sp_max, bk_max, c->zmax);
+        m3d::ResidentLayout Ly = m3d::resident_layout(c->ntr, sp_max, bk_max, c->zmax, false);
+        m3d::ResidentLayout Lt = m3d::resident_layout(c->ntr, sp_max, bk_max, c->zmax, true);
         c->resident_smem = (size_t)Ly.total;
+        c->resident_tri_smem = (size_t)Lt.total;
         const m3d::ResidentTile *rt_dev = nullptr;
         UP(upload_vec(c, &rt_dev, rt));
         c->R.rt = rt_dev;
         c->R.sp_max = sp_max;
         c->R.bk_max = bk_max;
+        // tridiagonal form of the implicit blocks, when every one of them has it
+        {
+            std::vector<double> tri((size_t)c->nmonth * 3 * c->n, 0.0);
+            bool ok = true;
+            for (int m = 0; m < c->nmonth && ok; m++)
+                for (int cc = 0; cc < g->ncol && ok; cc++) {
+                    int L = g->col_start[cc + 1] - g->col_start[cc], s0 = g->col_start[cc];
+                    double *base = tri.data() + (size_t)m * 3 * c->n;
+                    ok = tridiagonal_factors(mt->imp_blk + (size_t)m * s_imp + blk_off[cc], L, base + s0,
+                                             base + c->n + s0, base + 2 * (size_t)c->n + s0);
+                }
+            c->tri_ok = ok;
+            if (ok) {
+                const double *tri_dev = nullptr;
+                UP(upload_vec(c, &tri_dev, tri));
+                c->R.tri = tri_dev;
+                c->R.tri_mstride = 3LL * c->n;
+                std::vector<int> chains, chain_off(ntiles + 1, 0);
+                for (int t = 0; t < ntiles; t++) {
+                    int c0 = bounds[t], c1 = bounds[t + 1], cell0 = g->col_start[c0];
+                    std::vector<int> cols;
+                    for (int cc = c0; cc < c1; cc++) cols.push_back(cc);
+                    std::stable_sort(cols.begin(), cols.end(), [&](int a, int b) {
+                        return (g->col_start[a + 1] - g->col_start[a]) > (g->col_start[b + 1] - g->col_start[b]);
+                    });
+                    for (int cc : cols)
+                        for (int h = 0; h < 2; h++)
+                            for (int tr = 0; tr < c->ntr; tr++)
+                                chains.push_back(m3d::pack_chain(g->col_start[cc] - cell0,
+                                                                 g->col_start[cc + 1] - g->col_start[cc], tr, h));
+                    chain_off[t + 1] = (int)chains.size();
+                }
+                const int *ch_dev = nullptr, *choff_dev = nullptr;
+                UP(upload_vec(c, &ch_dev, chains));
+                UP(upload_vec(c, &choff_dev, chain_off));
+                c->R.chains = ch_dev;
+                c->R.chain_off = choff_dev;
+            }
+        }
         if (coop && c->rk.year && c->resident_smem <= (size_t)prop.sharedMemPerBlockOptin) {
             UP(cudaFuncSetAttribute((const void *)c->rk.year, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)c->resident_smem));
@@ -784,6 +917,16 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
                                                              c->resident_smem));
             c->resident_ok = (long long)rps * prop.multiProcessorCount >= ntiles;
         }
+        if (coop && c->tri_ok && c->rk.year_tri && c->resident_tri_smem <= (size_t)prop.sharedMemPerBlockOptin) {
+            UP(cudaFuncSetAttribute((const void *)c->rk.year_tri, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)c->resident_tri_smem));
+            int rps = 0;
+            UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rps, (const void *)c->rk.year_tri, m3d::kThreads,
+                                                             c->resident_tri_smem));
+            c->tri_resident_ok = (long long)rps * prop.multiProcessorCount >= ntiles;
+        }
+        if (c->tri_resident_ok && !c->resident_ok) c->resident_ok = 1;
+        c->implicit_form = c->tri_resident_ok ? M3D_IMPLICIT_TRIDIAGONAL : M3D_IMPLICIT_DENSE;
         c->plan = c->resident_ok ? M3D_PLAN_RESIDENT : (c->persistent_ok ? M3D_PLAN_PERSISTENT : M3D_PLAN_GRAPH);
     }
 #undef UP
@@ -876,8 +1019,10 @@ m3d_status run_year_from_ybuf(m3d_ctx *c, double *out, cudaMemcpyKind kind)
         double *b0 = c->ybuf[1], *b1 = c->ybuf[0];
         int j0 = 0, nsteps = c->nstep;
         void *args[] = {&P, &R, &S, &b0, &b1, &j0, &nsteps};
-        CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)c->rk.year, dim3(c->ntiles), dim3(m3d::kThreads),
-                                                    args, c->resident_smem, c->stream));
+        const bool tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL;
+        CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)(tri ? c->rk.year_tri : c->rk.year), dim3(c->ntiles),
+                                                    dim3(m3d::kThreads), args,
+                                                    tri ? c->resident_tri_smem : c->resident_smem, c->stream));
         CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost,
                                         c->stream));
         double *res = (nsteps & 1) ? b1 : b0;
@@ -1002,6 +1147,14 @@ m3d_status metos3d_set_option(m3d_ctx *c, int option, long long value)
         if (value <= 0) return fail(c, M3D_ERR_ARG, "timeout must be positive");
         c->S.timeout_ns = (unsigned long long)value;
         return M3D_OK;
+    case M3D_OPT_IMPLICIT_FORM:
+        if (value == M3D_IMPLICIT_TRIDIAGONAL && !c->tri_resident_ok)
+            return fail(c, M3D_ERR_UNSUPPORTED, "the implicit blocks have no usable tridiagonal form");
+        if (value == M3D_IMPLICIT_DENSE && !(c->resident_smem <= c->resident_tri_smem || c->resident_ok))
+            return fail(c, M3D_ERR_UNSUPPORTED, "the dense resident kernel does not fit");
+        if (value != M3D_IMPLICIT_DENSE && value != M3D_IMPLICIT_TRIDIAGONAL) return fail(c, M3D_ERR_ARG, "bad form");
+        c->implicit_form = (int)value;
+        return M3D_OK;
     case M3D_OPT_TEST_WITHHOLD_TILE:
         if (value < -1 || value >= c->ntiles) return fail(c, M3D_ERR_ARG, "tile out of range");
         c->S.withhold_tile = (int)value;
@@ -1019,6 +1172,7 @@ long long metos3d_get_option(const m3d_ctx *c, int option)
     case M3D_OPT_WAIT_TIMEOUT_NS: return (long long)c->S.timeout_ns;
     case M3D_OPT_TEST_WITHHOLD_TILE: return c->S.withhold_tile;
     case M3D_OPT_NTILES: return c->ntiles;
+    case M3D_OPT_IMPLICIT_FORM: return c->implicit_form;
     default: return -1;
     }
 }

@@ -17,7 +17,10 @@
 
 namespace m3d {
 
-constexpr int kThreads = 512;        // threads per tile CTA (16 warps: 4 per SM sub-partition)
+#ifndef M3D_THREADS
+#define M3D_THREADS 512
+#endif
+constexpr int kThreads = M3D_THREADS; // threads per tile CTA (512: 16 warps, 4 per SM sub-partition)
 constexpr int kModelNone = 0;
 constexpr int kModelNdop = 2;
 constexpr double kSigmaPar = 0.4;    // photosynthetically available fraction of I_SWR
@@ -53,6 +56,10 @@ struct StepParams {
     // whose column starts at tile-local cell bk_cb and has bk_L layers; element (c, l) at
     // (bk_off[s] + c) * 32 + l holds B[row][c] (0 beyond bk_L).
     const int *bk_len, *bk_off, *bk_row, *bk_cb, *bk_L;
+    // slices of each tile dealt to its warps so that the four SM sub-partitions (warp w runs
+    // on sub-partition w mod 4, each with its own FP64 unit) get equal FP64 work: the slices
+    // of warp w of tile t are wlist[woff[t*(nwarps+1) + w] .. woff[t*(nwarps+1) + w + 1])
+    const int *sp_wlist, *sp_woff, *bk_wlist, *bk_woff;
     const double *bk_b, *bk_d;             // [nmonth][...]: B_m and B_{m+1} - B_m
     long long bk_mstride;
     // biogeochemistry

@@ -153,6 +153,7 @@ def test_all_plans_agree_bitwise(m3d, name):
     u = cuda(mi.default_params_ndop())
     y0 = cuda(mi.random_state(p))
     ctx = ctx_for(m3d, p)
+    ctx.set_option(m3d.OPT_IMPLICIT_FORM, m3d.IMPLICIT_DENSE)
     out = {}
     for plan, code in PLANS.items():
         ctx.set_option(m3d.OPT_YEAR_PLAN, code)
@@ -161,6 +162,46 @@ def test_all_plans_agree_bitwise(m3d, name):
     ctx.sync()
     assert torch.equal(out["resident"], out["graph"])
     assert torch.equal(out["persistent"], out["graph"])
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["ndop_64x32x8", "ndop_128x64x15"])
+def test_tridiagonal_implicit_form_matches_dense(m3d, name):
+    """The synthetic implicit blocks are inverses of tridiagonal diffusion matrices: the
+    Thomas form is detected and agrees with the dense interpolated product to rounding."""
+    p, _ = problem(name)
+    u = cuda(mi.default_params_ndop())
+    y0 = cuda(mi.random_state(p))
+    ctx = ctx_for(m3d, p)
+    assert ctx.get_option(m3d.OPT_IMPLICIT_FORM) == m3d.IMPLICIT_TRIDIAGONAL
+    tri = torch.empty_like(y0)
+    dense = torch.empty_like(y0)
+    ctx.year_map(y0, tri, u)
+    ctx.set_option(m3d.OPT_IMPLICIT_FORM, m3d.IMPLICIT_DENSE)
+    ctx.year_map(y0, dense, u)
+    ctx.sync()
+    assert rel_err(tri.cpu().numpy(), dense.cpu().numpy()) < 1e-12
+    ctx.close()
+
+
+def test_general_dense_blocks_fall_back_to_dense_form(m3d):
+    """Implicit blocks that are not inverses of tridiagonal matrices keep the dense form."""
+    import copy
+    p0, _ = problem("tiny_6x4x4")
+    p = copy.copy(p0)
+    r = np.random.default_rng(3)
+    p.imp_blk = p0.imp_blk * (1.0 + 0.05 * r.random(p0.imp_blk.shape))
+    P = oracle.Problem(p)
+    ctx = ctx_for(m3d, p)
+    assert ctx.get_option(m3d.OPT_IMPLICIT_FORM) == m3d.IMPLICIT_DENSE
+    with pytest.raises(m3d.Metos3dError):
+        ctx.set_option(m3d.OPT_IMPLICIT_FORM, m3d.IMPLICIT_TRIDIAGONAL)
+    u_h = mi.default_params_ndop()
+    y0_h = mi.initial_state(p)
+    y1 = torch.empty((2, p.n), dtype=torch.float64, device="cuda")
+    ctx.year_map(cuda(y0_h), y1, cuda(u_h))
+    ctx.sync()
+    assert rel_err(y1.cpu().numpy(), oracle.year_map(P, y0_h, u_h)) < YEAR_TOL
     ctx.close()
 
 
