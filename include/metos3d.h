@@ -227,6 +227,60 @@ enum { M3D_PLAN_PERSISTENT = 0, M3D_PLAN_GRAPH = 1, M3D_PLAN_RESIDENT = 2 };
 m3d_status metos3d_set_option(m3d_ctx *ctx, int option, long long value);
 long long metos3d_get_option(const m3d_ctx *ctx, int option);
 
+/*
+ * Spin-up (Sections 4 and 7): the fixed-point iteration y <- phi(y) for up to nyears model
+ * years, stopping early when ||phi(y) - y||_2 <= tol.  y: device [ntracer][n], updated in
+ * place; u: device [nparam].  residuals_host (may be NULL) receives ||phi(y) - y||_2 of
+ * every year; *years_done the number of years run.  Synchronous.
+ */
+m3d_status metos3d_spinup(m3d_ctx *ctx, double *y, const double *u, int nyears, double tol,
+                          double *residuals_host, int *years_done);
+
+/*
+ * Matrix-free Newton-Krylov periodic solve (Sections 6 and 7): Newton's method on
+ * F(y) = y - phi(y) = 0, globalised by a backtracking line search with cubic interpolation
+ * (Armijo constant 1e-4, steps kept in [0.1, 0.5] of the previous one); each Newton system
+ * (I - phi'(y)) s = -F(y) is solved by restarted GMRES with modified Gram-Schmidt
+ * orthogonalisation to the Eisenstat-Walker tolerance (choice 2: eta_0 = 0.3,
+ * gamma = 0.9, alpha = (1+sqrt 5)/2, safeguarded, kept within [0.5 tol/||F||, 0.9]).
+ * Jacobian-vector products are finite differences, J v = v - (phi(y + h v) - phi(y)) / h
+ * with h = fd_eps ||y|| / ||v||.  phi conserves the total mass, so I - phi' is singular and
+ * the periodic solution is unique only for a given mass: each Newton step is projected on
+ * the zero-mass directions, and the solution keeps the mass of the initial state.
+ * y: device [ntracer][n], initial guess on entry and solution on exit; u: device [nparam];
+ * opts NULL for the defaults (metos3d_newton_default_options); report may be NULL.
+ * Returns M3D_NOT_CONVERGED (with the report filled in) if the tolerance is not met.
+ * Synchronous; allocates its Krylov basis ((restart + 11) state vectors) for the call.
+ */
+enum { M3D_JV_FD = 0, M3D_JV_TANGENT = 1 };
+typedef struct {
+    double tol;                 /* ||y - phi(y)||_2 at which to stop (default 1e-8) */
+    int max_newton;             /* Newton steps (default 40) */
+    int restart;                /* GMRES restart length (default 200, the paper's) */
+    int max_krylov;             /* GMRES iterations per Newton step (default 200) */
+    int jv;                     /* M3D_JV_FD (default) or M3D_JV_TANGENT */
+    double fd_eps;              /* relative finite-difference step (default 1e-8) */
+    int line_search;            /* 1: backtracking line search (default); 0: full Newton steps */
+} m3d_newton_opts;
+
+#define M3D_NEWTON_MAX_HIST 64
+typedef struct {
+    int converged;
+    int newton_steps;
+    int krylov_total;           /* GMRES iterations over all Newton steps */
+    int year_maps;              /* year maps evaluated (model-year equivalents) */
+    int tangent_maps;           /* tangent year maps evaluated */
+    double residual0, residual; /* ||F|| at the start and at the end */
+    double residuals[M3D_NEWTON_MAX_HIST];   /* ||F|| after each Newton step ([0]: initial) */
+    int krylov[M3D_NEWTON_MAX_HIST];         /* GMRES iterations of each Newton step */
+    double lambdas[M3D_NEWTON_MAX_HIST];     /* line-search step of each Newton step */
+    double seconds;
+} m3d_newton_report;
+
+void metos3d_newton_default_options(m3d_newton_opts *opts);
+m3d_status metos3d_newton_solve(m3d_ctx *ctx, double *y, const double *u, const m3d_newton_opts *opts,
+                                m3d_newton_report *report);
+
 /* Sizes of a context: n, ncol, ntracer, nstep (any pointer may be NULL). */
 m3d_status metos3d_info(const m3d_ctx *ctx, int *n, int *ncol, int *ntracer, int *nstep);
 

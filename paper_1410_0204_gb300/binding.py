@@ -58,6 +58,33 @@ class _Matrices(C.Structure):
                 ("s_imp", C.c_longlong), ("imp_blk", C.POINTER(C.c_double))]
 
 
+class NewtonOptions(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_newton", C.c_int), ("restart", C.c_int), ("max_krylov", C.c_int),
+                ("jv", C.c_int), ("fd_eps", C.c_double), ("line_search", C.c_int)]
+
+
+NEWTON_MAX_HIST = 64
+
+
+class NewtonReport(C.Structure):
+    _fields_ = [("converged", C.c_int), ("newton_steps", C.c_int), ("krylov_total", C.c_int),
+                ("year_maps", C.c_int), ("tangent_maps", C.c_int), ("residual0", C.c_double),
+                ("residual", C.c_double), ("residuals", C.c_double * NEWTON_MAX_HIST),
+                ("krylov", C.c_int * NEWTON_MAX_HIST), ("lambdas", C.c_double * NEWTON_MAX_HIST),
+                ("seconds", C.c_double)]
+
+    def to_dict(self):
+        k = self.newton_steps
+        return {"converged": bool(self.converged), "newton_steps": k, "krylov_total": self.krylov_total,
+                "year_maps": self.year_maps, "tangent_maps": self.tangent_maps, "residual0": self.residual0,
+                "residual": self.residual, "residuals": list(self.residuals[:k + 1]),
+                "krylov": list(self.krylov[:k]), "lambdas": list(self.lambdas[:k]), "seconds": self.seconds}
+
+
+JV_FD = 0
+JV_TANGENT = 1
+
+
 class _Model(C.Structure):
     _fields_ = [("model_id", C.c_int), ("ntracer", C.c_int), ("nparam", C.c_int),
                 ("nsub", C.c_int), ("nstep", C.c_int)]
@@ -106,13 +133,18 @@ def load(build_if_missing: bool = False):
     L.metos3d_set_option.argtypes = [vp, C.c_int, C.c_longlong]
     L.metos3d_get_option.argtypes = [vp, C.c_int]
     L.metos3d_get_option.restype = C.c_longlong
+    L.metos3d_newton_default_options.argtypes = [C.POINTER(NewtonOptions)]
+    L.metos3d_newton_default_options.restype = None
+    L.metos3d_newton_solve.argtypes = [vp, vp, vp, C.POINTER(NewtonOptions), C.POINTER(NewtonReport)]
+    L.metos3d_spinup.argtypes = [vp, vp, vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int)]
     L.metos3d_residual_static.argtypes = [vp, vp, C.c_longlong, vp, vp]
     L.metos3d_residual_static_error.argtypes = []
     L.metos3d_residual_static_error.restype = C.c_char_p
     for name in declared_symbols():
         fn = getattr(L, name)
         if name not in ("metos3d_last_error", "metos3d_free", "metos3d_last_launch_count",
-                        "metos3d_residual_static_error", "metos3d_get_option"):
+                        "metos3d_residual_static_error", "metos3d_get_option",
+                        "metos3d_newton_default_options"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -270,6 +302,31 @@ class Context:
     def check_finite(self, y):
         self._sync_stream()
         return self._L.metos3d_check_finite(self._ctx, _dev_ptr(y, self.numel, "y"))
+
+    def spinup(self, y, u, nyears, tol=0.0):
+        """y <- phi(y) for up to nyears years in place; returns the residual of every year."""
+        self._sync_stream()
+        res = np.zeros(max(int(nyears), 1))
+        done = C.c_int()
+        _check(self._L.metos3d_spinup(self._ctx, _dev_ptr(y, self.numel, "y", True),
+                                      _dev_ptr(u, self.nparam, "u") if self.nparam else None, int(nyears),
+                                      float(tol), _dp(res), C.byref(done)), self._ctx)
+        return res[:done.value]
+
+    def newton_solve(self, y, u, check=True, **opts):
+        """Newton-Krylov periodic solve in place on y; returns (status, report dict)."""
+        self._sync_stream()
+        o = NewtonOptions()
+        self._L.metos3d_newton_default_options(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        rep = NewtonReport()
+        st = self._L.metos3d_newton_solve(self._ctx, _dev_ptr(y, self.numel, "y", True),
+                                          _dev_ptr(u, self.nparam, "u") if self.nparam else None,
+                                          C.byref(o), C.byref(rep))
+        if check and st not in (M3D_OK, M3D_NOT_CONVERGED):
+            _check(st, self._ctx)
+        return st, rep.to_dict()
 
     def sync(self):
         """Wait for the stream; raises Metos3dError(M3D_ERR_TIMEOUT) if the last year map timed out."""

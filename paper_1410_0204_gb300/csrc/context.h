@@ -1,0 +1,76 @@
+// context.h -- the library context shared by the translation units of libmetos3d (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "metos3d.h"
+#include "tmm_kernels.cuh"
+#include "tmm_resident.cuh"
+
+using m3d::StepParams;
+using m3d::Tile;
+
+typedef void (*step_kernel_t)(StepParams, int, const double *, double *);
+typedef void (*year_kernel_t)(StepParams, m3d::SyncParams, double *, double *, int, int);
+typedef void (*resident_kernel_t)(StepParams, m3d::ResidentParams, m3d::SyncParams, double *, double *, int, int);
+typedef void (*layout_kernel_t)(int, const double *, double *);
+
+struct ResidentKernels {
+    resident_kernel_t year, year_tri;
+    layout_kernel_t to_interleaved, from_interleaved;
+};
+
+struct m3d_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n = 0, ncol = 0, ntr = 0, nparam = 0, nsub = 1, nstep = 0, nmonth = 0, model = 0;
+    int ntiles = 0, zmax = 0, nulat = 0;
+    size_t smem_bytes = 0;
+    std::vector<void *> allocs;
+    StepParams P{};
+    m3d::SyncParams S{};
+    step_kernel_t step_kernel = nullptr;
+    year_kernel_t year_kernel = nullptr;
+    int plan = 0;                       // M3D_PLAN_*
+    int persistent_ok = 0;              // all tiles fit on the GPU at once (streaming plan)
+    int resident_ok = 0;                // ... with their month of matrices in shared memory
+    int tri_ok = 0;                     // every implicit block is the inverse of a tridiagonal matrix
+    int tri_resident_ok = 0;            // ... and the tridiagonal resident kernel fits
+    int implicit_form = 0;              // M3D_IMPLICIT_DENSE or M3D_IMPLICIT_TRIDIAGONAL (resident plan)
+    m3d::ResidentParams R{};
+    ResidentKernels rk{};
+    size_t resident_smem = 0, resident_tri_smem = 0;
+    int *status_host = nullptr;         // pinned copy of S.status
+    double *qpar = nullptr;
+    double *u_dev = nullptr;
+    double *ybuf[2] = {nullptr, nullptr};
+    double *atten = nullptr, *mfrac = nullptr;
+    double *vol = nullptr, *h = nullptr, *zc = nullptr;
+    int *cell_kl = nullptr;
+    double *red_part = nullptr, *red_out = nullptr, *red_host = nullptr;
+    cudaGraphExec_t year_graph = nullptr;
+    int year_result_buf = 0;
+    long long last_launches = 0;
+    std::string err;
+};
+
+// Record a failure on c (or for metos3d_init when c is null) and return s.
+m3d_status fail(m3d_ctx *c, m3d_status s, const char *fmt, ...);
+
+#define CUDA_OR_FAIL(ctx, call)                                                              \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((ctx), M3D_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Internal entry points shared between translation units.
+// The year map from the device state y0 to y1 with the parameters already in c->u_dev.
+m3d_status m3d_year_device(m3d_ctx *c, const double *y0, double *y1);
+// Copy nparam parameters into c->u_dev (kind: cudaMemcpyDeviceToDevice or HostToDevice).
+m3d_status m3d_set_params(m3d_ctx *c, const double *u, cudaMemcpyKind kind);
+// Device allocation owned by the context (freed by metos3d_free).
+cudaError_t m3d_alloc(m3d_ctx *c, void **p, size_t bytes);

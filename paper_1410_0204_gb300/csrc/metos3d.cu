@@ -17,9 +17,8 @@
 #include "metos3d.h"
 #include "tmm_kernels.cuh"
 #include "tmm_resident.cuh"
+#include "context.h"
 
-using m3d::StepParams;
-using m3d::Tile;
 
 // ------------------------------------------------------------------------------ kernels
 namespace {
@@ -164,8 +163,6 @@ __global__ void k_bgc_column(int model, double dt, double insol, double ice, int
     }
 }
 
-typedef void (*step_kernel_t)(StepParams, int, const double *, double *);
-typedef void (*year_kernel_t)(StepParams, m3d::SyncParams, double *, double *, int, int);
 
 year_kernel_t pick_year_kernel(int model, int ntr)
 {
@@ -183,13 +180,6 @@ year_kernel_t pick_year_kernel(int model, int ntr)
     }
 }
 
-typedef void (*resident_kernel_t)(StepParams, m3d::ResidentParams, m3d::SyncParams, double *, double *, int, int);
-typedef void (*layout_kernel_t)(int, const double *, double *);
-
-struct ResidentKernels {
-    resident_kernel_t year, year_tri;
-    layout_kernel_t to_interleaved, from_interleaved;
-};
 
 template <int NTR, int MODEL>
 ResidentKernels resident_kernels()
@@ -230,46 +220,9 @@ step_kernel_t pick_step_kernel(int model, int ntr)
     }
 }
 
-thread_local std::string g_init_error;
-
 }  // namespace
 
-// ------------------------------------------------------------------------------ context
-struct m3d_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int n = 0, ncol = 0, ntr = 0, nparam = 0, nsub = 1, nstep = 0, nmonth = 0, model = 0;
-    int ntiles = 0, zmax = 0, nulat = 0;
-    size_t smem_bytes = 0;
-    std::vector<void *> allocs;
-    StepParams P{};
-    m3d::SyncParams S{};
-    step_kernel_t step_kernel = nullptr;
-    year_kernel_t year_kernel = nullptr;
-    int plan = 0;                       // M3D_PLAN_*
-    int persistent_ok = 0;              // all tiles fit on the GPU at once (streaming plan)
-    int resident_ok = 0;                // ... with their month of matrices in shared memory
-    int tri_ok = 0;                     // every implicit block is the inverse of a tridiagonal matrix
-    int tri_resident_ok = 0;            // ... and the tridiagonal resident kernel fits
-    int implicit_form = 0;              // M3D_IMPLICIT_DENSE or M3D_IMPLICIT_TRIDIAGONAL (resident plan)
-    m3d::ResidentParams R{};
-    ResidentKernels rk{};
-    size_t resident_smem = 0, resident_tri_smem = 0;
-    int *status_host = nullptr;         // pinned copy of S.status
-    double *qpar = nullptr;
-    double *u_dev = nullptr;
-    double *ybuf[2] = {nullptr, nullptr};
-    double *atten = nullptr, *mfrac = nullptr;
-    double *vol = nullptr, *h = nullptr, *zc = nullptr;
-    int *cell_kl = nullptr;
-    double *red_part = nullptr, *red_out = nullptr, *red_host = nullptr;
-    cudaGraphExec_t year_graph = nullptr;
-    int year_result_buf = 0;
-    long long last_launches = 0;
-    std::string err;
-};
-
-namespace {
+thread_local std::string g_init_error;
 
 m3d_status fail(m3d_ctx *c, m3d_status s, const char *fmt, ...)
 {
@@ -283,12 +236,7 @@ m3d_status fail(m3d_ctx *c, m3d_status s, const char *fmt, ...)
     return s;
 }
 
-#define CUDA_OR_FAIL(ctx, call)                                                              \
-    do {                                                                                     \
-        cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess)                                                               \
-            return fail((ctx), M3D_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
+namespace {
 
 template <typename T>
 cudaError_t upload(m3d_ctx *c, T **dst, const T *src, size_t count)
@@ -1241,3 +1189,29 @@ m3d_status metos3d_bgc(int model_id, double t, double dt, double lat, double ins
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------ internal
+m3d_status m3d_set_params(m3d_ctx *c, const double *u, cudaMemcpyKind kind)
+{
+    if (c->nparam > 0)
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_dev, u, sizeof(double) * c->nparam, kind, c->stream));
+    return M3D_OK;
+}
+
+m3d_status m3d_year_device(m3d_ctx *c, const double *y0, double *y1)
+{
+    size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    if (c->plan == M3D_PLAN_GRAPH && !c->year_graph) {
+        m3d_status st = build_year_graph(c);
+        if (st != M3D_OK) return st;
+    }
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], y0, len, cudaMemcpyDeviceToDevice, c->stream));
+    return run_year_from_ybuf(c, y1, cudaMemcpyDeviceToDevice);
+}
+
+cudaError_t m3d_alloc(m3d_ctx *c, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e == cudaSuccess) c->allocs.push_back(*p);
+    return e;
+}
