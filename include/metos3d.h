@@ -134,6 +134,18 @@ m3d_status metos3d_year_map_host(m3d_ctx *ctx, const double *y0_host, double *y1
                                  const double *u_host);
 
 /*
+ * The year map and its tangent-linear map (Section 6 names exact Jacobian-vector products
+ * by algorithmic differentiation as the alternative to finite differences):
+ * phi_out = phi(y0) and jv_out = phi'(y0) v in one pass over the year, the state and its
+ * direction advanced together through every step, so each matrix entry is read once for
+ * both.  The source term's tangent is the model code evaluated on dual numbers.
+ * PO4-DOP only (M3D_ERR_UNSUPPORTED otherwise).  Device arrays [ntracer][n]; u: device
+ * [nparam].  Asynchronous.
+ */
+m3d_status metos3d_year_tangent(m3d_ctx *ctx, const double *y0, const double *v, const double *u,
+                                double *phi_out, double *jv_out);
+
+/*
  * Diagnostics, synchronous, result on the host:
  *   metos3d_mass:     sum over tracers and cells of vol_i y_{tr,i} (total tracer mass);
  *   metos3d_residual: || a - b ||_2 over all ntracer * n entries (the paper's spin-up and
@@ -244,7 +256,8 @@ m3d_status metos3d_spinup(m3d_ctx *ctx, double *y, const double *u, int nyears, 
  * orthogonalisation to the Eisenstat-Walker tolerance (choice 2: eta_0 = 0.3,
  * gamma = 0.9, alpha = (1+sqrt 5)/2, safeguarded, kept within [0.5 tol/||F||, 0.9]).
  * Jacobian-vector products are finite differences, J v = v - (phi(y + h v) - phi(y)) / h
- * with h = fd_eps ||y|| / ||v||.  phi conserves the total mass, so I - phi' is singular and
+ * with h = fd_eps ||y|| / ||v|| (M3D_JV_FD), or exact, J v = v - phi'(y) v by the tangent
+ * year map (M3D_JV_TANGENT, see metos3d_year_tangent).  phi conserves the total mass, so I - phi' is singular and
  * the periodic solution is unique only for a given mass: each Newton step is projected on
  * the zero-mass directions, and the solution keeps the mass of the initial state.
  * y: device [ntracer][n], initial guess on entry and solution on exit; u: device [nparam];

@@ -47,6 +47,13 @@ def lib():
         L.oracle_step.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int, dp]
         L.oracle_year_map.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int]
         L.oracle_steps.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int]
+        L.oracle_bgc_tangent.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                         C.c_double, C.c_double, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp,
+                                         C.c_int, dp, C.c_int]
+        L.oracle_year_tangent.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, dp, dp, dp, dp, dp, C.c_int, C.c_int]
+        L.oracle_bgc_adjoint.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, dp, dp, dp,
+                                         dp, dp, C.c_int, dp, dp, C.c_int]
+        L.oracle_year_adjoint.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, dp, dp, dp]
         L.oracle_set_threads.argtypes = [C.c_int]
         # one thread unless asked otherwise: the oracle's reference mode is single-threaded
         L.oracle_set_threads(int(os.environ.get("M3D_ORACLE_THREADS", "1")))
@@ -145,3 +152,62 @@ def year_map(P: Problem, y0, u, model=MODEL_NDOP, nsub=1):
     if rc != 0:
         raise ValueError("oracle_year_map failed")
     return out
+
+
+def bgc_tangent(y, dy, h, d, u, t=0.0, dt=1.0 / 2880, lat=0.0, insol=0.0, dayfrac=0.5, ice=0.0,
+                model=MODEL_NDOP, nsub=1):
+    """The model interface and its tangent along dy on one column; returns (ybgc, dybgc)."""
+    y = _f64(y)
+    dy = _f64(dy)
+    ntr, nl = y.shape
+    h, d, u = _f64(h), _f64(d), _f64(u)
+    out = np.zeros_like(y)
+    dout = np.zeros_like(y)
+    rc = lib().oracle_bgc_tangent(model, t, dt, lat, insol, dayfrac, ice, 0.0, ntr, nl, _dp(h), _dp(d),
+                                  _dp(y), _dp(dy), _dp(out), _dp(dout), u.shape[0], _dp(u), nsub)
+    if rc != 0:
+        raise ValueError("oracle_bgc_tangent rejected its arguments")
+    return out, dout
+
+
+def year_tangent(P: Problem, y0, v, u, model=MODEL_NDOP, nsub=1):
+    """(phi(y0), phi'(y0) v)."""
+    y0 = _f64(y0)
+    v = _f64(v)
+    u = _f64(u)
+    y1 = np.empty_like(y0)
+    jv = np.empty_like(y0)
+    rc = lib().oracle_year_tangent(C.byref(P.s), model, y0.shape[0], _dp(y0), _dp(v), _dp(y1), _dp(jv), _dp(u),
+                                   u.shape[0], nsub)
+    if rc != 0:
+        raise ValueError("oracle_year_tangent failed")
+    return y1, jv
+
+
+def bgc_adjoint(y, ybgc_bar, h, d, u, dt=1.0 / 2880, insol=0.0, ice=0.0, model=MODEL_NDOP, nsub=1):
+    """Reverse of the model interface: returns (ybar, ubar) for the cotangent ybgc_bar."""
+    y = _f64(y)
+    yb_in = _f64(ybgc_bar)
+    ntr, nl = y.shape
+    h, d, u = _f64(h), _f64(d), _f64(u)
+    ybar = np.zeros_like(y)
+    ubar = np.zeros(u.shape[0])
+    rc = lib().oracle_bgc_adjoint(model, dt, insol, ice, ntr, nl, _dp(h), _dp(d), _dp(y), _dp(yb_in), _dp(ybar),
+                                  u.shape[0], _dp(u), _dp(ubar), nsub)
+    if rc != 0:
+        raise ValueError("oracle_bgc_adjoint rejected its arguments")
+    return ybar, ubar
+
+
+def year_adjoint(P: Problem, y0, u, ybar1, model=MODEL_NDOP, nsub=1):
+    """(phi_y^T ybar1, phi_u^T ybar1) for y1 = phi(y0; u)."""
+    y0 = _f64(y0)
+    u = _f64(u)
+    yb1 = _f64(ybar1)
+    ybar0 = np.empty_like(y0)
+    ubar = np.zeros(u.shape[0])
+    rc = lib().oracle_year_adjoint(C.byref(P.s), model, y0.shape[0], _dp(y0), _dp(u), u.shape[0], nsub, _dp(yb1),
+                                   _dp(ybar0), _dp(ubar))
+    if rc != 0:
+        raise ValueError("oracle_year_adjoint failed")
+    return ybar0, ubar

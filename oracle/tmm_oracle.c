@@ -316,3 +316,363 @@ int oracle_set_threads(int nthreads)
     return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------------------------
+ * Tangent-linear model.  Section 6 names exact Jacobian-vector products (by algorithmic
+ * differentiation) as the alternative to finite differences; here the derivative of the
+ * PO4-DOP equations of Section 2.2.1 is written out by hand:
+ *   df_k  = alpha K_N / (N_k + K_N)^2 I_k / (I_k + K_I) dN_k
+ *   dq1_k = -df_k + lambda dDOP_k,   dq2_k = sigma df_k - lambda dDOP_k      (euphotic)
+ *   dE    = (1 - sigma) sum_k df_k h_k,   dF(z) = dE (z / z_eu)^(-b)
+ *   dq1_k = (dF(z_top) - dF(z_bot)) / h_k + lambda dDOP_k, dq2_k = -lambda dDOP_k (aphotic)
+ * and each internal Euler step y <- y + ds q(y) has the tangent dy <- dy + ds dq(y; dy).
+ * --------------------------------------------------------------------------------- */
+static void ndop_q_tangent(int nlayer, const double *h, const double *d, double insol, double ice,
+                           const double *N, const double *DOP, const double *dN, const double *dDOP,
+                           const double *u, double *qN, double *qD, double *dqN, double *dqD)
+{
+    const double sigma_par = 0.4;
+    double kw = u[0], alpha = u[1] * 360.0, sigma = u[2], lambda = u[3];
+    double KN = u[4], KI = u[5], b = u[6];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double E = 0.0, dE = 0.0, zeu = 0.0;
+    for (int k = 0; k < neu; k++) {
+        double I = insol * sigma_par * (1.0 - ice) * exp(-d[k] * kw);
+        double LF = I / (I + KI);
+        double f = alpha * (N[k] / (N[k] + KN)) * LF;
+        double df = alpha * (KN / ((N[k] + KN) * (N[k] + KN))) * LF * dN[k];
+        qN[k] = -f + lambda * DOP[k];
+        qD[k] = sigma * f - lambda * DOP[k];
+        dqN[k] = -df + lambda * dDOP[k];
+        dqD[k] = sigma * df - lambda * dDOP[k];
+        E += (1.0 - sigma) * f * h[k];
+        dE += (1.0 - sigma) * df * h[k];
+        zeu += h[k];
+    }
+    double ztop = zeu;
+    for (int k = neu; k < nlayer; k++) {
+        double zbot = ztop + h[k];
+        double pt = pow(ztop / zeu, -b);
+        double pb = (k == nlayer - 1) ? 0.0 : pow(zbot / zeu, -b);
+        qN[k] = (E * pt - E * pb) / h[k] + lambda * DOP[k];
+        qD[k] = -lambda * DOP[k];
+        dqN[k] = (dE * pt - dE * pb) / h[k] + lambda * dDOP[k];
+        dqD[k] = -lambda * dDOP[k];
+        ztop = zbot;
+    }
+    if (nlayer <= neu) {
+        qN[nlayer - 1] += E / h[nlayer - 1];
+        dqN[nlayer - 1] += dE / h[nlayer - 1];
+    }
+}
+
+/* The model interface and its tangent: ybgc as oracle_bgc, dybgc its derivative along dy. */
+int oracle_bgc_tangent(int model, double t, double dt, double lat, double insol, double dayfrac,
+                       double ice, double wind, int ntracer, int nlayer, const double *h,
+                       const double *d, const double *y, const double *dy, double *ybgc,
+                       double *dybgc, int nparam, const double *u, int nsub)
+{
+    (void)t; (void)lat; (void)dayfrac; (void)wind;
+    if (nlayer < 1 || nlayer > ORACLE_MAX_LAYER || nsub < 1) return -1;
+    if (model == ORACLE_MODEL_NONE) {
+        for (int i = 0; i < ntracer * nlayer; i++) { ybgc[i] = 0.0; dybgc[i] = 0.0; }
+        return 0;
+    }
+    if (model != ORACLE_MODEL_NDOP || ntracer != 2 || nparam != 7) return -1;
+    double ys[2 * ORACLE_MAX_LAYER], dys[2 * ORACLE_MAX_LAYER];
+    double qN[ORACLE_MAX_LAYER], qD[ORACLE_MAX_LAYER], dqN[ORACLE_MAX_LAYER], dqD[ORACLE_MAX_LAYER];
+    memcpy(ys, y, sizeof(double) * 2 * nlayer);
+    memcpy(dys, dy, sizeof(double) * 2 * nlayer);
+    double ds = dt / nsub;
+    for (int s = 0; s < nsub; s++) {
+        ndop_q_tangent(nlayer, h, d, insol, ice, ys, ys + nlayer, dys, dys + nlayer, u, qN, qD, dqN, dqD);
+        for (int k = 0; k < nlayer; k++) {
+            ys[k] += ds * qN[k];
+            ys[nlayer + k] += ds * qD[k];
+            dys[k] += ds * dqN[k];
+            dys[nlayer + k] += ds * dqD[k];
+        }
+    }
+    for (int i = 0; i < 2 * nlayer; i++) {
+        ybgc[i] = ys[i] - y[i];
+        dybgc[i] = dys[i] - dy[i];
+    }
+    return 0;
+}
+
+/* One TMM step and its tangent: y_out as oracle_step, dy_out = A_imp (A_exp dy + dq). */
+int oracle_step_tangent(const oracle_problem *P, int model, int ntracer, int j, const double *y,
+                        const double *dy, double *y_out, double *dy_out, const double *u, int nparam,
+                        int nsub, double *work, double *dwork)
+{
+    int n = P->n;
+    int m0, m1;
+    double w;
+    oracle_month_weights(j, P->nstep, P->nmonth, &m0, &m1, &w);
+    double t = (double)j / P->nstep;
+    double dt = 1.0 / P->nstep;
+    const double *a0 = P->exp_val + (size_t)m0 * P->nnz;
+    const double *a1 = P->exp_val + (size_t)m1 * P->nnz;
+    const double *b0 = P->imp_blk + (size_t)m0 * P->s_imp;
+    const double *b1 = P->imp_blk + (size_t)m1 * P->s_imp;
+    double *z = work, *dz = dwork;
+    int bad = 0;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; i++) {
+        for (int tr = 0; tr < ntracer; tr++) {
+            double s = 0.0, ds = 0.0;
+            for (int p = P->rowptr[i]; p < P->rowptr[i + 1]; p++) {
+                double a = (1.0 - w) * a0[p] + w * a1[p];
+                s += a * y[(size_t)tr * n + P->colidx[p]];
+                ds += a * dy[(size_t)tr * n + P->colidx[p]];
+            }
+            z[(size_t)tr * n + i] = s;
+            dz[(size_t)tr * n + i] = ds;
+        }
+    }
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int c = 0; c < P->ncol; c++) {
+        int s0 = P->col_start[c];
+        int L = P->col_start[c + 1] - s0;
+        double ycol[ORACLE_MAX_LAYER * ORACLE_MAX_TRACER], dycol[ORACLE_MAX_LAYER * ORACLE_MAX_TRACER];
+        double dq[ORACLE_MAX_LAYER * ORACLE_MAX_TRACER], ddq[ORACLE_MAX_LAYER * ORACLE_MAX_TRACER];
+        if (L > ORACLE_MAX_LAYER || ntracer > ORACLE_MAX_TRACER) { bad |= 1; continue; }
+        for (int tr = 0; tr < ntracer; tr++)
+            for (int k = 0; k < L; k++) {
+                ycol[tr * L + k] = y[(size_t)tr * n + s0 + k];
+                dycol[tr * L + k] = dy[(size_t)tr * n + s0 + k];
+            }
+        double dayfrac;
+        double insol = oracle_insolation(P->lat[c], t, &dayfrac);
+        if (oracle_bgc_tangent(model, t, dt, P->lat[c], insol, dayfrac, 0.0, 0.0, ntracer, L, P->h + s0,
+                               P->zc + s0, ycol, dycol, dq, ddq, nparam, u, nsub) != 0) {
+            bad |= 1;
+            continue;
+        }
+        for (int tr = 0; tr < ntracer; tr++)
+            for (int k = 0; k < L; k++) {
+                z[(size_t)tr * n + s0 + k] += dq[tr * L + k];
+                dz[(size_t)tr * n + s0 + k] += ddq[tr * L + k];
+            }
+        const double *B0 = b0 + P->blk_off[c];
+        const double *B1 = b1 + P->blk_off[c];
+        for (int tr = 0; tr < ntracer; tr++) {
+            for (int r = 0; r < L; r++) {
+                double s = 0.0, ds = 0.0;
+                for (int k = 0; k < L; k++) {
+                    double bb = (1.0 - w) * B0[r * L + k] + w * B1[r * L + k];
+                    s += bb * z[(size_t)tr * n + s0 + k];
+                    ds += bb * dz[(size_t)tr * n + s0 + k];
+                }
+                y_out[(size_t)tr * n + s0 + r] = s;
+                dy_out[(size_t)tr * n + s0 + r] = ds;
+            }
+        }
+    }
+    return bad ? -1 : 0;
+}
+
+/* The year map and its tangent: y1 = phi(y0), dy1 = phi'(y0) dy0. */
+int oracle_year_tangent(const oracle_problem *P, int model, int ntracer, const double *y0,
+                        const double *dy0, double *y1, double *dy1, const double *u, int nparam, int nsub)
+{
+    size_t len = (size_t)ntracer * P->n;
+    double *a = (double *)malloc(sizeof(double) * len), *b = (double *)malloc(sizeof(double) * len);
+    double *da = (double *)malloc(sizeof(double) * len), *db = (double *)malloc(sizeof(double) * len);
+    double *w1 = (double *)malloc(sizeof(double) * len), *w2 = (double *)malloc(sizeof(double) * len);
+    int rc = (a && b && da && db && w1 && w2) ? 0 : -2;
+    if (rc == 0) {
+        memcpy(a, y0, sizeof(double) * len);
+        memcpy(da, dy0, sizeof(double) * len);
+        for (int j = 0; j < P->nstep && rc == 0; j++) {
+            rc = oracle_step_tangent(P, model, ntracer, j, a, da, b, db, u, nparam, nsub, w1, w2);
+            double *t1 = a; a = b; b = t1;
+            double *t2 = da; da = db; db = t2;
+        }
+        memcpy(y1, a, sizeof(double) * len);
+        memcpy(dy1, da, sizeof(double) * len);
+    }
+    free(a); free(b); free(da); free(db); free(w1); free(w2);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Adjoint model (reverse mode), for gradients with respect to the state and to the model
+ * parameters u (the parameter optimisation named in Sections 1 and 9).  For one step
+ * y_{j+1} = B (A y_j + dq(y_j, u)) and a cotangent ybar_{j+1}:
+ *   zbar = B^T ybar_{j+1},  ybar_j = A^T zbar + (d dq / dy)^T zbar,  ubar += (d dq / du)^T zbar.
+ * dq is the increment of nsub explicit Euler steps; its reverse runs the internal steps
+ * backwards: ybar^(s) = ybar^(s+1) + ds (dq/dy)^T ybar^(s+1), ubar += ds (dq/du)^T ybar^(s+1).
+ * --------------------------------------------------------------------------------- */
+
+/* Reverse of one evaluation of the PO4-DOP q at (N, DOP): given cotangents qbN, qbD of
+ * (qN, qD), add the cotangents of N, DOP into Nb, Db and of u into ub. */
+static void ndop_q_adjoint(int nlayer, const double *h, const double *d, double insol, double ice,
+                           const double *N, const double *DOP, const double *u, const double *qbN,
+                           const double *qbD, double *Nb, double *Db, double *ub)
+{
+    const double sigma_par = 0.4;
+    double kw = u[0], alpha = u[1] * 360.0, sigma = u[2], lambda = u[3];
+    double KN = u[4], KI = u[5], b = u[6];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double f[ORACLE_MAX_LAYER], I[ORACLE_MAX_LAYER];
+    double E = 0.0, zeu = 0.0, sumfh = 0.0;
+    for (int k = 0; k < neu; k++) {
+        I[k] = insol * sigma_par * (1.0 - ice) * exp(-d[k] * kw);
+        f[k] = alpha * (N[k] / (N[k] + KN)) * (I[k] / (I[k] + KI));
+        sumfh += f[k] * h[k];
+        zeu += h[k];
+    }
+    E = (1.0 - sigma) * sumfh;
+    /* aphotic layers and the bottom deposit: contributions to Ebar, DOP, lambda, b */
+    double Eb = 0.0;
+    double ztop = zeu;
+    for (int k = neu; k < nlayer; k++) {
+        double zbot = ztop + h[k];
+        double pt = pow(ztop / zeu, -b);
+        double pb = (k == nlayer - 1) ? 0.0 : pow(zbot / zeu, -b);
+        double dpt = -log(ztop / zeu) * pt;            /* d pt / d b */
+        double dpb = (k == nlayer - 1) ? 0.0 : -log(zbot / zeu) * pb;
+        Eb += qbN[k] * (pt - pb) / h[k];
+        ub[6] += qbN[k] * E * (dpt - dpb) / h[k];
+        Db[k] += lambda * (qbN[k] - qbD[k]);
+        ub[3] += (qbN[k] - qbD[k]) * DOP[k];
+        ztop = zbot;
+    }
+    if (nlayer <= neu) Eb += qbN[nlayer - 1] / h[nlayer - 1];
+    /* E = (1 - sigma) sum f_k h_k */
+    ub[2] += -Eb * sumfh;
+    for (int k = 0; k < neu; k++) {
+        double fb = Eb * (1.0 - sigma) * h[k] - qbN[k] + sigma * qbD[k];
+        ub[2] += qbD[k] * f[k];
+        Db[k] += lambda * (qbN[k] - qbD[k]);
+        ub[3] += (qbN[k] - qbD[k]) * DOP[k];
+        /* f = alpha' N/(N+KN) I/(I+KI), alpha' = 360 alpha, I = I_s exp(-d kw) */
+        double M = N[k] / (N[k] + KN), LF = I[k] / (I[k] + KI);
+        ub[1] += fb * 360.0 * M * LF;
+        Nb[k] += fb * alpha * LF * KN / ((N[k] + KN) * (N[k] + KN));
+        ub[4] += fb * alpha * LF * (-N[k] / ((N[k] + KN) * (N[k] + KN)));
+        ub[5] += fb * alpha * M * (-I[k] / ((I[k] + KI) * (I[k] + KI)));
+        ub[0] += fb * alpha * M * (KI / ((I[k] + KI) * (I[k] + KI))) * (-d[k] * I[k]);
+    }
+}
+
+/* Reverse of the model interface: given ybgc_bar (cotangent of ybgc), add the cotangent of
+ * y into ybar and of u into ubar (both accumulated). */
+int oracle_bgc_adjoint(int model, double dt, double insol, double ice, int ntracer, int nlayer,
+                       const double *h, const double *d, const double *y, const double *ybgc_bar,
+                       double *ybar, int nparam, const double *u, double *ubar, int nsub)
+{
+    if (nlayer < 1 || nlayer > ORACLE_MAX_LAYER || nsub < 1 || nsub > 64) return -1;
+    if (model == ORACLE_MODEL_NONE) return 0;
+    if (model != ORACLE_MODEL_NDOP || ntracer != 2 || nparam != 7) return -1;
+    /* forward internal states y^(0..nsub-1) */
+    static __thread double st[64][2 * ORACLE_MAX_LAYER];
+    double qN[ORACLE_MAX_LAYER], qD[ORACLE_MAX_LAYER];
+    double ds = dt / nsub;
+    memcpy(st[0], y, sizeof(double) * 2 * nlayer);
+    for (int s = 0; s + 1 < nsub; s++) {
+        ndop_q(nlayer, h, d, insol, ice, st[s], st[s] + nlayer, u, qN, qD);
+        for (int k = 0; k < nlayer; k++) {
+            st[s + 1][k] = st[s][k] + ds * qN[k];
+            st[s + 1][nlayer + k] = st[s][nlayer + k] + ds * qD[k];
+        }
+    }
+    /* ybgc = y^(nsub) - y^(0): ybar^(nsub) = ybgc_bar, and -ybgc_bar goes to y^(0) */
+    double yb[2 * ORACLE_MAX_LAYER], qbN[ORACLE_MAX_LAYER], qbD[ORACLE_MAX_LAYER];
+    memcpy(yb, ybgc_bar, sizeof(double) * 2 * nlayer);
+    for (int s = nsub - 1; s >= 0; s--) {
+        for (int k = 0; k < nlayer; k++) { qbN[k] = ds * yb[k]; qbD[k] = ds * yb[nlayer + k]; }
+        ndop_q_adjoint(nlayer, h, d, insol, ice, st[s], st[s] + nlayer, u, qbN, qbD, yb, yb + nlayer, ubar);
+    }
+    for (int i = 0; i < 2 * nlayer; i++) ybar[i] += yb[i] - ybgc_bar[i];
+    return 0;
+}
+
+/* Reverse of one TMM step at state y (step j): ybar_in = cotangent of y_{j+1};
+ * ybar_out = cotangent of y_j; ubar accumulated.  work: [ntracer][n] scratch. */
+int oracle_step_adjoint(const oracle_problem *P, int model, int ntracer, int j, const double *y,
+                        const double *ybar_in, double *ybar_out, const double *u, int nparam,
+                        double *ubar, int nsub, double *zbar)
+{
+    int n = P->n;
+    int m0, m1;
+    double w;
+    oracle_month_weights(j, P->nstep, P->nmonth, &m0, &m1, &w);
+    double t = (double)j / P->nstep;
+    double dt = 1.0 / P->nstep;
+    const double *a0 = P->exp_val + (size_t)m0 * P->nnz;
+    const double *a1 = P->exp_val + (size_t)m1 * P->nnz;
+    const double *b0 = P->imp_blk + (size_t)m0 * P->s_imp;
+    const double *b1 = P->imp_blk + (size_t)m1 * P->s_imp;
+    /* zbar = B^T ybar_in */
+    for (int c = 0; c < P->ncol; c++) {
+        int s0 = P->col_start[c], L = P->col_start[c + 1] - s0;
+        const double *B0 = b0 + P->blk_off[c], *B1 = b1 + P->blk_off[c];
+        for (int tr = 0; tr < ntracer; tr++)
+            for (int k = 0; k < L; k++) {
+                double s = 0.0;
+                for (int r = 0; r < L; r++) {
+                    double bb = (1.0 - w) * B0[r * L + k] + w * B1[r * L + k];
+                    s += bb * ybar_in[(size_t)tr * n + s0 + r];
+                }
+                zbar[(size_t)tr * n + s0 + k] = s;
+            }
+    }
+    /* ybar_out = A^T zbar */
+    for (size_t i = 0; i < (size_t)ntracer * n; i++) ybar_out[i] = 0.0;
+    for (int i = 0; i < n; i++)
+        for (int p = P->rowptr[i]; p < P->rowptr[i + 1]; p++) {
+            double a = (1.0 - w) * a0[p] + w * a1[p];
+            for (int tr = 0; tr < ntracer; tr++)
+                ybar_out[(size_t)tr * n + P->colidx[p]] += a * zbar[(size_t)tr * n + i];
+        }
+    /* + (d dq/dy)^T zbar, ubar += (d dq/du)^T zbar, column by column */
+    for (int c = 0; c < P->ncol; c++) {
+        int s0 = P->col_start[c], L = P->col_start[c + 1] - s0;
+        double ycol[ORACLE_MAX_LAYER * ORACLE_MAX_TRACER], zb[ORACLE_MAX_LAYER * ORACLE_MAX_TRACER];
+        double yb[ORACLE_MAX_LAYER * ORACLE_MAX_TRACER];
+        if (L > ORACLE_MAX_LAYER || ntracer > ORACLE_MAX_TRACER) return -1;
+        for (int tr = 0; tr < ntracer; tr++)
+            for (int k = 0; k < L; k++) {
+                ycol[tr * L + k] = y[(size_t)tr * n + s0 + k];
+                zb[tr * L + k] = zbar[(size_t)tr * n + s0 + k];
+                yb[tr * L + k] = 0.0;
+            }
+        double dayfrac;
+        double insol = oracle_insolation(P->lat[c], t, &dayfrac);
+        if (oracle_bgc_adjoint(model, dt, insol, 0.0, ntracer, L, P->h + s0, P->zc + s0, ycol, zb, yb, nparam, u,
+                               ubar, nsub) != 0)
+            return -1;
+        for (int tr = 0; tr < ntracer; tr++)
+            for (int k = 0; k < L; k++) ybar_out[(size_t)tr * n + s0 + k] += yb[tr * L + k];
+    }
+    return 0;
+}
+
+/* Gradient of the year map: given ybar1 (cotangent of y1 = phi(y0; u)), ybar0 = phi_y^T ybar1
+ * and ubar = phi_u^T ybar1.  Stores every state of the year (plain and memory hungry). */
+int oracle_year_adjoint(const oracle_problem *P, int model, int ntracer, const double *y0,
+                        const double *u, int nparam, int nsub, const double *ybar1, double *ybar0,
+                        double *ubar)
+{
+    size_t len = (size_t)ntracer * P->n;
+    double *states = (double *)malloc(sizeof(double) * len * (size_t)P->nstep);
+    double *work = (double *)malloc(sizeof(double) * len);
+    double *ya = (double *)malloc(sizeof(double) * len), *yb = (double *)malloc(sizeof(double) * len);
+    int rc = (states && work && ya && yb) ? 0 : -2;
+    if (rc == 0) {
+        memcpy(states, y0, sizeof(double) * len);
+        for (int j = 0; j + 1 < P->nstep && rc == 0; j++)
+            rc = oracle_step(P, model, ntracer, j, states + len * j, states + len * (j + 1), u, nparam, nsub, work);
+        for (int k = 0; k < nparam; k++) ubar[k] = 0.0;
+        memcpy(ya, ybar1, sizeof(double) * len);
+        for (int j = P->nstep - 1; j >= 0 && rc == 0; j--) {
+            rc = oracle_step_adjoint(P, model, ntracer, j, states + len * j, ya, yb, u, nparam, ubar, nsub, work);
+            double *tmp = ya; ya = yb; yb = tmp;
+        }
+        memcpy(ybar0, ya, sizeof(double) * len);
+    }
+    free(states); free(work); free(ya); free(yb);
+    return rc;
+}

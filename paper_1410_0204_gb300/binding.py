@@ -137,6 +137,7 @@ def load(build_if_missing: bool = False):
     L.metos3d_newton_default_options.restype = None
     L.metos3d_newton_solve.argtypes = [vp, vp, vp, C.POINTER(NewtonOptions), C.POINTER(NewtonReport)]
     L.metos3d_spinup.argtypes = [vp, vp, vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int)]
+    L.metos3d_year_tangent.argtypes = [vp, vp, vp, vp, vp, vp]
     L.metos3d_residual_static.argtypes = [vp, vp, C.c_longlong, vp, vp]
     L.metos3d_residual_static_error.argtypes = []
     L.metos3d_residual_static_error.restype = C.c_char_p
@@ -267,6 +268,15 @@ class Context:
                                         _dev_ptr(y1, self.numel, "y1", True),
                                         _dev_ptr(u, self.nparam, "u") if self.nparam else None), self._ctx)
         return y1
+
+    def year_tangent(self, y0, v, u, phi_out, jv_out):
+        """phi(y0) into phi_out and phi'(y0) v into jv_out (CUDA tensors)."""
+        self._sync_stream()
+        _check(self._L.metos3d_year_tangent(self._ctx, _dev_ptr(y0, self.numel, "y0"), _dev_ptr(v, self.numel, "v"),
+                                            _dev_ptr(u, self.nparam, "u") if self.nparam else None,
+                                            _dev_ptr(phi_out, self.numel, "phi_out", True),
+                                            _dev_ptr(jv_out, self.numel, "jv_out", True)), self._ctx)
+        return phi_out, jv_out
 
     def year_map_host(self, y0, u, out=None):
         self._sync_stream()

@@ -23,6 +23,18 @@ struct ResidentKernels {
     layout_kernel_t to_interleaved, from_interleaved;
 };
 
+// One way of running the year: the forward model, or the model with its tangent (twice the
+// tracers).  Kernels, their shared memory, and which plans fit on the GPU.
+struct YearVariant {
+    int ntr = 0;
+    int model = 0;                      // m3d::kModel*
+    step_kernel_t step = nullptr;
+    year_kernel_t year = nullptr;
+    ResidentKernels rk{};
+    size_t smem = 0, resident_smem = 0, resident_tri_smem = 0;
+    int persistent_ok = 0, resident_ok = 0, tri_resident_ok = 0;
+};
+
 struct m3d_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -43,6 +55,9 @@ struct m3d_ctx {
     m3d::ResidentParams R{};
     ResidentKernels rk{};
     size_t resident_smem = 0, resident_tri_smem = 0;
+    YearVariant tan;                    // the model with its tangent (PO4-DOP only)
+    m3d::ResidentParams R_tan{};        // resident layout of the tangent (its own Thomas chains)
+    int tan_ok = 0;
     int *status_host = nullptr;         // pinned copy of S.status
     double *qpar = nullptr;
     double *u_dev = nullptr;
@@ -72,5 +87,7 @@ m3d_status fail(m3d_ctx *c, m3d_status s, const char *fmt, ...);
 m3d_status m3d_year_device(m3d_ctx *c, const double *y0, double *y1);
 // Copy nparam parameters into c->u_dev (kind: cudaMemcpyDeviceToDevice or HostToDevice).
 m3d_status m3d_set_params(m3d_ctx *c, const double *u, cudaMemcpyKind kind);
+// phi(y0) and phi'(y0) v with the parameters already in c->u_dev.
+m3d_status m3d_year_tangent_device(m3d_ctx *c, const double *y0, const double *v, double *phi, double *jv);
 // Device allocation owned by the context (freed by metos3d_free).
 cudaError_t m3d_alloc(m3d_ctx *c, void **p, size_t bytes);

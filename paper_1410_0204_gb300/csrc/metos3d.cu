@@ -204,6 +204,18 @@ ResidentKernels pick_resident_kernels(int model, int ntr)
     }
 }
 
+// The model with its tangent: the state (N, DOP, dN, dDOP) as four tracers.
+YearVariant tangent_kernels()
+{
+    YearVariant V;
+    V.ntr = 4;
+    V.model = m3d::kModelNdopTangent;
+    V.step = k_step<4, m3d::kModelNdopTangent>;
+    V.year = k_year<4, m3d::kModelNdopTangent>;
+    V.rk = resident_kernels<4, m3d::kModelNdopTangent>();
+    return V;
+}
+
 step_kernel_t pick_step_kernel(int model, int ntr)
 {
     if (model == m3d::kModelNdop) return ntr == 2 ? k_step<2, m3d::kModelNdop> : nullptr;
@@ -759,8 +771,9 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     P.atten = c->atten;
     P.mfrac = c->mfrac;
     UP(upload(c, &c->u_dev, (const double *)nullptr, (size_t)std::max(1, c->nparam)));
-    UP(upload(c, &c->ybuf[0], (const double *)nullptr, (size_t)c->ntr * c->n));
-    UP(upload(c, &c->ybuf[1], (const double *)nullptr, (size_t)c->ntr * c->n));
+    const size_t ybuf_len = (size_t)(c->model == M3D_MODEL_NDOP ? 2 * c->ntr : c->ntr) * c->n;
+    UP(upload(c, &c->ybuf[0], (const double *)nullptr, ybuf_len));
+    UP(upload(c, &c->ybuf[1], (const double *)nullptr, ybuf_len));
     UP(upload(c, &c->red_part, (const double *)nullptr, (size_t)kRedBlocks));
     UP(upload(c, &c->red_out, (const double *)nullptr, (size_t)1));
     UP(cudaMallocHost((void **)&c->red_host, sizeof(double)));
@@ -778,7 +791,7 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
         UP(cudaDeviceSynchronize());
     }
     P.I0tab = I0;
-    c->smem_bytes = sizeof(double) * (size_t)(c->ntr + 1) * c->zmax;
+    c->smem_bytes = sizeof(double) * (size_t)(c->ntr + 2) * c->zmax;
     if (c->smem_bytes > 48 * 1024) {
         UP(cudaFuncSetAttribute((const void *)c->step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)c->smem_bytes));
@@ -818,6 +831,9 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
         c->R.rt = rt_dev;
         c->R.sp_max = sp_max;
         c->R.bk_max = bk_max;
+        c->R_tan.rt = rt_dev;
+        c->R_tan.sp_max = sp_max;
+        c->R_tan.bk_max = bk_max;
         // tridiagonal form of the implicit blocks, when every one of them has it
         {
             std::vector<double> tri((size_t)c->nmonth * 3 * c->n, 0.0);
@@ -835,26 +851,35 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
                 UP(upload_vec(c, &tri_dev, tri));
                 c->R.tri = tri_dev;
                 c->R.tri_mstride = 3LL * c->n;
-                std::vector<int> chains, chain_off(ntiles + 1, 0);
-                for (int t = 0; t < ntiles; t++) {
-                    int c0 = bounds[t], c1 = bounds[t + 1], cell0 = g->col_start[c0];
-                    std::vector<int> cols;
-                    for (int cc = c0; cc < c1; cc++) cols.push_back(cc);
-                    std::stable_sort(cols.begin(), cols.end(), [&](int a, int b) {
-                        return (g->col_start[a + 1] - g->col_start[a]) > (g->col_start[b + 1] - g->col_start[b]);
-                    });
-                    for (int cc : cols)
-                        for (int h = 0; h < 2; h++)
-                            for (int tr = 0; tr < c->ntr; tr++)
-                                chains.push_back(m3d::pack_chain(g->col_start[cc] - cell0,
-                                                                 g->col_start[cc + 1] - g->col_start[cc], tr, h));
-                    chain_off[t + 1] = (int)chains.size();
+                c->R_tan.tri = tri_dev;
+                c->R_tan.tri_mstride = 3LL * c->n;
+                // Thomas chains (column, component, month) per tile, deepest columns first; the
+                // model with its tangent has twice the components
+                for (int variant = 0; variant < 2; variant++) {
+                    const int ncomp = variant == 0 ? c->ntr : 2 * c->ntr;
+                    if (variant == 1 && c->model != M3D_MODEL_NDOP) break;
+                    std::vector<int> chains, chain_off(ntiles + 1, 0);
+                    for (int t = 0; t < ntiles; t++) {
+                        int c0 = bounds[t], c1 = bounds[t + 1], cell0 = g->col_start[c0];
+                        std::vector<int> cols;
+                        for (int cc = c0; cc < c1; cc++) cols.push_back(cc);
+                        std::stable_sort(cols.begin(), cols.end(), [&](int a, int b) {
+                            return (g->col_start[a + 1] - g->col_start[a]) > (g->col_start[b + 1] - g->col_start[b]);
+                        });
+                        for (int cc : cols)
+                            for (int h = 0; h < 2; h++)
+                                for (int tr = 0; tr < ncomp; tr++)
+                                    chains.push_back(m3d::pack_chain(g->col_start[cc] - cell0,
+                                                                     g->col_start[cc + 1] - g->col_start[cc], tr, h));
+                        chain_off[t + 1] = (int)chains.size();
+                    }
+                    const int *ch_dev = nullptr, *choff_dev = nullptr;
+                    UP(upload_vec(c, &ch_dev, chains));
+                    UP(upload_vec(c, &choff_dev, chain_off));
+                    m3d::ResidentParams &RR = variant == 0 ? c->R : c->R_tan;
+                    RR.chains = ch_dev;
+                    RR.chain_off = choff_dev;
                 }
-                const int *ch_dev = nullptr, *choff_dev = nullptr;
-                UP(upload_vec(c, &ch_dev, chains));
-                UP(upload_vec(c, &choff_dev, chain_off));
-                c->R.chains = ch_dev;
-                c->R.chain_off = choff_dev;
             }
         }
         if (coop && c->rk.year && c->resident_smem <= (size_t)prop.sharedMemPerBlockOptin) {
@@ -876,6 +901,34 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
         if (c->tri_resident_ok && !c->resident_ok) c->resident_ok = 1;
         c->implicit_form = c->tri_resident_ok ? M3D_IMPLICIT_TRIDIAGONAL : M3D_IMPLICIT_DENSE;
         c->plan = c->resident_ok ? M3D_PLAN_RESIDENT : (c->persistent_ok ? M3D_PLAN_PERSISTENT : M3D_PLAN_GRAPH);
+        if (c->model == M3D_MODEL_NDOP) {
+            // the model with its tangent: same tiles, four state components
+            YearVariant &V = c->tan;
+            V = tangent_kernels();
+            V.smem = sizeof(double) * (size_t)(V.ntr + 2) * c->zmax;
+            V.resident_smem = (size_t)m3d::resident_layout(V.ntr, sp_max, bk_max, c->zmax, false).total;
+            V.resident_tri_smem = (size_t)m3d::resident_layout(V.ntr, sp_max, bk_max, c->zmax, true).total;
+            int occ = 0;
+            if (V.smem > 48 * 1024)
+                UP(cudaFuncSetAttribute((const void *)V.year, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V.smem));
+            UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)V.year, m3d::kThreads, V.smem));
+            V.persistent_ok = coop && (long long)occ * prop.multiProcessorCount >= ntiles;
+            if (coop && V.resident_smem <= (size_t)prop.sharedMemPerBlockOptin) {
+                UP(cudaFuncSetAttribute((const void *)V.rk.year, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)V.resident_smem));
+                UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)V.rk.year, m3d::kThreads,
+                                                                 V.resident_smem));
+                V.resident_ok = (long long)occ * prop.multiProcessorCount >= ntiles;
+            }
+            if (coop && c->tri_ok && V.resident_tri_smem <= (size_t)prop.sharedMemPerBlockOptin) {
+                UP(cudaFuncSetAttribute((const void *)V.rk.year_tri, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)V.resident_tri_smem));
+                UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)V.rk.year_tri, m3d::kThreads,
+                                                                 V.resident_tri_smem));
+                V.tri_resident_ok = (long long)occ * prop.multiProcessorCount >= ntiles;
+            }
+            c->tan_ok = V.persistent_ok || V.resident_ok || V.tri_resident_ok;
+        }
     }
 #undef UP
     *out = c;
@@ -902,8 +955,9 @@ m3d_status launch_step(m3d_ctx *c, int j, const double *y, double *yn)
     return M3D_OK;
 }
 
-// One cooperative launch for nsteps steps from step j0: y in buf[0], result in buf[nsteps & 1].
-m3d_status launch_year_persistent(m3d_ctx *c, int j0, int nsteps)
+// One cooperative launch of a streaming persistent year kernel for nsteps steps from j0:
+// y in buf[0], result in buf[nsteps & 1].
+m3d_status launch_year_persistent(m3d_ctx *c, year_kernel_t kernel, size_t smem, int j0, int nsteps)
 {
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.flags, 0, sizeof(int) * c->ntiles, c->stream));
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.status, 0, sizeof(int) * 4, c->stream));
@@ -911,8 +965,8 @@ m3d_status launch_year_persistent(m3d_ctx *c, int j0, int nsteps)
     m3d::SyncParams S = c->S;
     double *b0 = c->ybuf[0], *b1 = c->ybuf[1];
     void *args[] = {&P, &S, &b0, &b1, &j0, &nsteps};
-    CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)c->year_kernel, dim3(c->ntiles), dim3(m3d::kThreads),
-                                                args, c->smem_bytes, c->stream));
+    CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)kernel, dim3(c->ntiles), dim3(m3d::kThreads), args, smem,
+                                                c->stream));
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
     return M3D_OK;
 }
@@ -989,7 +1043,7 @@ m3d_status run_year_from_ybuf(m3d_ctx *c, double *out, cudaMemcpyKind kind)
     if (c->plan == M3D_PLAN_PERSISTENT) {
         m3d_status st = launch_prologue(c, c->u_dev);
         if (st != M3D_OK) return st;
-        st = launch_year_persistent(c, 0, c->nstep);
+        st = launch_year_persistent(c, c->year_kernel, c->smem_bytes, 0, c->nstep);
         if (st != M3D_OK) return st;
         CUDA_OR_FAIL(c, cudaMemcpyAsync(out, c->ybuf[c->nstep & 1], len, kind, c->stream));
         c->last_launches = (c->model == M3D_MODEL_NDOP ? 1 : 0) + 1;
@@ -998,6 +1052,52 @@ m3d_status run_year_from_ybuf(m3d_ctx *c, double *out, cudaMemcpyKind kind)
         CUDA_OR_FAIL(c, cudaMemcpyAsync(out, c->ybuf[c->year_result_buf], len, kind, c->stream));
         c->last_launches = (c->model == M3D_MODEL_NDOP ? 1 : 0) + c->nstep;
     }
+    return M3D_OK;
+}
+
+// The year of the model with its tangent from ybuf[0] = [y; v] ([4][n]); result [phi; phi' v]
+// into out_y and out_v (device).  Uses the resident plan where it fits, else the streaming
+// persistent kernel.
+m3d_status run_year_tangent(m3d_ctx *c, double *out_y, double *out_v)
+{
+    const YearVariant &V = c->tan;
+    const size_t half = sizeof(double) * (size_t)c->ntr * c->n;
+    m3d_status st = launch_prologue(c, c->u_dev);
+    if (st != M3D_OK) return st;
+    const bool tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && V.tri_resident_ok;
+    const bool resident = c->plan == M3D_PLAN_RESIDENT && (tri || V.resident_ok);
+    if (resident) {
+        const int nb = (c->n + 255) / 256;
+        V.rk.to_interleaved<<<nb, 256, 0, c->stream>>>(c->n, c->ybuf[0], c->ybuf[1]);
+        CUDA_OR_FAIL(c, cudaGetLastError());
+        CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.flags, 0, sizeof(int) * c->ntiles, c->stream));
+        CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.status, 0, sizeof(int) * 4, c->stream));
+        StepParams P = c->P;
+        m3d::ResidentParams R = c->R_tan;
+        m3d::SyncParams S = c->S;
+        double *b0 = c->ybuf[1], *b1 = c->ybuf[0];
+        int j0 = 0, nsteps = c->nstep;
+        void *args[] = {&P, &R, &S, &b0, &b1, &j0, &nsteps};
+        CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)(tri ? V.rk.year_tri : V.rk.year), dim3(c->ntiles),
+                                                    dim3(m3d::kThreads), args,
+                                                    tri ? V.resident_tri_smem : V.resident_smem, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost,
+                                        c->stream));
+        double *res = (nsteps & 1) ? b1 : b0, *other = (nsteps & 1) ? b0 : b1;
+        V.rk.from_interleaved<<<nb, 256, 0, c->stream>>>(c->n, res, other);
+        CUDA_OR_FAIL(c, cudaGetLastError());
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(out_y, other, half, cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(out_v, (char *)other + half, half, cudaMemcpyDeviceToDevice, c->stream));
+        c->last_launches = 4;
+        return M3D_OK;
+    }
+    if (!V.persistent_ok) return fail(c, M3D_ERR_UNSUPPORTED, "the tangent year kernel does not fit on this GPU");
+    st = launch_year_persistent(c, V.year, V.smem, 0, c->nstep);
+    if (st != M3D_OK) return st;
+    double *res = c->ybuf[c->nstep & 1];
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(out_y, res, half, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(out_v, (char *)res + half, half, cudaMemcpyDeviceToDevice, c->stream));
+    c->last_launches = 2;
     return M3D_OK;
 }
 
@@ -1214,4 +1314,24 @@ cudaError_t m3d_alloc(m3d_ctx *c, void **p, size_t bytes)
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
     if (e == cudaSuccess) c->allocs.push_back(*p);
     return e;
+}
+
+m3d_status m3d_year_tangent_device(m3d_ctx *c, const double *y0, const double *v, double *phi, double *jv)
+{
+    if (!c->tan_ok) return fail(c, M3D_ERR_UNSUPPORTED, "this model has no tangent year kernel");
+    const size_t half = sizeof(double) * (size_t)c->ntr * c->n;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], y0, half, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync((char *)c->ybuf[0] + half, v, half, cudaMemcpyDeviceToDevice, c->stream));
+    return run_year_tangent(c, phi, jv);
+}
+
+extern "C" m3d_status metos3d_year_tangent(m3d_ctx *c, const double *y0, const double *v, const double *u,
+                                           double *phi_out, double *jv_out)
+{
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_tangent: null context");
+    if (!y0 || !v || !phi_out || !jv_out || (c->nparam > 0 && !u))
+        return fail(c, M3D_ERR_ARG, "metos3d_year_tangent: null pointer");
+    m3d_status st = m3d_set_params(c, u, cudaMemcpyDeviceToDevice);
+    if (st != M3D_OK) return st;
+    return m3d_year_tangent_device(c, y0, v, phi_out, jv_out);
 }

@@ -109,6 +109,8 @@ struct Solver {
     Workspace W;
     long long N;
     int grid;
+    bool tangent = false;           // Jacobian-vector products by the tangent year map
+    int *tangent_maps = nullptr;
 
     m3d_status launch_ok() { CUDA_OR_FAIL(c, cudaGetLastError()); return M3D_OK; }
 
@@ -157,10 +159,18 @@ struct Solver {
     }
 };
 
-// J v = v - (phi(y + h v) - phi(y)) / h with h = eps ||y|| / ||v||
+// J v = v - phi'(y) v: by the tangent year map, or by finite differences
+// v - (phi(y + h v) - phi(y)) / h with h = eps ||y|| / ||v||
 m3d_status apply_jacobian(Solver &S, const double *y, const double *py, double ynorm, double eps,
                           const double *v, double vnorm, double *w, int *year_maps)
 {
+    if (S.tangent) {
+        (*S.tangent_maps)++;
+        m3d_status st = m3d_year_tangent_device(S.c, y, v, S.W.phv, S.W.tmp);
+        if (st != M3D_OK) return st;
+        k_axpby<<<S.grid, 256, 0, S.c->stream>>>(w, 1.0, v, -1.0, S.W.tmp, S.N);
+        return S.launch_ok();
+    }
     double h = eps * ynorm / vnorm;
     if (!(h > 0.0)) h = eps;
     m3d_status st = S.axpby(S.W.tmp, 1.0, y, h, v);
@@ -369,12 +379,15 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
     if (opts_in) o = *opts_in;
     if (!(o.tol > 0.0) || o.max_newton < 0 || o.restart < 1 || o.max_krylov < 1 || !(o.fd_eps > 0.0))
         return fail(c, M3D_ERR_ARG, "metos3d_newton_solve: bad options");
-    if (o.jv != M3D_JV_FD)
-        return fail(c, M3D_ERR_UNSUPPORTED, "metos3d_newton_solve: only finite-difference products are built");
+    if (o.jv != M3D_JV_FD && o.jv != M3D_JV_TANGENT) return fail(c, M3D_ERR_ARG, "metos3d_newton_solve: bad jv");
+    if (o.jv == M3D_JV_TANGENT && !c->tan_ok)
+        return fail(c, M3D_ERR_UNSUPPORTED, "metos3d_newton_solve: this model has no tangent year map");
     auto t0 = std::chrono::steady_clock::now();
     m3d_newton_report R;
     memset(&R, 0, sizeof R);
     Solver S{c, {}, 0, 0};
+    S.tangent = o.jv == M3D_JV_TANGENT;
+    S.tangent_maps = &R.tangent_maps;
     m3d_status st = ensure_workspace(c, S, o.restart);
     if (st != M3D_OK) { release_workspace(c, S.W); return st; }
     Workspace &W = S.W;

@@ -23,6 +23,7 @@ namespace m3d {
 constexpr int kThreads = M3D_THREADS; // threads per tile CTA (512: 16 warps, 4 per SM sub-partition)
 constexpr int kModelNone = 0;
 constexpr int kModelNdop = 2;
+constexpr int kModelNdopTangent = 102;   // PO4-DOP with its tangent: state (N, DOP, dN, dDOP)
 constexpr double kSigmaPar = 0.4;    // photosynthetically available fraction of I_SWR
 constexpr int kEuphotic = 2;         // euphotic layers (Section 7: two)
 
@@ -104,29 +105,54 @@ __device__ __forceinline__ double insolation(double lat_deg, double t)
     return 1361.0 / pi * (h0 * sin(phi) * sin(delta) + cos(phi) * cos(delta) * sin(h0));
 }
 
+// Dual numbers (value, directional derivative) for the tangent of the source term: the
+// model functions below are templates over the scalar, so their tangent is the same code
+// evaluated on dual numbers.
+struct Dual {
+    double v, d;
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.v * b.d + a.d * b.v}; }
+__device__ __forceinline__ Dual operator*(double c, Dual a) { return {c * a.v, c * a.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, double c) { return {a.v * c, a.d * c}; }
+__device__ __forceinline__ Dual operator+(Dual a, double c) { return {a.v + c, a.d}; }
+__device__ __forceinline__ Dual operator+(double c, Dual a) { return {c + a.v, a.d}; }
+__device__ __forceinline__ Dual operator/(Dual a, double c) { return {a.v / c, a.d / c}; }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b)
+{
+    const double q = a.v / b.v;
+    return {q, (a.d - q * b.d) / b.v};
+}
+__device__ __forceinline__ Dual &operator+=(Dual &a, Dual b) { a = a + b; return a; }
+
+template <class T> __device__ __forceinline__ T zero_of();
+template <> __device__ __forceinline__ double zero_of<double>() { return 0.0; }
+template <> __device__ __forceinline__ Dual zero_of<Dual>() { return {0.0, 0.0}; }
+
 // PO4-DOP euphotic cell over nsub internal steps (Section 2.2.1), light I fixed:
 //   f = alpha N/(N+K_N) I/(I+K_I),  dN = -f + lambda DOP,  dDOP = sigma f - lambda DOP.
 // Returns the increments and the production summed over the internal steps.  With one
 // internal step the two Michaelis-Menten quotients share one division.
-__device__ __forceinline__ void ndop_euphotic(double N, double D, double I, double alpha,
-                                              double sigma, double lambda, double KN, double KI,
-                                              double ds, int nsub, double &dN, double &dD,
-                                              double &fsum)
+template <class T>
+__device__ __forceinline__ void ndop_euphotic(T N, T D, double I, double alpha, double sigma, double lambda,
+                                              double KN, double KI, double ds, int nsub, T &dN, T &dD, T &fsum)
 {
     if (nsub == 1) {
-        double f = (alpha * N * I) / ((N + KN) * (I + KI));
-        double lD = lambda * D;
+        T f = (alpha * N * I) / ((N + KN) * (I + KI));
+        T lD = lambda * D;
         dN = ds * (lD - f);
         dD = ds * (sigma * f - lD);
         fsum = f;
         return;
     }
     double aLF = alpha * (I / (I + KI));
-    double N0 = N, D0 = D;
-    fsum = 0.0;
+    T N0 = N, D0 = D;
+    fsum = zero_of<T>();
     for (int s = 0; s < nsub; s++) {
-        double f = aLF * (N / (N + KN));
-        double lD = lambda * D;
+        T f = aLF * (N / (N + KN));
+        T lD = lambda * D;
         N = N + ds * (lD - f);
         D = D + ds * (sigma * f - lD);
         fsum += f;
@@ -137,16 +163,17 @@ __device__ __forceinline__ void ndop_euphotic(double N, double D, double I, doub
 
 // Aphotic PO4-DOP cell: DOP remineralises at lambda; the sinking flux deposits
 // Esum * mfrac, Esum being the export summed over the internal steps.
-__device__ __forceinline__ void ndop_aphotic(double D, double Esum, double mfrac, double lambda,
-                                             double ds, int nsub, double &dN, double &dD)
+template <class T>
+__device__ __forceinline__ void ndop_aphotic(T D, T Esum, double mfrac, double lambda, double ds, int nsub, T &dN,
+                                             T &dD)
 {
     if (nsub == 1) {
-        double lD = lambda * D;
+        T lD = lambda * D;
         dN = ds * (lD + mfrac * Esum);
         dD = ds * (-lD);
         return;
     }
-    double D0 = D, Dsum = 0.0;
+    T D0 = D, Dsum = zero_of<T>();
     for (int s = 0; s < nsub; s++) {
         Dsum += D;
         D = D + ds * (-(lambda * D));
@@ -171,23 +198,23 @@ __device__ __forceinline__ double martin_fraction(const double *hcol, int k, int
 
 // A whole shallow column (L <= number of euphotic layers) on one thread, with the export
 // kept in its bottom layer inside every internal step.
-__device__ __forceinline__ void ndop_shallow_column(int L, const double *hcol, const double *N0,
-                                                 const double *D0, const double *I, double alpha,
-                                                 double sigma, double lambda, double KN, double KI,
-                                                 double ds, int nsub, double *dN, double *dD)
+template <class T>
+__device__ __forceinline__ void ndop_shallow_column(int L, const double *hcol, const T *N0, const T *D0,
+                                                    const double *I, double alpha, double sigma, double lambda,
+                                                    double KN, double KI, double ds, int nsub, T *dN, T *dD)
 {
-    double N[kEuphotic], D[kEuphotic];
+    T N[kEuphotic], D[kEuphotic];
     for (int k = 0; k < L; k++) { N[k] = N0[k]; D[k] = D0[k]; }
     for (int s = 0; s < nsub; s++) {
-        double E = 0.0, f[kEuphotic];
+        T E = zero_of<T>(), f[kEuphotic];
         for (int k = 0; k < L; k++) {
             f[k] = alpha * (N[k] / (N[k] + KN)) * (I[k] / (I[k] + KI));
             E += (1.0 - sigma) * f[k] * hcol[k];
         }
         for (int k = 0; k < L; k++) {
-            double qN = -f[k] + lambda * D[k];
+            T qN = -f[k] + lambda * D[k];
             if (k == L - 1) qN += E / hcol[k];
-            double qD = sigma * f[k] - lambda * D[k];
+            T qD = sigma * f[k] - lambda * D[k];
             N[k] = N[k] + ds * qN;
             D[k] = D[k] + ds * qD;
         }
@@ -239,16 +266,54 @@ __device__ __forceinline__ void barrier_sub(int id)
     else asm volatile("bar.sync 1, %0;" :: "n"(kThreads - 32) : "memory");
 }
 
+// Access to the model state of one cell as a scalar (N or DOP) or, for the tangent, as a
+// dual number (N, dN) or (DOP, dDOP) from components (0, 2) and (1, 3).
+template <class T> struct ModelState;
+template <> struct ModelState<double> {
+    template <class SV> __device__ __forceinline__ static double get(const SV &Y, int cell, int which)
+    {
+        return Y.get(cell, which);
+    }
+    __device__ __forceinline__ static void put(double *dq, int zmax, int i, int which, double v) { dq[which * zmax + i] = v; }
+    __device__ __forceinline__ static void add(double *dq, int zmax, int i, int which, double v) { dq[which * zmax + i] += v; }
+    __device__ __forceinline__ static void put_e(double *ek, int zmax, int i, double v) { ek[i] = v; }
+    __device__ __forceinline__ static double get_e(const double *ek, int zmax, int i) { return ek[i]; }
+};
+template <> struct ModelState<Dual> {
+    template <class SV> __device__ __forceinline__ static Dual get(const SV &Y, int cell, int which)
+    {
+        return {Y.get(cell, which), Y.get(cell, which + 2)};
+    }
+    __device__ __forceinline__ static void put(double *dq, int zmax, int i, int which, Dual v)
+    {
+        dq[which * zmax + i] = v.v;
+        dq[(which + 2) * zmax + i] = v.d;
+    }
+    __device__ __forceinline__ static void add(double *dq, int zmax, int i, int which, Dual v)
+    {
+        dq[which * zmax + i] += v.v;
+        dq[(which + 2) * zmax + i] += v.d;
+    }
+    __device__ __forceinline__ static void put_e(double *ek, int zmax, int i, Dual v)
+    {
+        ek[i] = v.v;
+        ek[zmax + i] = v.d;
+    }
+    __device__ __forceinline__ static Dual get_e(const double *ek, int zmax, int i) { return {ek[i], ek[zmax + i]}; }
+};
+
 // The source-minus-sink increment of the PO4-DOP model (Section 2.2.1) for every cell of a
 // tile, computed from y_j and written to dq[t * zmax + i].  Reads only the tile's own cells.
 // Run by threads [0, nthr) of the CTA, which synchronise on named barrier `bar`:
 // euphotic cells first, then aphotic cells (which need their column's export) and the
 // export kept in the bottom layer of shallow columns.  With several internal steps a
 // shallow column runs whole on one thread, since its cells then couple at every step.
-template <int NTR, class SV>
-__device__ __forceinline__ void ndop_source_tile(const StepParams &P, const Tile &T, int j, const SV &Y,
+// T = double: the model; T = Dual: the model and its tangent (ek then holds 2 * zmax).
+template <class T, class SV>
+__device__ __forceinline__ void ndop_source_tile(const StepParams &P, const Tile &T_, int j, const SV &Y,
                                                  double *dq, double *ek, int nthr, int bar)
 {
+    typedef ModelState<T> MS;
     const int tid = threadIdx.x;
     const int zmax = P.zmax;
     const double alpha = __ldg(P.qpar + kQAlpha), sigma = __ldg(P.qpar + kQSigma);
@@ -257,56 +322,60 @@ __device__ __forceinline__ void ndop_source_tile(const StepParams &P, const Tile
     const int nsub = P.nsub;
     const double ds = P.ds;
     const double *I0row = P.I0tab + (size_t)j * P.nulat;
-    for (int e = T.eu0 + tid; e < T.eu1; e += nthr) {
+    for (int e = T_.eu0 + tid; e < T_.eu1; e += nthr) {
         const int i = __ldg(P.eu_list + e);
-        const int cell = T.cell0 + i;
+        const int cell = T_.cell0 + i;
         const int L = __ldg(P.cell_kl + cell) >> 8;
         const double I0 = __ldg(I0row + __ldg(P.cell_ulat + cell));
         if (L <= kEuphotic && nsub > 1) {
-            double N0[kEuphotic], D0[kEuphotic], I[kEuphotic], dN[kEuphotic], dD[kEuphotic];
+            T N0[kEuphotic], D0[kEuphotic], dN[kEuphotic], dD[kEuphotic];
+            double I[kEuphotic];
             for (int kk = 0; kk < L; kk++) {
-                N0[kk] = Y.get(cell + kk, 0);
-                D0[kk] = Y.get(cell + kk, 1);
+                N0[kk] = MS::get(Y, cell + kk, 0);
+                D0[kk] = MS::get(Y, cell + kk, 1);
                 I[kk] = I0 * __ldg(P.atten + cell + kk);
             }
-            ndop_shallow_column(L, P.h + cell, N0, D0, I, alpha, sigma, lambda, KN, KI, ds, nsub, dN, dD);
+            ndop_shallow_column<T>(L, P.h + cell, N0, D0, I, alpha, sigma, lambda, KN, KI, ds, nsub, dN, dD);
             for (int kk = 0; kk < L; kk++) {
-                dq[i + kk] = dN[kk];
-                dq[zmax + i + kk] = dD[kk];
+                MS::put(dq, zmax, i + kk, 0, dN[kk]);
+                MS::put(dq, zmax, i + kk, 1, dD[kk]);
             }
         } else {
-            double v[NTR];
-            Y.gather(cell, v);
-            double dN, dD, fsum;
-            ndop_euphotic(v[0], v[1], I0 * __ldg(P.atten + cell), alpha, sigma, lambda, KN, KI, ds, nsub,
-                          dN, dD, fsum);
-            dq[i] = dN;
-            dq[zmax + i] = dD;
-            ek[i] = oms * fsum * __ldg(P.h + cell);
+            T dN, dD, fsum;
+            ndop_euphotic<T>(MS::get(Y, cell, 0), MS::get(Y, cell, 1), I0 * __ldg(P.atten + cell), alpha, sigma,
+                             lambda, KN, KI, ds, nsub, dN, dD, fsum);
+            MS::put(dq, zmax, i, 0, dN);
+            MS::put(dq, zmax, i, 1, dD);
+            MS::put_e(ek, zmax, i, oms * fsum * __ldg(P.h + cell));
         }
     }
     barrier_sub(bar);
-    for (int a = T.ap0 + tid; a < T.ap1; a += nthr) {
+    for (int a = T_.ap0 + tid; a < T_.ap1; a += nthr) {
         const int i = __ldg(P.ap_list + a);
-        const int cell = T.cell0 + i;
+        const int cell = T_.cell0 + i;
         const int k = __ldg(P.cell_kl + cell) & 0xff;
-        const double Esum = ek[i - k] + ek[i - k + 1];
-        double dN, dD;
-        ndop_aphotic(Y.get(cell, 1), Esum, __ldg(P.mfrac + cell), lambda, ds, nsub, dN, dD);
-        dq[i] = dN;
-        dq[zmax + i] = dD;
+        const T Esum = MS::get_e(ek, zmax, i - k) + MS::get_e(ek, zmax, i - k + 1);
+        T dN, dD;
+        ndop_aphotic<T>(MS::get(Y, cell, 1), Esum, __ldg(P.mfrac + cell), lambda, ds, nsub, dN, dD);
+        MS::put(dq, zmax, i, 0, dN);
+        MS::put(dq, zmax, i, 1, dD);
     }
     // shallow columns (one internal step): the export stays in the bottom layer
-    for (int b = T.sh0 + tid; b < T.sh1; b += nthr) {
+    for (int b = T_.sh0 + tid; b < T_.sh1; b += nthr) {
         const int i = __ldg(P.sh_list + b);
-        const int cell = T.cell0 + i;
+        const int cell = T_.cell0 + i;
         const int k = __ldg(P.cell_kl + cell) & 0xff;
-        const double Esum = (k == 0) ? ek[i] : ek[i - 1] + ek[i];
-        dq[i] += ds * (Esum / __ldg(P.h + cell));
+        const T Esum = (k == 0) ? MS::get_e(ek, zmax, i) : MS::get_e(ek, zmax, i - 1) + MS::get_e(ek, zmax, i);
+        MS::add(dq, zmax, i, 0, ds * (Esum / __ldg(P.h + cell)));
     }
 }
 
-// One TMM step on one tile.  smem: (NTR + 1) * zmax doubles.
+// Whether a model has a source term, and its scalar type.
+template <int MODEL> struct ModelTraits { static constexpr bool has_q = false; typedef double scalar; };
+template <> struct ModelTraits<kModelNdop> { static constexpr bool has_q = true; typedef double scalar; };
+template <> struct ModelTraits<kModelNdopTangent> { static constexpr bool has_q = true; typedef Dual scalar; };
+
+// One TMM step on one tile.  smem: (NTR + 2) * zmax doubles.
 // Order: q increment of the tile's own cells into z (no neighbour data needed), then
 // z += A_exp(t_j) y_j, then y_{j+1} = A_imp(t_j) z.
 template <int NTR, int MODEL, bool COHERENT>
@@ -321,15 +390,15 @@ __device__ __forceinline__ void step_tile(const StepParams &P, int tile, int j,
     const int n = P.n;
     const int zmax = P.zmax;
     double *z = smem;                 // [NTR][zmax] dq, then A_exp y + dq, tile-local cells
-    double *ek = smem + NTR * zmax;   // [zmax] export contributions of euphotic cells
+    double *ek = smem + NTR * zmax;   // [2 zmax] export contributions of euphotic cells (and tangent)
 
     const int m0 = __ldg(P.m0tab + j);
     const double w = __ldg(P.wtab + j);
 
     // ---- source-minus-sink increment on y_j (Section 2.2.1)
-    if (MODEL == kModelNdop) {
+    if (ModelTraits<MODEL>::has_q) {
         StateView<NTR, false, COHERENT> Y{y, n};
-        ndop_source_tile<NTR>(P, T, j, Y, z, ek, blockDim.x, 0);
+        ndop_source_tile<typename ModelTraits<MODEL>::scalar>(P, T, j, Y, z, ek, blockDim.x, 0);
         __syncthreads();
     }
 
@@ -356,7 +425,7 @@ __device__ __forceinline__ void step_tile(const StepParams &P, int tile, int j,
             if (row >= 0) {
 #pragma unroll
                 for (int t = 0; t < NTR; t++)
-                    z[t * zmax + row] = (MODEL == kModelNdop) ? acc[t] + z[t * zmax + row] : acc[t];
+                    z[t * zmax + row] = ModelTraits<MODEL>::has_q ? acc[t] + z[t * zmax + row] : acc[t];
             }
         }
     }

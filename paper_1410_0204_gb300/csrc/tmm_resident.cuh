@@ -57,7 +57,7 @@ __host__ __device__ inline ResidentLayout resident_layout(int ntr, int sp_max, i
     L.si = o;  o += sp_max * 4;
     o = (o + 15) & ~15;
     L.z = o;   o += ntr * zmax * 8;
-    L.ek = o;  o += zmax * 8;
+    L.ek = o;  o += 2 * zmax * 8;
     L.total = (o + 15) & ~15;
     return L;
 }
@@ -118,7 +118,7 @@ __device__ __forceinline__ void transport_tile_resident(const StepParams &P, con
         if (row >= 0) {
 #pragma unroll
             for (int t = 0; t < NTR; t++)
-                z[t * zmax + row] = (MODEL == kModelNdop) ? acc[t] + z[t * zmax + row] : acc[t];
+                z[t * zmax + row] = ModelTraits<MODEL>::has_q ? acc[t] + z[t * zmax + row] : acc[t];
         }
     }
     __syncthreads();
@@ -265,9 +265,9 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
         // neighbouring tiles while the other warps compute it.
         const int nwork = blockDim.x - 32;
         if ((int)threadIdx.x < nwork) {
-            if (MODEL == kModelNdop) {
+            if (ModelTraits<MODEL>::has_q) {
                 const StateView<NTR, true, true> Y{y, P.n};
-                ndop_source_tile<NTR>(P, T, j, Y, z, ek, nwork, 1);
+                ndop_source_tile<typename ModelTraits<MODEL>::scalar>(P, T, j, Y, z, ek, nwork, 1);
             }
         } else if (s > 0) {
             bool ok = wait_neighbours(S, tile, s, s);
