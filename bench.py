@@ -48,26 +48,35 @@ def peaks():
     return hbm, src
 
 
+# DRAM bytes (read + write) per launch of the year kernel, from one ncu capture of this
+# workload (see profiles/); None where no capture of the current kernel exists.
+TRAFFIC_PER_LAUNCH = {("resident", True): 178656768 + 3875584}
+
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz maximum SM clock.
 # (A DFMA throughput probe on this GPU measured 1.20 TFLOP/s, 1.92 FMA/clock/SM at the
 # clock it ran.)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def algorithmic_per_step(prob, ntr=2):
+def algorithmic_per_step(prob, ntr=2, tridiagonal=False):
     """Algorithmic bytes and FP64 flops of one TMM step.
 
     bytes: explicit values of two months and their column indices, row pointers, the
-    implicit blocks of two months, and the state read and written once.
-    flops: one FMA to interpolate each matrix entry plus one FMA per tracer (explicit and
-    implicit), and the source term: ~20 flops per euphotic cell, ~8 per aphotic cell,
-    plus adding the increment to every tracer.
+    implicit operator of two months (dense blocks: S_imp values each; tridiagonal form:
+    three Thomas factors per cell each), and the state read and written once.
+    flops: explicit part, one FMA to interpolate each entry plus one FMA per tracer;
+    implicit part, the same per dense block entry, or per cell and tracer two Thomas
+    solves (forward FMA, scaling multiply, backward FMA: 5 flops each) and the
+    interpolation (3 flops); the source term, ~20 flops per euphotic cell, ~8 per aphotic
+    cell, plus adding the increment to every tracer.
     """
     n, nnz, s_imp = prob.n, prob.nnz, prob.s_imp
-    bytes_ = nnz * (2 * 8 + 4) + 4 * (n + 1) + s_imp * 2 * 8 + ntr * n * (8 + 8)
+    imp_bytes = (2 * 3 * n * 8) if tridiagonal else s_imp * 2 * 8
+    bytes_ = nnz * (2 * 8 + 4) + 4 * (n + 1) + imp_bytes + ntr * n * (8 + 8)
     L = prob.nlayer
     n_eu = int(np.minimum(L, 2).sum())
-    flops = (nnz + s_imp) * (2 + 2 * ntr) + 20 * n_eu + 8 * (n - n_eu) + 2 * ntr * n
+    imp_flops = (13 * ntr * n) if tridiagonal else s_imp * (2 + 2 * ntr)
+    flops = nnz * (2 + 2 * ntr) + imp_flops + 20 * n_eu + 8 * (n - n_eu) + 2 * ntr * n
     return bytes_, flops
 
 
@@ -202,6 +211,9 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         ctx = m3d.Context.from_problem(prob, model=m3d.MODEL_NDOP, ntracer=2, nparam=7, stream=stream)
+        tridiagonal = ctx.get_option(m3d.OPT_IMPLICIT_FORM) == m3d.IMPLICIT_TRIDIAGONAL
+        plan = {m3d.PLAN_RESIDENT: "resident", m3d.PLAN_PERSISTENT: "persistent",
+                m3d.PLAN_GRAPH: "graph"}[ctx.get_option(m3d.OPT_YEAR_PLAN)]
         y0 = torch.from_numpy(y0_h).cuda()
         u = torch.from_numpy(u_h).cuda()
         ya = torch.empty_like(y0)
@@ -250,6 +262,21 @@ def run_ours(args):
             t = torch.tensor([e2e_dt], dtype=torch.float64, device="cuda")
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             e2e_value = world * e2e_steps / float(t.item())
+
+        # Newton-Krylov periodic solve to ||phi(y) - y|| < 1e-8 from the constant initial state
+        newton = {}
+        if not args.no_newton:
+            modes = [("fd", m3d.JV_FD)] + ([("tangent", m3d.JV_TANGENT)] if args.newton_tangent else [])
+            for label, jv in modes:
+                yN = torch.from_numpy(y0_h).cuda()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, rep = ctx.newton_solve(yN, u, tol=1e-8, jv=jv)
+                dt_n = time.perf_counter() - t0
+                newton[label] = {"seconds": dt_n, "converged": bool(rep["converged"]), "residual": rep["residual"],
+                                 "newton_steps": rep["newton_steps"], "krylov_iterations": rep["krylov_total"],
+                                 "year_maps": rep["year_maps"], "tangent_maps": rep["tangent_maps"],
+                                 "model_year_equivalents": rep["year_maps"] + rep["tangent_maps"]}
         ctx.close()
 
     if rank != 0:
@@ -257,7 +284,7 @@ def run_ours(args):
             pg.destroy_process_group()
         return 0
     hbm_peak, hbm_src = peaks()
-    bytes_step, flops_step = algorithmic_per_step(prob)
+    bytes_step, flops_step = algorithmic_per_step(prob, tridiagonal=tridiagonal)
     t_year = total / args.steps
     flops_year = flops_step * prob.nstep
     bytes_year = bytes_step * prob.nstep
@@ -273,8 +300,12 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed iterations (256 MiB write); 12 months of matrices (~270 MB) exceed L2"},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "k_step (one launch per TMM step, whole year timed)",
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get((plan, tridiagonal)),
+                     "traffic_unit": "DRAM bytes per launch (one model year)",
+                     "kernel": {"resident": "k_year_resident (one launch per model year)",
+                                "persistent": "k_year (one launch per model year)",
+                                "graph": "k_step (one launch per TMM step)"}[plan],
+                     "plan": plan, "implicit_form": "tridiagonal" if tridiagonal else "dense",
                      "peak_source": "FP64 units x max SM clock (152 SMs x 2 FMA/clk x 2.07 GHz)"},
         "hbm_roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src,
@@ -283,6 +314,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(y0_h.nbytes)},
         "gpu_launches": launches,
         "clocks": clock,
+        "newton": newton,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
@@ -317,6 +349,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-newton", action="store_true", help="skip the Newton-Krylov solve timing")
+    ap.add_argument("--newton-tangent", action="store_true",
+                    help="also time Newton-Krylov with tangent Jacobian-vector products")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run this many single TMM steps of the workload (for profilers)")
     args = ap.parse_args()
