@@ -146,6 +146,20 @@ m3d_status metos3d_year_tangent(m3d_ctx *ctx, const double *y0, const double *v,
                                 double *phi_out, double *jv_out);
 
 /*
+ * The adjoint of the year map, for gradients (the parameter optimisation of Sections 1 and 9;
+ * exact derivatives by algorithmic differentiation, Section 6): for y1 = phi(y0; u) and a
+ * cotangent ybar1, ybar0 = phi_y(y0; u)^T ybar1 (device [ntracer][n]; may alias ybar1) and
+ * ubar = phi_u(y0; u)^T ybar1 (host [nparam], may be NULL), the gradient of <ybar1, y1>
+ * with respect to the state and the model parameters.  The forward sweep keeps one
+ * checkpoint every ckpt_every steps (<= 0: 240) and recomputes each segment before its
+ * reverse sweep: about three year maps of work and ckpt_every + 1 states of memory,
+ * allocated for the call.  PO4-DOP with one internal step and the resident plan only
+ * (M3D_ERR_UNSUPPORTED otherwise).  Synchronous.
+ */
+m3d_status metos3d_year_adjoint(m3d_ctx *ctx, const double *y0, const double *u, const double *ybar1,
+                                double *ybar0, double *ubar_host, int ckpt_every);
+
+/*
  * Diagnostics, synchronous, result on the host:
  *   metos3d_mass:     sum over tracers and cells of vol_i y_{tr,i} (total tracer mass);
  *   metos3d_residual: || a - b ||_2 over all ntracer * n entries (the paper's spin-up and

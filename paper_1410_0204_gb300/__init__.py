@@ -9,4 +9,5 @@ from .binding import (Context, Metos3dError, bgc, declared_symbols, load, librar
                       M3D_ERR_TIMEOUT, M3D_ERR_UNSUPPORTED, M3D_NOT_CONVERGED, OPT_YEAR_PLAN,
                       OPT_WAIT_TIMEOUT_NS, OPT_TEST_WITHHOLD_TILE, OPT_NTILES, PLAN_PERSISTENT, PLAN_GRAPH,
                       PLAN_RESIDENT, OPT_IMPLICIT_FORM, IMPLICIT_DENSE, IMPLICIT_TRIDIAGONAL,
-                      JV_FD, JV_TANGENT, NewtonOptions, NewtonReport)
+                      JV_FD, JV_TANGENT, NewtonOptions, NewtonReport,
+                      year_map_autograd)

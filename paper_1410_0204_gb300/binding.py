@@ -138,6 +138,7 @@ def load(build_if_missing: bool = False):
     L.metos3d_newton_solve.argtypes = [vp, vp, vp, C.POINTER(NewtonOptions), C.POINTER(NewtonReport)]
     L.metos3d_spinup.argtypes = [vp, vp, vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int)]
     L.metos3d_year_tangent.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.metos3d_year_adjoint.argtypes = [vp, vp, vp, vp, vp, dp, C.c_int]
     L.metos3d_residual_static.argtypes = [vp, vp, C.c_longlong, vp, vp]
     L.metos3d_residual_static_error.argtypes = []
     L.metos3d_residual_static_error.restype = C.c_char_p
@@ -278,6 +279,16 @@ class Context:
                                             _dev_ptr(jv_out, self.numel, "jv_out", True)), self._ctx)
         return phi_out, jv_out
 
+    def year_adjoint(self, y0, u, ybar1, ybar0, ckpt_every=240):
+        """ybar0 = phi_y^T ybar1 (into the CUDA tensor ybar0); returns ubar = phi_u^T ybar1 (numpy)."""
+        self._sync_stream()
+        ubar = np.zeros(max(self.nparam, 1))
+        _check(self._L.metos3d_year_adjoint(self._ctx, _dev_ptr(y0, self.numel, "y0"), _dev_ptr(u, self.nparam, "u"),
+                                            _dev_ptr(ybar1, self.numel, "ybar1"),
+                                            _dev_ptr(ybar0, self.numel, "ybar0", True), _dp(ubar),
+                                            int(ckpt_every)), self._ctx)
+        return ubar[:self.nparam]
+
     def year_map_host(self, y0, u, out=None):
         self._sync_stream()
         y0 = np.ascontiguousarray(y0, dtype=np.float64)
@@ -364,3 +375,40 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def _year_map_function():
+    """torch.autograd.Function for the year map: forward metos3d_year_map, backward the adjoint."""
+    torch = _torch()
+
+    class YearMap(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, y0, u, m3d_ctx, ckpt_every=240):
+            y1 = torch.empty_like(y0)
+            m3d_ctx.year_map(y0.detach().contiguous(), y1, u.detach().contiguous())
+            fctx.save_for_backward(y0, u)
+            fctx.m3d_ctx = m3d_ctx
+            fctx.ckpt_every = ckpt_every
+            return y1
+
+        @staticmethod
+        def backward(fctx, gy1):
+            y0, u = fctx.saved_tensors
+            gy0 = torch.empty_like(y0)
+            ubar = fctx.m3d_ctx.year_adjoint(y0.detach().contiguous(), u.detach().contiguous(),
+                                             gy1.detach().contiguous(), gy0, fctx.ckpt_every)
+            gu = torch.from_numpy(ubar).to(device=u.device, dtype=u.dtype)
+            return gy0, gu, None, None
+
+    return YearMap
+
+
+_YearMap = None
+
+
+def year_map_autograd(y0, u, ctx, ckpt_every=240):
+    """phi(y0; u) as a differentiable torch operation (gradients by the adjoint year map)."""
+    global _YearMap
+    if _YearMap is None:
+        _YearMap = _year_map_function()
+    return _YearMap.apply(y0, u, ctx, ckpt_every)

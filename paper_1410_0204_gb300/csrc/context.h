@@ -15,7 +15,8 @@ using m3d::Tile;
 
 typedef void (*step_kernel_t)(StepParams, int, const double *, double *);
 typedef void (*year_kernel_t)(StepParams, m3d::SyncParams, double *, double *, int, int);
-typedef void (*resident_kernel_t)(StepParams, m3d::ResidentParams, m3d::SyncParams, double *, double *, int, int);
+typedef void (*resident_kernel_t)(StepParams, m3d::ResidentParams, m3d::SyncParams, double *, long long, int, int,
+                                  int);
 typedef void (*layout_kernel_t)(int, const double *, double *);
 
 struct ResidentKernels {
@@ -55,13 +56,21 @@ struct m3d_ctx {
     m3d::ResidentParams R{};
     ResidentKernels rk{};
     size_t resident_smem = 0, resident_tri_smem = 0;
+    // adjoint: transposed operators (same layouts), its tables and kernels' shared memory
+    int adj_ok = 0, adj_tri_ok = 0, adj_dense_ok = 0;
+    StepParams PT{};
+    m3d::ResidentParams RTadj{};
+    m3d::AdjointParams A{};
+    size_t adj_smem_dense = 0, adj_smem_tri = 0;
+    double *mfrac_b = nullptr;
     YearVariant tan;                    // the model with its tangent (PO4-DOP only)
     m3d::ResidentParams R_tan{};        // resident layout of the tangent (its own Thomas chains)
     int tan_ok = 0;
     int *status_host = nullptr;         // pinned copy of S.status
     double *qpar = nullptr;
     double *u_dev = nullptr;
-    double *ybuf[2] = {nullptr, nullptr};
+    double *ybuf[2] = {nullptr, nullptr};   // ybuf[1] = ybuf[0] + ybuf_cap (one allocation)
+    long long ybuf_cap = 0;
     double *atten = nullptr, *mfrac = nullptr;
     double *vol = nullptr, *h = nullptr, *zc = nullptr;
     int *cell_kl = nullptr;
@@ -89,5 +98,7 @@ m3d_status m3d_year_device(m3d_ctx *c, const double *y0, double *y1);
 m3d_status m3d_set_params(m3d_ctx *c, const double *u, cudaMemcpyKind kind);
 // phi(y0) and phi'(y0) v with the parameters already in c->u_dev.
 m3d_status m3d_year_tangent_device(m3d_ctx *c, const double *y0, const double *v, double *phi, double *jv);
+// The per-call model tables (attenuation, Martin profile, model scalars) from c->u_dev.
+m3d_status m3d_prologue(m3d_ctx *c);
 // Device allocation owned by the context (freed by metos3d_free).
 cudaError_t m3d_alloc(m3d_ctx *c, void **p, size_t bytes);

@@ -18,6 +18,7 @@
 #include "tmm_kernels.cuh"
 #include "tmm_resident.cuh"
 #include "context.h"
+#include "adjoint.h"
 
 
 // ------------------------------------------------------------------------------ kernels
@@ -41,10 +42,10 @@ __global__ void __launch_bounds__(m3d::kThreads, 1) k_year(StepParams P, m3d::Sy
 
 template <int NTR, int MODEL, bool TRI>
 __global__ void __launch_bounds__(m3d::kThreads, 1) k_year_resident(StepParams P, m3d::ResidentParams R,
-                                                                 m3d::SyncParams S, double *buf0, double *buf1,
-                                                                 int j0, int nsteps)
+                                                                 m3d::SyncParams S, double *base, long long stride,
+                                                                 int period, int j0, int nsteps)
 {
-    m3d::year_resident<NTR, MODEL, TRI>(P, R, S, buf0, buf1, j0, nsteps);
+    m3d::year_resident<NTR, MODEL, TRI>(P, R, S, base, stride, period, j0, nsteps);
 }
 
 // Per-call tables of the PO4-DOP model that depend on the parameters u:
@@ -312,6 +313,37 @@ std::vector<int> partition_columns(const m3d_grid *g, const int *rowptr, int ntr
     return bounds;
 }
 
+// Deal the slices [s0, s1) (cost = slot count) to the warps of one tile: longest first to
+// the least loaded SM sub-partition (warp w sits on sub-partition w mod 4), round robin over
+// that sub-partition's warps.  Appends to wlist and woff (nwarps + 1 offsets).
+void deal_slices(int s0, int s1, const std::vector<int> &len, int nwarps, std::vector<int> &wlist,
+                 std::vector<int> &woff)
+{
+    std::vector<int> order;
+    for (int s = s0; s < s1; s++) order.push_back(s);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return len[a] > len[b]; });
+    const int nsub = 4;
+    std::vector<long long> load(nsub, 0);
+    std::vector<int> next(nsub, 0);
+    std::vector<std::vector<int>> per_warp(nwarps);
+    for (int s : order) {
+        int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[g] += len[s];
+        int w = g + nsub * (next[g] % (nwarps / nsub));
+        next[g]++;
+        per_warp[w].push_back(s);
+    }
+    int base = (int)wlist.size();
+    for (int w = 0; w < nwarps; w++) {
+        woff.push_back(base);
+        wlist.insert(wlist.end(), per_warp[w].begin(), per_warp[w].end());
+        base = (int)wlist.size();
+    }
+    woff.push_back(base);
+}
+
+}  // namespace
+
 // If the L x L row-major block B is the inverse of a tridiagonal matrix M (to 1e-11 relative),
 // write the Thomas factors of M: nl[k] = -l_k, rd[k] = 1/d_k, ne[k] = -e_k, and return true.
 bool tridiagonal_factors(const double *B, int L, double *nl, double *rd, double *ne)
@@ -358,37 +390,6 @@ bool tridiagonal_factors(const double *B, int L, double *nl, double *rd, double 
     }
     return true;
 }
-
-// Deal the slices [s0, s1) (cost = slot count) to the warps of one tile: longest first to
-// the least loaded SM sub-partition (warp w sits on sub-partition w mod 4), round robin over
-// that sub-partition's warps.  Appends to wlist and woff (nwarps + 1 offsets).
-void deal_slices(int s0, int s1, const std::vector<int> &len, int nwarps, std::vector<int> &wlist,
-                 std::vector<int> &woff)
-{
-    std::vector<int> order;
-    for (int s = s0; s < s1; s++) order.push_back(s);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return len[a] > len[b]; });
-    const int nsub = 4;
-    std::vector<long long> load(nsub, 0);
-    std::vector<int> next(nsub, 0);
-    std::vector<std::vector<int>> per_warp(nwarps);
-    for (int s : order) {
-        int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        load[g] += len[s];
-        int w = g + nsub * (next[g] % (nwarps / nsub));
-        next[g]++;
-        per_warp[w].push_back(s);
-    }
-    int base = (int)wlist.size();
-    for (int w = 0; w < nwarps; w++) {
-        woff.push_back(base);
-        wlist.insert(wlist.end(), per_warp[w].begin(), per_warp[w].end());
-        base = (int)wlist.size();
-    }
-    woff.push_back(base);
-}
-
-}  // namespace
 
 // ------------------------------------------------------------------------------ C ABI
 extern "C" {
@@ -772,8 +773,9 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     P.mfrac = c->mfrac;
     UP(upload(c, &c->u_dev, (const double *)nullptr, (size_t)std::max(1, c->nparam)));
     const size_t ybuf_len = (size_t)(c->model == M3D_MODEL_NDOP ? 2 * c->ntr : c->ntr) * c->n;
-    UP(upload(c, &c->ybuf[0], (const double *)nullptr, ybuf_len));
-    UP(upload(c, &c->ybuf[1], (const double *)nullptr, ybuf_len));
+    UP(upload(c, &c->ybuf[0], (const double *)nullptr, 2 * ybuf_len));   // one allocation: the
+    c->ybuf[1] = c->ybuf[0] + ybuf_len;                                   // resident kernel strides
+    c->ybuf_cap = (long long)ybuf_len;
     UP(upload(c, &c->red_part, (const double *)nullptr, (size_t)kRedBlocks));
     UP(upload(c, &c->red_out, (const double *)nullptr, (size_t)1));
     UP(cudaMallocHost((void **)&c->red_host, sizeof(double)));
@@ -930,6 +932,12 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
             c->tan_ok = V.persistent_ok || V.resident_ok || V.tri_resident_ok;
         }
     }
+    {
+        AdjointSetup as{g, mt, s_imp, &sp_rows_flat, &sp_len, &sp_off, &bk_rows_flat, &bk_len, &bk_off, &bounds,
+                        &cell_col, &blk_off};
+        m3d_status ast = setup_adjoint(c, as);
+        if (ast != M3D_OK) return bail(ast);
+    }
 #undef UP
     *out = c;
     return M3D_OK;
@@ -1019,8 +1027,9 @@ m3d_status run_year_from_ybuf(m3d_ctx *c, double *out, cudaMemcpyKind kind)
         m3d::ResidentParams R = c->R;
         m3d::SyncParams S = c->S;
         double *b0 = c->ybuf[1], *b1 = c->ybuf[0];
-        int j0 = 0, nsteps = c->nstep;
-        void *args[] = {&P, &R, &S, &b0, &b1, &j0, &nsteps};
+        long long stride = -c->ybuf_cap;                    // y_s = ybuf[1] - (s mod 2) cap
+        int period = 2, j0 = 0, nsteps = c->nstep;
+        void *args[] = {&P, &R, &S, &b0, &stride, &period, &j0, &nsteps};
         const bool tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL;
         CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)(tri ? c->rk.year_tri : c->rk.year), dim3(c->ntiles),
                                                     dim3(m3d::kThreads), args,
@@ -1076,8 +1085,9 @@ m3d_status run_year_tangent(m3d_ctx *c, double *out_y, double *out_v)
         m3d::ResidentParams R = c->R_tan;
         m3d::SyncParams S = c->S;
         double *b0 = c->ybuf[1], *b1 = c->ybuf[0];
-        int j0 = 0, nsteps = c->nstep;
-        void *args[] = {&P, &R, &S, &b0, &b1, &j0, &nsteps};
+        long long stride = -c->ybuf_cap;
+        int period = 2, j0 = 0, nsteps = c->nstep;
+        void *args[] = {&P, &R, &S, &b0, &stride, &period, &j0, &nsteps};
         CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)(tri ? V.rk.year_tri : V.rk.year), dim3(c->ntiles),
                                                     dim3(m3d::kThreads), args,
                                                     tri ? V.resident_tri_smem : V.resident_smem, c->stream));
@@ -1335,3 +1345,5 @@ extern "C" m3d_status metos3d_year_tangent(m3d_ctx *c, const double *y0, const d
     if (st != M3D_OK) return st;
     return m3d_year_tangent_device(c, y0, v, phi_out, jv_out);
 }
+
+m3d_status m3d_prologue(m3d_ctx *c) { return launch_prologue(c, c->u_dev); }

@@ -1,12 +1,14 @@
 // tmm_resident.cuh -- the year map (Metos3D, arXiv:1410.0204, Section 4) as one persistent
-// launch whose tiles keep their month of transport matrices in shared memory.
+// launch whose tiles keep their month of transport matrices in shared memory, and the
+// reverse (adjoint) sweep of the year map in the same form.
 //
-// Within one month of the year (240 of the 2880 steps) a tile reads the same four arrays
-// every step: A_m, A_{m+1} - A_m, B_m, B_{m+1} - B_m; only the interpolation weight w
-// changes.  On the 128 x 64 x 15 grid those arrays take about 25 MB in total, less than
-// the 152 x 228 KB of shared memory of a GB300.  So each tile loads its part once per month
-// and every step then reads its matrices on chip; only the neighbours' state comes from L2.
-// The state is kept interleaved, [cell][tracer], so one gather serves all tracers.
+// Within one month of the year (240 of the 2880 steps) a tile reads the same arrays every
+// step: A_m, A_{m+1} - A_m and the implicit operator of months m and m+1; only the
+// interpolation weight w changes.  On the 128 x 64 x 15 grid those arrays take about 25 MB
+// in total, less than the 152 x 228 KB of shared memory of a GB300.  So each tile loads its
+// part once per month and every step then reads its matrices on chip; only the neighbours'
+// state comes from L2.  The state is kept interleaved, [cell][tracer], so one gather
+// serves all tracers.
 #pragma once
 
 #include "tmm_kernels.cuh"
@@ -41,7 +43,7 @@ __host__ __device__ inline int pack_chain(int cb, int L, int t, int h) { return 
 
 // Shared memory layout of one tile, in bytes from the dynamic shared memory base.
 struct ResidentLayout {
-    int sa, sd, sb, sbd, si, tri, yt, z, ek, total;
+    int sa, sd, sb, sbd, si, tri, yt, z, ek, aux, total;
 };
 
 __host__ __device__ inline ResidentLayout resident_layout(int ntr, int sp_max, int bk_max, int zmax, bool tri)
@@ -58,6 +60,7 @@ __host__ __device__ inline ResidentLayout resident_layout(int ntr, int sp_max, i
     o = (o + 15) & ~15;
     L.z = o;   o += ntr * zmax * 8;
     L.ek = o;  o += 2 * zmax * 8;
+    L.aux = o; o += zmax * 8;
     L.total = (o + 15) & ~15;
     return L;
 }
@@ -77,31 +80,76 @@ __device__ __forceinline__ void copy_to_shared_int(int *dst, const int *__restri
     for (int i = threadIdx.x; i < count / 4; i += blockDim.x) d4[i] = __ldg(s4 + i);
 }
 
-// The explicit and implicit parts of one TMM step of one tile with its month resident in
-// shared memory: z += A_exp(t_j) y_j (z holds the source increment already), then
-// y_{j+1} = A_imp(t_j) z into the interleaved state.
-template <int NTR, int MODEL, bool TRI>
-__device__ __forceinline__ void transport_tile_resident(const StepParams &P, const Tile &T, int j,
-                                                        const double *__restrict__ y, double *__restrict__ yn,
-                                                        const double *sa, const double *sd, const double *sb,
-                                                        const double *sbd, const int *si, double *z,
-                                                        int sp_first, int bk_first)
-{
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int zmax = P.zmax;
-    const double w = __ldg(P.wtab + j);
-    const StateView<NTR, true, true> Y{y, P.n};
+// Shared memory views of one tile.
+struct TileSmem {
+    double *sa, *sd, *sb, *sbd, *tl, *yt, *z, *ek, *aux;
+    int *si;
+    int sp_first, bk_first;     // first slot of the tile's explicit / implicit slices
+};
 
-    // ---- explicit part from shared memory; neighbour state from L2
+__device__ __forceinline__ TileSmem tile_smem(unsigned char *dsm, const ResidentLayout &Ly, const StepParams &P,
+                                              const Tile &T)
+{
+    TileSmem M;
+    M.sa = reinterpret_cast<double *>(dsm + Ly.sa);
+    M.sd = reinterpret_cast<double *>(dsm + Ly.sd);
+    M.sb = reinterpret_cast<double *>(dsm + Ly.sb);
+    M.sbd = reinterpret_cast<double *>(dsm + Ly.sbd);
+    M.tl = reinterpret_cast<double *>(dsm + Ly.tri);
+    M.yt = reinterpret_cast<double *>(dsm + Ly.yt);
+    M.z = reinterpret_cast<double *>(dsm + Ly.z);
+    M.ek = reinterpret_cast<double *>(dsm + Ly.ek);
+    M.aux = reinterpret_cast<double *>(dsm + Ly.aux);
+    M.si = reinterpret_cast<int *>(dsm + Ly.si);
+    M.sp_first = T.sp0 < T.sp1 ? __ldg(P.sp_off + T.sp0) : 0;
+    M.bk_first = T.bk0 < T.bk1 ? __ldg(P.bk_off + T.bk0) : 0;
+    return M;
+}
+
+// Load the explicit values of month m (A_m and A_{m+1} - A_m from the arrays a, d).
+__device__ __forceinline__ void load_explicit_month(const StepParams &P, const ResidentTile &RT, const double *a,
+                                                    const double *d, int m, const TileSmem &M)
+{
+    copy_to_shared(M.sa, a + (long long)m * P.sp_mstride + RT.sp_base, RT.sp_n);
+    copy_to_shared(M.sd, d + (long long)m * P.sp_mstride + RT.sp_base, RT.sp_n);
+}
+
+// Load the implicit operator of months m and m+1: Thomas factors (TRI) or dense slices.
+template <bool TRI>
+__device__ __forceinline__ void load_implicit_month(const StepParams &P, const ResidentParams &R,
+                                                    const ResidentTile &RT, const Tile &T, const double *tri,
+                                                    const double *b, const double *bd, int m, const TileSmem &M)
+{
+    if (TRI) {
+        const int m1 = (m + 1) % P.nmonth;
+        for (int h = 0; h < 2; h++)
+            for (int f = 0; f < 3; f++) {
+                const double *src = tri + (long long)(h ? m1 : m) * R.tri_mstride + (long long)f * P.n + T.cell0;
+                double *dst = M.tl + (3 * h + f) * P.zmax;
+                for (int i = threadIdx.x; i < T.ncell; i += blockDim.x) dst[i] = __ldg(src + i);
+            }
+    } else {
+        copy_to_shared(M.sb, b + (long long)m * P.bk_mstride + RT.bk_base, RT.bk_n);
+        copy_to_shared(M.sbd, bd + (long long)m * P.bk_mstride + RT.bk_base, RT.bk_n);
+    }
+}
+
+// Explicit part from shared memory: z[t][row] = (A_m0 + w D_m0) y for the tile's rows, plus
+// z[t][row] when ADD (z then holds the source increment).  Neighbour state from L2.
+template <int NTR, bool ADD>
+__device__ __forceinline__ void spmv_resident(const StepParams &P, const Tile &T, double w,
+                                              const double *__restrict__ y, const TileSmem &M)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int zmax = P.zmax;
+    const StateView<NTR, true, true> Y{y, P.n};
     const int *wl = P.sp_wlist + __ldg(P.sp_woff + blockIdx.x * (nwarps + 1) + warp);
     const int wn = __ldg(P.sp_woff + blockIdx.x * (nwarps + 1) + warp + 1) -
                    __ldg(P.sp_woff + blockIdx.x * (nwarps + 1) + warp);
     for (int ws = 0; ws < wn; ws++) {
         const int s = __ldg(wl + ws);
         const int len = __ldg(P.sp_len + s);
-        const int base = (__ldg(P.sp_off + s) - sp_first) * 32 + lane;
+        const int base = (__ldg(P.sp_off + s) - M.sp_first) * 32 + lane;
         const int row = __ldg(P.sp_row + s * 32 + lane);
         double acc[NTR];
 #pragma unroll
@@ -110,28 +158,46 @@ __device__ __forceinline__ void transport_tile_resident(const StepParams &P, con
         for (int q = 0; q < len; q++) {
             const int idx = base + q * 32;
             double v[NTR];
-            Y.gather(si[idx], v);
-            const double a = fma(w, sd[idx], sa[idx]);
+            Y.gather(M.si[idx], v);
+            const double a = fma(w, M.sd[idx], M.sa[idx]);
 #pragma unroll
             for (int t = 0; t < NTR; t++) acc[t] = fma(a, v[t], acc[t]);
         }
         if (row >= 0) {
 #pragma unroll
-            for (int t = 0; t < NTR; t++)
-                z[t * zmax + row] = ModelTraits<MODEL>::has_q ? acc[t] + z[t * zmax + row] : acc[t];
+            for (int t = 0; t < NTR; t++) M.z[t * zmax + row] = ADD ? acc[t] + M.z[t * zmax + row] : acc[t];
         }
     }
-    __syncthreads();
-    if (TRI) return;
+}
 
-    // ---- implicit part from shared memory into the interleaved y_{j+1}
+// Write the tile's values v[t] of one cell into the interleaved state.
+template <int NTR>
+__device__ __forceinline__ void store_cell(double *__restrict__ yn, int cell, const double *v)
+{
+    double *o = yn + (size_t)cell * NTR;
+    if (NTR % 2 == 0) {
+#pragma unroll
+        for (int t = 0; t < NTR; t += 2) *reinterpret_cast<double2 *>(o + t) = make_double2(v[t], v[t + 1]);
+    } else {
+#pragma unroll
+        for (int t = 0; t < NTR; t++) o[t] = v[t];
+    }
+}
+
+// Implicit part, dense blocks from shared memory: yn = (B_m0 + w (B_m1 - B_m0)) z.
+template <int NTR>
+__device__ __forceinline__ void implicit_dense_resident(const StepParams &P, const Tile &T, double w,
+                                                        const TileSmem &M, double *__restrict__ yn)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int zmax = P.zmax;
     const int *bl = P.bk_wlist + __ldg(P.bk_woff + blockIdx.x * (nwarps + 1) + warp);
     const int bn = __ldg(P.bk_woff + blockIdx.x * (nwarps + 1) + warp + 1) -
                    __ldg(P.bk_woff + blockIdx.x * (nwarps + 1) + warp);
     for (int ws = 0; ws < bn; ws++) {
         const int s = __ldg(bl + ws);
         const int len = __ldg(P.bk_len + s);
-        const int base = (__ldg(P.bk_off + s) - bk_first) * 32 + lane;
+        const int base = (__ldg(P.bk_off + s) - M.bk_first) * 32 + lane;
         const int row = __ldg(P.bk_row + s * 32 + lane);
         const int cb = __ldg(P.bk_cb + s * 32 + lane);
         const int Lc = __ldg(P.bk_L + s * 32 + lane);
@@ -141,53 +207,41 @@ __device__ __forceinline__ void transport_tile_resident(const StepParams &P, con
 #pragma unroll 4
         for (int c = 0; c < len; c++) {
             const int idx = base + c * 32;
-            const double b = fma(w, sbd[idx], sb[idx]);
+            const double b = fma(w, M.sbd[idx], M.sb[idx]);
             const int zi = cb + (c < Lc ? c : 0);
 #pragma unroll
-            for (int t = 0; t < NTR; t++) acc[t] = fma(b, z[t * zmax + zi], acc[t]);
+            for (int t = 0; t < NTR; t++) acc[t] = fma(b, M.z[t * zmax + zi], acc[t]);
         }
-        if (row >= 0) {
-            double *o = yn + (size_t)(T.cell0 + row) * NTR;
-            if (NTR % 2 == 0) {
-#pragma unroll
-                for (int t = 0; t < NTR; t += 2)
-                    *reinterpret_cast<double2 *>(o + t) = make_double2(acc[t], acc[t + 1]);
-            } else {
-#pragma unroll
-                for (int t = 0; t < NTR; t++) o[t] = acc[t];
-            }
-        }
+        if (row >= 0) store_cell<NTR>(yn, T.cell0 + row, acc);
     }
 }
 
-// Implicit part in tridiagonal form: y_{j+1} = z0 + w (z1 - z0) with z_h = M_{m_h}^{-1} z
-// solved by Thomas' algorithm, one thread per (column, tracer, month) chain, then one
-// combining pass.  Equal to (B_m0 + w (B_m1 - B_m0)) z up to rounding, because the monthly
-// blocks are the inverses B_m = M_m^{-1}.
+// Implicit part in tridiagonal form: yn = z0 + w (z1 - z0) with z_h = M_{m_h}^{-1} z solved by
+// Thomas' algorithm, one thread per (column, tracer, month) chain, then one combining pass.
+// Equal to (B_m0 + w (B_m1 - B_m0)) z up to rounding, because the monthly blocks are the
+// inverses B_m = M_m^{-1}.
 template <int NTR>
-__device__ __forceinline__ void implicit_tridiagonal_tile(const StepParams &P, const ResidentParams &R,
-                                                          const Tile &T, int j, const double *z,
-                                                          const double *tl, double *yt, int ch0, int ch1,
-                                                          double *__restrict__ yn)
+__device__ __forceinline__ void implicit_tri_resident(const StepParams &P, const ResidentParams &R, const Tile &T,
+                                                      double w, const TileSmem &M, double *__restrict__ yn)
 {
     const int zmax = P.zmax;
-    const double w = __ldg(P.wtab + j);
+    const int ch0 = __ldg(R.chain_off + blockIdx.x), ch1 = __ldg(R.chain_off + blockIdx.x + 1);
     for (int c = ch0 + (int)threadIdx.x; c < ch1; c += blockDim.x) {
         const int pc = __ldg(R.chains + c);
         const int cb = pc & 0xffff, L = (pc >> 16) & 0x7f, t = (pc >> 23) & 0xf, h = (pc >> 27) & 1;
-        const double *nl = tl + (3 * h + 0) * zmax + cb;
-        const double *rd = tl + (3 * h + 1) * zmax + cb;
-        const double *ne = tl + (3 * h + 2) * zmax + cb;
-        const double *zc = z + t * zmax + cb;
-        double *x = yt + (h * NTR + t) * zmax + cb;
-        // forward: x_k = z_k - l_k x_{k-1}, stored as x_k / d_k (off the dependency chain)
+        const double *nl = M.tl + (3 * h + 0) * zmax + cb;
+        const double *rd = M.tl + (3 * h + 1) * zmax + cb;
+        const double *ne = M.tl + (3 * h + 2) * zmax + cb;
+        const double *zc = M.z + t * zmax + cb;
+        double *x = M.yt + (h * NTR + t) * zmax + cb;
+        // forward: x_k = z_k - l_k x_{k-1}, stored as x_k / d_k
         double xk = zc[0];
         x[0] = xk * rd[0];
         for (int k = 1; k < L; k++) {
             xk = fma(nl[k], xk, zc[k]);
             x[k] = xk * rd[k];
         }
-        // back: y_k = x_k / d_k - (e_k / d_k) y_{k+1}, one dependent FMA per layer
+        // back: y_k = x_k / d_k - (e_k / d_k) y_{k+1}
         double yk = x[L - 1];
         for (int k = L - 2; k >= 0; k--) {
             yk = fma(ne[k], yk, x[k]);
@@ -199,23 +253,27 @@ __device__ __forceinline__ void implicit_tridiagonal_tile(const StepParams &P, c
         double v[NTR];
 #pragma unroll
         for (int t = 0; t < NTR; t++) {
-            const double a = yt[t * zmax + i], b = yt[(NTR + t) * zmax + i];
+            const double a = M.yt[t * zmax + i], b = M.yt[(NTR + t) * zmax + i];
             v[t] = fma(w, b - a, a);
         }
-        double *o = yn + (size_t)(T.cell0 + i) * NTR;
-        if (NTR % 2 == 0) {
-#pragma unroll
-            for (int t = 0; t < NTR; t += 2) *reinterpret_cast<double2 *>(o + t) = make_double2(v[t], v[t + 1]);
-        } else {
-#pragma unroll
-            for (int t = 0; t < NTR; t++) o[t] = v[t];
-        }
+        store_cell<NTR>(yn, T.cell0 + i, v);
     }
 }
 
+template <int NTR, bool TRI>
+__device__ __forceinline__ void implicit_resident(const StepParams &P, const ResidentParams &R, const Tile &T,
+                                                  double w, const TileSmem &M, double *__restrict__ yn)
+{
+    if (TRI) implicit_tri_resident<NTR>(P, R, T, w, M, yn);
+    else implicit_dense_resident<NTR>(P, T, w, M, yn);
+}
+
+// The year (or nsteps steps from step j0) with the tiles' months resident in shared memory.
+// State of step s (interleaved): base + (s mod period) * stride; period 2 is a ping-pong,
+// period nsteps + 1 keeps every state (the trajectory an adjoint sweep reads back).
 template <int NTR, int MODEL, bool TRI>
 __device__ __forceinline__ void year_resident(const StepParams &P, const ResidentParams &R, const SyncParams &S,
-                                              double *buf0, double *buf1, int j0, int nsteps)
+                                              double *base, long long stride, int period, int j0, int nsteps)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ int abort_flag;
@@ -223,42 +281,20 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
     const Tile T = P.tiles[tile];
     const ResidentTile RT = R.rt[tile];
     const ResidentLayout Ly = resident_layout(NTR, R.sp_max, R.bk_max, P.zmax, TRI);
-    double *sa = reinterpret_cast<double *>(dsm + Ly.sa);
-    double *sd = reinterpret_cast<double *>(dsm + Ly.sd);
-    double *sb = reinterpret_cast<double *>(dsm + Ly.sb);
-    double *sbd = reinterpret_cast<double *>(dsm + Ly.sbd);
-    int *si = reinterpret_cast<int *>(dsm + Ly.si);
-    double *z = reinterpret_cast<double *>(dsm + Ly.z);
-    double *ek = reinterpret_cast<double *>(dsm + Ly.ek);
-    double *tl = reinterpret_cast<double *>(dsm + Ly.tri);
-    double *yt = reinterpret_cast<double *>(dsm + Ly.yt);
-    const int ch0 = TRI ? __ldg(R.chain_off + tile) : 0, ch1 = TRI ? __ldg(R.chain_off + tile + 1) : 0;
-    const int sp_first = T.sp0 < T.sp1 ? __ldg(P.sp_off + T.sp0) : 0;
-    const int bk_first = T.bk0 < T.bk1 ? __ldg(P.bk_off + T.bk0) : 0;
+    const TileSmem M = tile_smem(dsm, Ly, P, T);
 
-    copy_to_shared_int(si, P.sp_col + RT.sp_base, RT.sp_n);
+    copy_to_shared_int(M.si, P.sp_col + RT.sp_base, RT.sp_n);
     int cur_month = -1;
     for (int s = 0; s < nsteps; s++) {
         const int j = (j0 + s) % P.nstep;
-        const double *y = (s & 1) ? buf1 : buf0;
-        double *yn = (s & 1) ? buf0 : buf1;
+        const double *y = base + (long long)(s % period) * stride;
+        double *yn = base + (long long)((s + 1) % period) * stride;
         const int m0 = __ldg(P.m0tab + j);
+        const double w = __ldg(P.wtab + j);
         if (m0 != cur_month) {
             // a new month: load this tile's matrices (independent of the state, so before the wait)
-            copy_to_shared(sa, P.sp_a + (long long)m0 * P.sp_mstride + RT.sp_base, RT.sp_n);
-            copy_to_shared(sd, P.sp_d + (long long)m0 * P.sp_mstride + RT.sp_base, RT.sp_n);
-            if (TRI) {
-                const int m1 = (m0 + 1) % P.nmonth;
-                for (int h = 0; h < 2; h++)
-                    for (int f = 0; f < 3; f++) {
-                        const double *src = R.tri + (long long)(h ? m1 : m0) * R.tri_mstride + (long long)f * P.n + T.cell0;
-                        double *dst = tl + (3 * h + f) * P.zmax;
-                        for (int i = threadIdx.x; i < T.ncell; i += blockDim.x) dst[i] = __ldg(src + i);
-                    }
-            } else {
-                copy_to_shared(sb, P.bk_b + (long long)m0 * P.bk_mstride + RT.bk_base, RT.bk_n);
-                copy_to_shared(sbd, P.bk_d + (long long)m0 * P.bk_mstride + RT.bk_base, RT.bk_n);
-            }
+            load_explicit_month(P, RT, P.sp_a, P.sp_d, m0, M);
+            load_implicit_month<TRI>(P, R, RT, T, R.tri, P.bk_b, P.bk_d, m0, M);
             cur_month = m0;
         }
         // The source term needs only this tile's own cells: the last warp waits for the
@@ -267,7 +303,7 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
         if ((int)threadIdx.x < nwork) {
             if (ModelTraits<MODEL>::has_q) {
                 const StateView<NTR, true, true> Y{y, P.n};
-                ndop_source_tile<typename ModelTraits<MODEL>::scalar>(P, T, j, Y, z, ek, nwork, 1);
+                ndop_source_tile<typename ModelTraits<MODEL>::scalar>(P, T, j, Y, M.z, M.ek, nwork, 1);
             }
         } else if (s > 0) {
             bool ok = wait_neighbours(S, tile, s, s);
@@ -275,11 +311,207 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
         }
         __syncthreads();
         if (s > 0 && abort_flag) return;
-        transport_tile_resident<NTR, MODEL, TRI>(P, T, j, y, yn, sa, sd, sb, sbd, si, z, sp_first, bk_first);
-        if (TRI) implicit_tridiagonal_tile<NTR>(P, R, T, j, z, tl, yt, ch0, ch1, yn);
+        spmv_resident<NTR, ModelTraits<MODEL>::has_q>(P, T, w, y, M);
+        __syncthreads();
+        implicit_resident<NTR, TRI>(P, R, T, w, M, yn);
         // the CTA barrier orders every thread's stores of y_{j+1} before thread 0's release
         __syncthreads();
         if (threadIdx.x == 0 && tile != S.withhold_tile) store_release(S.flags + tile, s + 1);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Reverse (adjoint) sweep.  For one step y_{j+1} = B_j (A_j y_j + dq_j(y_j, u)) and the
+// cotangent zbar_j = B_j^T ybar_{j+1}:
+//     ybar_j = A_j^T zbar_j + (d dq_j / dy)^T zbar_j,   ubar += (d dq_j / du)^T zbar_j,
+// then zbar_{j-1} = B_{j-1}^T ybar_j.  The transposed operators have the same slice layouts
+// as the forward ones (the explicit pattern is structurally symmetric), so the same
+// device code applies them.
+
+// Per-call tables and outputs of the adjoint of the PO4-DOP term.
+struct AdjointParams {
+    const double *mfrac_b;     // [n] d mfrac / d b (aphotic cells)
+    const double *zc;          // [n] layer-centre depth
+    const int *col_list;       // per tile: its columns, tile-local first cell | layers << 16
+    const int *col_off;        // [ntiles+1]
+    double *ubar_part;         // [ntiles][8] parameter gradient of each tile
+};
+
+// Reverse of the PO4-DOP increment dq = ds q(y) (one internal step) on the tile's cells:
+// given zbar (cotangent of dq, global interleaved) and y_j, add (d dq/dy)^T zbar into M.z
+// (the tile's ybar_j) and (d dq/du)^T zbar into ub[7].
+//   euphotic: f = alpha' N/(N+K_N) I/(I+K_I), qN = -f + lambda D, qD = sigma f - lambda D
+//   E = (1 - sigma) sum f h;  aphotic: qN = E mfrac + lambda D, qD = -lambda D
+//   shallow column: the bottom layer also gets E / h.
+template <int NTR>
+__device__ __forceinline__ void ndop_source_adjoint_tile(const StepParams &P, const AdjointParams &A, const Tile &T,
+                                                         int j, const double *__restrict__ y,
+                                                         const double *__restrict__ zbar, const TileSmem &M,
+                                                         double *ub)
+{
+    const int zmax = P.zmax;
+    const double alpha = __ldg(P.qpar + kQAlpha), sigma = __ldg(P.qpar + kQSigma);
+    const double lambda = __ldg(P.qpar + kQLambda), KN = __ldg(P.qpar + kQKN);
+    const double KI = __ldg(P.qpar + kQKI), oms = __ldg(P.qpar + kQOneMinusSigma);
+    const double ds = P.ds;
+    const double *I0row = P.I0tab + (size_t)j * P.nulat;
+    double *fk = M.ek;                 // [zmax] production f of euphotic cells
+    double *ehk = M.ek + zmax;         // [zmax] (1 - sigma) f h of euphotic cells
+    double *Ebar = M.aux;              // per column, at its first cell
+    // (a) forward production of the euphotic cells
+    for (int e = T.eu0 + (int)threadIdx.x; e < T.eu1; e += blockDim.x) {
+        const int i = __ldg(P.eu_list + e);
+        const int cell = T.cell0 + i;
+        const double I = __ldg(I0row + __ldg(P.cell_ulat + cell)) * __ldg(P.atten + cell);
+        const double N = __ldcg(y + (size_t)cell * NTR);
+        const double f = (alpha * N * I) / ((N + KN) * (I + KI));
+        fk[i] = f;
+        ehk[i] = oms * f * __ldg(P.h + cell);
+    }
+    __syncthreads();
+    // (b) per column: the cotangent of its export, and the Martin exponent's gradient
+    const int c0 = __ldg(A.col_off + blockIdx.x), c1 = __ldg(A.col_off + blockIdx.x + 1);
+    for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) {
+        const int pc = __ldg(A.col_list + c);
+        const int cb = pc & 0xffff, L = pc >> 16;
+        const int neu = L < kEuphotic ? L : kEuphotic;
+        double E = 0.0, sfh = 0.0;
+        for (int k = 0; k < neu; k++) {
+            E += ehk[cb + k];
+            sfh += fk[cb + k] * __ldg(P.h + T.cell0 + cb + k);
+        }
+        double eb = 0.0, bb = 0.0;
+        for (int k = neu; k < L; k++) {
+            const int cell = T.cell0 + cb + k;
+            const double qbN = ds * __ldcg(zbar + (size_t)cell * NTR);
+            eb = fma(qbN, __ldg(P.mfrac + cell), eb);
+            bb = fma(qbN * E, __ldg(A.mfrac_b + cell), bb);
+        }
+        if (L <= kEuphotic) {
+            const int cell = T.cell0 + cb + L - 1;
+            eb += ds * __ldcg(zbar + (size_t)cell * NTR) / __ldg(P.h + cell);
+        }
+        Ebar[cb] = eb;
+        ub[6] += bb;
+        ub[2] -= eb * sfh;                        // d E / d sigma = -sum f h
+    }
+    __syncthreads();
+    // (c) every cell: DOP remineralisation; euphotic cells: production
+    for (int i = threadIdx.x; i < T.ncell; i += blockDim.x) {
+        const int cell = T.cell0 + i;
+        const int k = __ldg(P.cell_kl + cell) & 0xff;
+        const double qbN = ds * __ldcg(zbar + (size_t)cell * NTR);
+        const double qbD = ds * __ldcg(zbar + (size_t)cell * NTR + 1);
+        const double D = __ldcg(y + (size_t)cell * NTR + 1);
+        const double dl = qbN - qbD;
+        M.z[zmax + i] += lambda * dl;            // d q / d DOP
+        ub[3] += dl * D;                          // d q / d lambda
+        if (k < kEuphotic) {
+            const double N = __ldcg(y + (size_t)cell * NTR);
+            const double I = __ldg(I0row + __ldg(P.cell_ulat + cell)) * __ldg(P.atten + cell);
+            const double f = fk[i];
+            const double fb = Ebar[i - k] * oms * __ldg(P.h + cell) - qbN + sigma * qbD;
+            ub[2] += qbD * f;
+            const double NK = N + KN, IK = I + KI;
+            const double Mm = N / NK, LF = I / IK;
+            M.z[i] += fb * alpha * LF * (KN / (NK * NK));            // d f / d N
+            ub[1] += fb * 360.0 * Mm * LF;                            // d f / d alpha (alpha per day)
+            ub[4] += fb * alpha * LF * (-N / (NK * NK));              // d f / d K_N
+            ub[5] += fb * alpha * Mm * (-I / (IK * IK));              // d f / d K_I
+            ub[0] += fb * alpha * Mm * (KI / (IK * IK)) * (-__ldg(A.zc + cell) * I);   // d f / d k_w
+        }
+    }
+}
+
+// Reverse sweep over steps j0 + nsteps - 1 down to j0.  traj: the interleaved forward
+// states y_{j0} .. y_{j0+nsteps-1} (stride apart); ybar_in: cotangent of y_{j0+nsteps}; out:
+// cotangent of y_{j0}.  zb0, zb1: the interleaved ping-pong of zbar.  PT and RTp carry the
+// transposed operators (same layouts as the forward ones).
+template <int NTR, bool TRI>
+__device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, const ResidentParams &RTp,
+                                                      const SyncParams &S, const AdjointParams &A,
+                                                      const double *traj, long long stride,
+                                                      const double *ybar_in, double *out, double *zb0, double *zb1,
+                                                      int j0, int nsteps)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ int abort_flag;
+    __shared__ double red[kThreads / 32][7];
+    const int tile = blockIdx.x;
+    const Tile T = PT.tiles[tile];
+    const ResidentTile RT = RTp.rt[tile];
+    const ResidentLayout Ly = resident_layout(NTR, RTp.sp_max, RTp.bk_max, PT.zmax, TRI);
+    const TileSmem M = tile_smem(dsm, Ly, PT, T);
+    const int zmax = PT.zmax;
+    double ub[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+
+    copy_to_shared_int(M.si, PT.sp_col + RT.sp_base, RT.sp_n);
+    int exp_month = -1, imp_month = -1;
+    // zbar_{last} = B_last^T ybar_in on the tile's own cells
+    {
+        const int j = (j0 + nsteps - 1) % PT.nstep;
+        const int m = __ldg(PT.m0tab + j);
+        load_implicit_month<TRI>(PT, RTp, RT, T, RTp.tri, PT.bk_b, PT.bk_d, m, M);
+        imp_month = m;
+        for (int i = threadIdx.x; i < T.ncell; i += blockDim.x)
+            for (int t = 0; t < NTR; t++) M.z[t * zmax + i] = __ldcg(ybar_in + (size_t)(T.cell0 + i) * NTR + t);
+        __syncthreads();
+        implicit_resident<NTR, TRI>(PT, RTp, T, __ldg(PT.wtab + j), M, zb0);
+        __syncthreads();
+        if (threadIdx.x == 0 && tile != S.withhold_tile) store_release(S.flags + tile, 1);
+    }
+    bool aborted = false;
+    for (int s = 0; s < nsteps; s++) {
+        const int j = (j0 + nsteps - 1 - s) % PT.nstep;
+        const double *zb = (s & 1) ? zb1 : zb0;
+        double *zn = (s & 1) ? zb0 : zb1;
+        const double *y = traj + (long long)(nsteps - 1 - s) * stride;
+        const int m = __ldg(PT.m0tab + j);
+        if (m != exp_month) {
+            load_explicit_month(PT, RT, PT.sp_a, PT.sp_d, m, M);
+            exp_month = m;
+        }
+        if (threadIdx.x < 32) {
+            bool ok = wait_neighbours(S, tile, s + 1, s);
+            if (threadIdx.x == 0) abort_flag = ok ? 0 : 1;
+        }
+        __syncthreads();
+        if (abort_flag) { aborted = true; break; }
+        spmv_resident<NTR, false>(PT, T, __ldg(PT.wtab + j), zb, M);       // ybar_j = A_j^T zbar_j
+        __syncthreads();
+        ndop_source_adjoint_tile<NTR>(PT, A, T, j, y, zb, M, ub);           // + (d dq/dy)^T zbar_j
+        __syncthreads();
+        if (s + 1 < nsteps) {
+            const int jm = (j + PT.nstep - 1) % PT.nstep;
+            const int mm = __ldg(PT.m0tab + jm);
+            if (mm != imp_month) {
+                load_implicit_month<TRI>(PT, RTp, RT, T, RTp.tri, PT.bk_b, PT.bk_d, mm, M);
+                imp_month = mm;
+                __syncthreads();
+            }
+            implicit_resident<NTR, TRI>(PT, RTp, T, __ldg(PT.wtab + jm), M, zn);   // zbar_{j-1}
+        } else {
+            for (int i = threadIdx.x; i < T.ncell; i += blockDim.x) {
+                double v[NTR];
+                for (int t = 0; t < NTR; t++) v[t] = M.z[t * zmax + i];
+                store_cell<NTR>(out, T.cell0 + i, v);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && tile != S.withhold_tile) store_release(S.flags + tile, s + 2);
+    }
+    if (aborted) return;
+    // the tile's parameter gradient: fixed-order block reduction
+    for (int k = 0; k < 7; k++) {
+        double v = ub[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[w][threadIdx.x];
+        A.ubar_part[(size_t)tile * 8 + threadIdx.x] = v;
     }
 }
 

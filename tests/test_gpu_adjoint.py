@@ -1,0 +1,133 @@
+"""The adjoint year map on the GPU: against the oracle's adjoint, the GPU tangent (dot-product
+test), central finite differences of the parameter gradient, and through torch.autograd."""
+import numpy as np
+import pytest
+
+import m3d_inputs as mi
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def m3d():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1410_0204_gb300 as m
+    m.load()
+    return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("name", ["tiny_6x4x4", "ndop_64x32x8"])
+@pytest.mark.parametrize("form", ["tridiagonal", "dense"])
+def test_adjoint_matches_oracle(m3d, name, form):
+    p = mi.make_problem(name)
+    P = oracle.Problem(p)
+    u = mi.default_params_ndop()
+    y0 = mi.random_state(p)
+    wbar = mi.random_state(p, seed=8) - 1.0
+    ctx = m3d.Context.from_problem(p)
+    if form == "dense":
+        ctx.set_option(m3d.OPT_IMPLICIT_FORM, m3d.IMPLICIT_DENSE)
+    ybar0 = torch.empty((2, p.n), dtype=torch.float64, device="cuda")
+    ubar = ctx.year_adjoint(cuda(y0), cuda(u), cuda(wbar), ybar0)
+    want_y, want_u = oracle.year_adjoint(P, y0, u, wbar)
+    assert rel(ybar0.cpu().numpy(), want_y) < 1e-10
+    assert np.abs(ubar - want_u).max() <= 1e-9 * np.abs(want_u).max()
+    ctx.close()
+
+
+def test_adjoint_dot_product_with_gpu_tangent(m3d):
+    p = mi.make_problem("ndop_64x32x8")
+    u = cuda(mi.default_params_ndop())
+    y0 = cuda(mi.random_state(p))
+    v = cuda(mi.random_state(p, seed=5) - mi.random_state(p, seed=6))
+    w = cuda(mi.random_state(p, seed=8) - 1.0)
+    ctx = m3d.Context.from_problem(p)
+    phi = torch.empty_like(y0)
+    jv = torch.empty_like(y0)
+    ctx.year_tangent(y0, v, u, phi, jv)
+    wbar0 = torch.empty_like(y0)
+    ctx.year_adjoint(y0, u, w, wbar0)
+    ctx.sync()
+    lhs = float(torch.sum(w * jv))
+    rhs = float(torch.sum(wbar0 * v))
+    assert abs(lhs - rhs) <= 1e-12 * float(torch.sum(torch.abs(w) * torch.abs(jv)))
+    ctx.close()
+
+
+@pytest.mark.parametrize("ckpt", [240, 100, 2880])
+def test_checkpoint_interval_does_not_change_the_result(m3d, ckpt):
+    p = mi.make_problem("tiny_6x4x4")
+    u = cuda(mi.default_params_ndop())
+    y0 = cuda(mi.random_state(p))
+    w = cuda(mi.random_state(p, seed=8) - 1.0)
+    ctx = m3d.Context.from_problem(p)
+    ref = torch.empty_like(y0)
+    ub_ref = ctx.year_adjoint(y0, u, w, ref, 240)
+    got = torch.empty_like(y0)
+    ub = ctx.year_adjoint(y0, u, w, got, ckpt)
+    assert torch.equal(ref, got)
+    # the parameter gradient is summed segment by segment: equal up to the grouping of the sum
+    assert np.allclose(ub, ub_ref, rtol=1e-13, atol=0)
+    ctx.close()
+
+
+def test_misfit_gradient_matches_central_differences(m3d):
+    """The parameter optimisation's gradient: J(u) = 1/2 |M (phi(y0; u) - obs)|^2 on a random 10 %
+    of the cells, observations from perturbed parameters plus 5 % noise."""
+    p = mi.make_problem("ndop_64x32x8")
+    r = mi.rng(1410, "observations")
+    u0 = mi.default_params_ndop()
+    y0 = cuda(mi.random_state(p))
+    ctx = m3d.Context.from_problem(p)
+    mask = torch.from_numpy((r.random((2, p.n)) < 0.1).astype(np.float64)).cuda()
+    u_true = cuda(u0 * r.uniform(0.8, 1.2, 7))
+    obs = torch.empty_like(y0)
+    ctx.year_map(y0, obs, u_true)
+    obs = obs * cuda(1.0 + 0.05 * r.standard_normal((2, p.n)))
+    u = cuda(u0)
+
+    def J(uu):
+        y1 = torch.empty_like(y0)
+        ctx.year_map(y0, y1, uu)
+        return 0.5 * float(torch.sum((mask * (y1 - obs)) ** 2))
+
+    y1 = torch.empty_like(y0)
+    ctx.year_map(y0, y1, u)
+    ybar1 = mask * mask * (y1 - obs)
+    ybar0 = torch.empty_like(y0)
+    grad = ctx.year_adjoint(y0, u, ybar1, ybar0)
+    for k in range(7):
+        e = 1e-6 * u0[k]
+        up, um = u0.copy(), u0.copy()
+        up[k] += e
+        um[k] -= e
+        fd = (J(cuda(up)) - J(cuda(um))) / (2 * e)
+        assert abs(grad[k] - fd) <= 1e-5 * abs(fd) + 1e-9 * abs(J(u)), (k, grad[k], fd)
+    ctx.close()
+
+
+def test_autograd_function(m3d):
+    p = mi.make_problem("tiny_6x4x4")
+    ctx = m3d.Context.from_problem(p)
+    y0 = cuda(mi.random_state(p)).requires_grad_(True)
+    u = cuda(mi.default_params_ndop()).requires_grad_(True)
+    w = cuda(mi.random_state(p, seed=8) - 1.0)
+    y1 = m3d.year_map_autograd(y0, u, ctx)
+    loss = torch.sum(w * y1)
+    loss.backward()
+    ybar0 = torch.empty_like(w)
+    ubar = ctx.year_adjoint(y0.detach(), u.detach(), w, ybar0)
+    assert torch.equal(y0.grad, ybar0)
+    assert np.array_equal(u.grad.cpu().numpy(), ubar)
+    ctx.close()
