@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible mistakes.
 
-Each case plants one mistake in a copy of the oracle's C source (on the CPU only),
-builds it, and runs the pin suite against it: the suite must fail for every mutant.
+Each case plants one mistake in a copy of the oracle's C source (on the CPU only), in the
+forward model, builds it, and runs the pin suite against it: the suite must fail for
+every mutant.
 """
 import os
 import subprocess
@@ -38,9 +39,10 @@ MUTANTS = {
 def test_pins_catch_mutant(name, tmp_path):
     old, new = MUTANTS[name]
     text = open(SRC).read()
-    assert text.count(old) == 1, "mutation site not found: %s" % name
+    assert old in text, "mutation site not found: %s" % name
+    # the first occurrence is in the forward model (its tangent and adjoint follow later)
     mutated = tmp_path / "tmm_oracle_mut.c"
-    mutated.write_text(text.replace(old, new))
+    mutated.write_text(text.replace(old, new, 1))
     lib = tmp_path / "liboracle_mut.so"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
                            "-o", str(lib), str(mutated), "-lm"])
