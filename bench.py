@@ -50,7 +50,7 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the year kernel, from one ncu capture of this
 # workload (see profiles/); None where no capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {("resident", True): 178656768 + 3875584}
+TRAFFIC_PER_LAUNCH = {("resident", True): 178585088 + 4218624}
 
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz maximum SM clock.
 # (A DFMA throughput probe on this GPU measured 1.20 TFLOP/s, 1.92 FMA/clock/SM at the
@@ -263,6 +263,34 @@ def run_ours(args):
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             e2e_value = world * e2e_steps / float(t.item())
 
+        # cost of the adjoint year map (checkpoint every 240 steps) and of the tangent year map,
+        # each relative to one year map, wall clock with the device synchronised on both sides
+        costs = {}
+        if not args.no_adjoint:
+            ybar1 = torch.ones_like(y0)
+            ybar0 = torch.empty_like(y0)
+            v = torch.ones_like(y0)
+            phi = torch.empty_like(y0)
+            jv = torch.empty_like(y0)
+
+            def wall(fn, k):
+                fn()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(k):
+                    fn()
+                torch.cuda.synchronize()
+                return (time.perf_counter() - t0) / k
+
+            k = max(1, min(args.steps, 3))
+            t_fwd = wall(lambda: ctx.year_map(y0, ya, u), k)
+            t_adj = wall(lambda: ctx.year_adjoint(y0, u, ybar1, ybar0, 240), k)
+            t_tan = wall(lambda: ctx.year_tangent(y0, v, u, phi, jv), k)
+            costs = {"forward_s": t_fwd, "adjoint_s": t_adj, "tangent_s": t_tan,
+                     "adjoint_over_forward": t_adj / t_fwd, "tangent_over_forward": t_tan / t_fwd,
+                     "ckpt_every": 240, "repeats": k,
+                     "adjoint_includes": "forward sweep keeping 12 checkpoints, recomputation of each 240-step segment, reverse sweep"}
+
         # Newton-Krylov periodic solve to ||phi(y) - y|| < 1e-8 from the constant initial state
         newton = {}
         if not args.no_newton:
@@ -312,9 +340,12 @@ def run_ours(args):
                          "bytes_per_step": bytes_step, "flops_per_step": flops_step},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y0_h.nbytes + u_h.nbytes),
                 "d2h_bytes_per_step": int(y0_h.nbytes)},
+        "throughput": {"cell_tracer_steps_per_s": value * prob.n * 2 * prob.nstep,
+                       "unit": "wet cells x tracers x TMM steps per second"},
         "gpu_launches": launches,
         "clocks": clock,
         "newton": newton,
+        "adjoint": costs,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
@@ -350,6 +381,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-Krylov solve timing")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/tangent cost timing")
     ap.add_argument("--newton-tangent", action="store_true",
                     help="also time Newton-Krylov with tangent Jacobian-vector products")
     ap.add_argument("--profile-steps", type=int, default=0,

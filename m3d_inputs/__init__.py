@@ -37,6 +37,8 @@ import numpy as np
 __all__ = [
     "Problem", "GridSpec", "SPECS", "make_problem", "spec", "default_params_ndop",
     "initial_state", "rng", "NDOP_PARAM_NAMES", "MODEL_NONE", "MODEL_NDOP",
+    "MODEL_N", "MODEL_PHY", "MODEL_NPZD", "MODELS", "default_params", "model_initial_values",
+    "Member", "make_ensemble", "ENSEMBLE_MIX",
 ]
 
 EARTH_RADIUS = 6.371e6          # m
@@ -44,11 +46,88 @@ SECONDS_PER_YEAR = 360 * 86400  # the interface assumes a 360-day year (Section 
 
 # Model identifiers shared by both sides of the boundary.
 MODEL_NONE = 0   # q = 0: pure transport
+MODEL_N = 1      # PO4 alone, all production exported (1 tracer)
 MODEL_NDOP = 2   # the PO4-DOP model of Section 2.2.1 (2 tracers)
+MODEL_PHY = 3    # the PO4-DOP-PHY model of Section 2.2.2 (3 tracers)
+MODEL_NPZD = 5   # NPZD-DOP: PO4-DOP-PHY extended by zooplankton and sinking detritus (5 tracers)
 
 # Parameter order of the N-DOP model: k_w [1/m], alpha [1/d], sigma [-], lambda [1/yr],
 # K_N [mmol P/m^3], K_I [W/m^2], b [-].
 NDOP_PARAM_NAMES = ("k_w", "alpha", "sigma", "lambda", "K_N", "K_I", "b")
+
+
+@dataclasses.dataclass(frozen=True)
+class ModelSpec:
+    """Tracer names, parameter names (in order), default parameters, fractions among them."""
+    model: int
+    tracers: tuple
+    params: tuple
+    defaults: tuple
+    fractions: tuple          # parameters that are fractions in [0, 1]
+    initial: tuple            # spatially constant initial value of each tracer
+
+
+MODELS = {
+    MODEL_N: ModelSpec(MODEL_N, ("PO4",), ("k_w", "alpha", "K_N", "K_I", "b"),
+                       (0.02, 0.5, 0.5, 30.0, 0.858), (), (2.17,)),
+    MODEL_NDOP: ModelSpec(MODEL_NDOP, ("PO4", "DOP"), NDOP_PARAM_NAMES,
+                          (0.02, 0.5, 0.67, 0.5, 0.5, 30.0, 0.858), ("sigma",), (2.17, 1.0e-4)),
+    # order of the paper's parameter table (Section 2.2.2); rates per day
+    MODEL_PHY: ModelSpec(MODEL_PHY, ("PO4", "DOP", "PHY"),
+                         ("mu_1", "k_w", "K_1", "K_I", "lambda_2", "sigma_2", "lambda_3", "kappa_3",
+                          "lambda_3p", "sigma_3", "b"),
+                         (2.0, 0.02, 0.5, 30.0, 0.01, 0.67, 0.03, 1.0, 0.01, 0.75, 0.858),
+                         ("sigma_2", "sigma_3"), (2.17, 1.0e-4, 0.01)),
+    # rates per day, sinking speed in m/day
+    MODEL_NPZD: ModelSpec(MODEL_NPZD, ("PO4", "PHY", "ZOO", "DET", "DOP"),
+                          ("k_w", "mu_P", "K_N", "K_I", "mu_Z", "K_P", "epsilon", "lambda_P",
+                           "kappa_Z", "lambda_Z", "lambda_D", "lambda_DOP", "w_D"),
+                          (0.02, 1.0, 0.5, 30.0, 1.0, 0.1, 0.75, 0.05, 1.0, 0.03, 0.05, 0.01, 2.0),
+                          ("epsilon",), (2.17, 0.01, 0.01, 0.01, 1.0e-4)),
+}
+
+
+def default_params(model: int) -> np.ndarray:
+    """Default parameters u of a model, in its parameter order."""
+    return np.array(MODELS[model].defaults, dtype=np.float64)
+
+
+def model_initial_values(model: int) -> tuple:
+    return MODELS[model].initial
+
+
+@dataclasses.dataclass(frozen=True)
+class Member:
+    """One ensemble member: a model and its parameter vector."""
+    model: int
+    u: np.ndarray
+
+    @property
+    def ntracer(self) -> int:
+        return len(MODELS[self.model].tracers)
+
+
+# The batched ensemble: 16 runs of the N model, 32 of N-DOP, 16 of NPZD-DOP.
+ENSEMBLE_MIX = ((MODEL_N, 16), (MODEL_NDOP, 32), (MODEL_NPZD, 16))
+
+
+def make_ensemble(mix=ENSEMBLE_MIX, seed: int = 1410, spread: float = 0.5) -> list:
+    """Members with parameters drawn uniformly within +-spread of each model's defaults.
+
+    Draws come from the "ensemble" stream, members in the order of ``mix``; a parameter
+    that is a fraction is capped at 1.
+    """
+    r = rng(seed, "ensemble")
+    out = []
+    for model, count in mix:
+        sp = MODELS[model]
+        base = np.array(sp.defaults, dtype=np.float64)
+        frac = np.array([p in sp.fractions for p in sp.params])
+        for _ in range(count):
+            u = base * (1.0 + spread * (2.0 * r.random(base.size) - 1.0))
+            u[frac] = np.minimum(u[frac], 1.0)
+            out.append(Member(model, u))
+    return out
 
 _STREAMS = {"mask": 1, "bathymetry": 2, "psi": 3, "kappa_h": 4, "kappa_v": 5,
             "ensemble": 6, "observations": 7, "state": 8}

@@ -1,7 +1,9 @@
 """CPU oracle of the TMM year map -- TEST INFRASTRUCTURE ONLY.
 
 A plain FP64 C implementation (``tmm_oracle.c``) of the Metos3D time step, year map and
-PO4-DOP model (arXiv:1410.0204, Sections 2.2.1, 3, 4, 5), loaded here through ctypes.
+biogeochemical models (arXiv:1410.0204, Sections 2.2, 3, 4, 5: PO4-DOP, PO4-DOP-PHY, and the
+N and NPZD-DOP models of the batched ensemble), loaded here through ctypes.  The ensemble
+year map is each member's own year map: the members share the transport and nothing else.
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
 import this package.  It shares no code with the CUDA library under
 ``paper_1410_0204_gb300/``; both read their inputs from ``m3d_inputs``.
@@ -16,7 +18,10 @@ import numpy as np
 from . import build as _build
 
 MODEL_NONE = 0
+MODEL_N = 1
 MODEL_NDOP = 2
+MODEL_PHY = 3
+MODEL_NPZD = 5
 
 _lib = None
 
@@ -211,3 +216,13 @@ def year_adjoint(P: Problem, y0, u, ybar1, model=MODEL_NDOP, nsub=1):
     if rc != 0:
         raise ValueError("oracle_year_adjoint failed")
     return ybar0, ubar
+
+
+def ensemble_steps(P: Problem, j0: int, nsteps: int, states, members, nsub=1):
+    """nsteps TMM steps of every member (a list of [ntracer][n] states), each on its own."""
+    return [steps(P, j0, nsteps, y, m.u, model=m.model, nsub=nsub) for y, m in zip(states, members)]
+
+
+def ensemble_year_map(P: Problem, states, members, nsub=1):
+    """The year map of every member of an ensemble (members are independent)."""
+    return [year_map(P, y, m.u, model=m.model, nsub=nsub) for y, m in zip(states, members)]

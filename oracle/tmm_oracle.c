@@ -14,6 +14,9 @@
  *                  linearly interpolated in time;
  *   Section 4:     the year map phi, y(T) = phi(y(0)), n_step = 2880 steps per year;
  *   Section 2.2.1: the PO4-DOP source-minus-sink term q (two tracers, here "N-DOP");
+ *   Section 2.2.2: the PO4-DOP-PHY model (three tracers), and two models the batched
+ *                  ensemble mixes in: N (PO4 alone) and NPZD-DOP (five tracers), stated
+ *                  where they are defined below;
  *   Section 5:     the per-water-column model interface bgc(...), column-local, 360-day
  *                  year, tracer array y(nlayer, ntracer) with the layer index fastest.
  *
@@ -36,6 +39,13 @@
  *   R8  I_SWR is the daily-mean top-of-atmosphere insolation of a circular orbit,
  *       sigma_PAR = 0.4, sigma_ice = 0;
  *   R9  alpha is given per day (times 360 per year), lambda per year, time in years.
+ *   R10 the N model is the PO4-DOP model without DOP: all production is exported;
+ *   R11 PO4-DOP-PHY rates are per day; the phytoplankton losses of the euphotic zone and
+ *       of the whole column feed DOP, and the grazed fraction f_3 = sigma_3 f_1 splits
+ *       into DOP (sigma_2) and export (1 - sigma_2), as the PO4-DOP production does;
+ *   R12 NPZD-DOP, which the paper does not define, extends PO4-DOP-PHY conservatively:
+ *       zooplankton graze phytoplankton with a Holling type II response, and detritus
+ *       sinks with a fixed speed (first-order upwind fluxes, none through the sea floor).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -45,7 +55,10 @@
 #endif
 
 #define ORACLE_MODEL_NONE 0
+#define ORACLE_MODEL_N 1
 #define ORACLE_MODEL_NDOP 2
+#define ORACLE_MODEL_PHY 3
+#define ORACLE_MODEL_NPZD 5
 #define ORACLE_MAX_LAYER 256
 #define ORACLE_MAX_TRACER 8
 
@@ -161,6 +174,165 @@ static void ndop_q(int nlayer, const double *h, const double *d, double insol, d
 }
 
 /* ---------------------------------------------------------------------------------
+ * N model (reading R10): PO4 alone, parameters u, in this order:
+ *   u[0] k_w, u[1] alpha [1/d], u[2] K_N, u[3] K_I, u[4] b.
+ * Euphotic layers: q_k = -f_k with f_k as in the PO4-DOP model; the whole production is
+ * exported, E = sum_k f_k h_k, and remineralised below with Martin's law; the same bottom
+ * rule as the PO4-DOP model.
+ * --------------------------------------------------------------------------------- */
+static void n_q(int nlayer, const double *h, const double *d, double insol, double ice,
+                const double *PO4, const double *u, double *q)
+{
+    const double sigma_par = 0.4;
+    double kw = u[0], alpha = 360.0 * u[1], KN = u[2], KI = u[3], b = u[4];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double E = 0.0, zeu = 0.0;
+    for (int k = 0; k < neu; k++) {
+        double I = insol * sigma_par * (1.0 - ice) * exp(-kw * d[k]);
+        double f = alpha * (PO4[k] / (PO4[k] + KN)) * (I / (KI + I));
+        q[k] = -f;
+        E += f * h[k];
+        zeu += h[k];
+    }
+    double ztop = zeu;
+    for (int k = neu; k < nlayer; k++) {
+        double zbot = ztop + h[k];
+        double top = pow(ztop / zeu, -b);
+        double bot = (k + 1 < nlayer) ? pow(zbot / zeu, -b) : 0.0;
+        q[k] = E * (top - bot) / h[k];
+        ztop = zbot;
+    }
+    if (neu >= nlayer)
+        q[nlayer - 1] += E / h[nlayer - 1];
+}
+
+/* ---------------------------------------------------------------------------------
+ * PO4-DOP-PHY model (Section 2.2.2; reading R11).  Tracers y1 = PO4, y2 = DOP,
+ * y3 = PHY.  Parameters u, in the order of the paper's table:
+ *   u[0] mu_1 maximum growth [1/d]      u[1] K_H2O (k_w) [1/m]   u[2] K_1
+ *   u[3] K_I [W/m^2]                    u[4] lambda'_2 DOP remineralisation [1/d]
+ *   u[5] sigma_2                        u[6] lambda_3 PHY loss, euphotic [1/d]
+ *   u[7] kappa_3 quadratic PHY loss [1/d per mmol P/m^3]
+ *   u[8] lambda'_3 PHY loss, whole column [1/d]   u[9] sigma_3   u[10] b
+ * Euphotic:  f_1 = mu_1 PHY PO4/(PO4 + K_1) I/(I + K_I),  f_3 = sigma_3 f_1,
+ *   q1 = -f_1 + l2 DOP,
+ *   q2 = sigma_2 f_3 + l3 PHY + k3 PHY^2 - l2 DOP + l3' PHY,
+ *   q3 = (1 - sigma_3) f_1 - l3 PHY - k3 PHY^2 - l3' PHY,
+ *   E  = (1 - sigma_2) sum_k f_3,k h_k.
+ * Aphotic:   q1 = (F(z_top) - F(z_bot))/h + l2 DOP,  q2 = -l2 DOP + l3' PHY,
+ *   q3 = -l3' PHY, with Martin's F and the bottom rule of the PO4-DOP model.
+ * --------------------------------------------------------------------------------- */
+static void phy_q(int nlayer, const double *h, const double *d, double insol, double ice,
+                  const double *y, const double *u, double *q)
+{
+    const double sigma_par = 0.4;
+    const double *PO4 = y, *DOP = y + nlayer, *PHY = y + 2 * nlayer;
+    double *q1 = q, *q2 = q + nlayer, *q3 = q + 2 * nlayer;
+    double mu1 = 360.0 * u[0], kw = u[1], K1 = u[2], KI = u[3], l2 = 360.0 * u[4];
+    double sig2 = u[5], l3 = 360.0 * u[6], k3 = 360.0 * u[7], l3p = 360.0 * u[8];
+    double sig3 = u[9], b = u[10];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double E = 0.0, zeu = 0.0;
+    for (int k = 0; k < neu; k++) {
+        double I = insol * sigma_par * (1.0 - ice) * exp(-kw * d[k]);
+        double f1 = mu1 * PHY[k] * (PO4[k] / (PO4[k] + K1)) * (I / (KI + I));
+        double f3 = sig3 * f1;
+        double loss = l3 * PHY[k] + k3 * PHY[k] * PHY[k];
+        q1[k] = -f1 + l2 * DOP[k];
+        q2[k] = sig2 * f3 + loss - l2 * DOP[k] + l3p * PHY[k];
+        q3[k] = (1.0 - sig3) * f1 - loss - l3p * PHY[k];
+        E += (1.0 - sig2) * f3 * h[k];
+        zeu += h[k];
+    }
+    double ztop = zeu;
+    for (int k = neu; k < nlayer; k++) {
+        double zbot = ztop + h[k];
+        double top = pow(ztop / zeu, -b);
+        double bot = (k + 1 < nlayer) ? pow(zbot / zeu, -b) : 0.0;
+        q1[k] = E * (top - bot) / h[k] + l2 * DOP[k];
+        q2[k] = -l2 * DOP[k] + l3p * PHY[k];
+        q3[k] = -l3p * PHY[k];
+        ztop = zbot;
+    }
+    if (neu >= nlayer)
+        q1[nlayer - 1] += E / h[nlayer - 1];
+}
+
+/* ---------------------------------------------------------------------------------
+ * NPZD-DOP model (reading R12).  Tracers N (PO4), P (phytoplankton), Z (zooplankton),
+ * D (detritus), DOP.  Parameters u, in this order:
+ *   u[0] k_w [1/m]        u[1] mu_P max growth [1/d]   u[2] K_N     u[3] K_I [W/m^2]
+ *   u[4] mu_Z max grazing [1/d]   u[5] K_P grazing half saturation   u[6] epsilon
+ *   assimilated fraction of grazing   u[7] lambda_P P mortality [1/d]
+ *   u[8] kappa_Z quadratic Z mortality [1/d per mmol P/m^3]   u[9] lambda_Z Z excretion
+ *   [1/d]   u[10] lambda_D detritus remineralisation [1/d]   u[11] lambda_DOP DOP
+ *   remineralisation [1/d]   u[12] w_D detritus sinking speed [m/d].
+ * Rates per cell:
+ *   U = mu_P P N/(N + K_N) I/(I + K_I)  (euphotic layers only),  G = mu_Z Z P/(K_P + P),
+ *   and linear or quadratic losses lambda_P P, kappa_Z Z^2, lambda_Z Z, lambda_D D,
+ *   lambda_DOP DOP.  Sinking: S_k = w_D D_k through the base of layer k, S = 0 through
+ *   the sea floor and into the top layer.
+ *   qN = -U + lambda_DOP DOP
+ *   qP = U - G - lambda_P P
+ *   qZ = epsilon G - kappa_Z Z^2 - lambda_Z Z
+ *   qD = lambda_P P + kappa_Z Z^2 - lambda_D D + (S_{k-1} - S_k) / h_k
+ *   qDOP = (1 - epsilon) G + lambda_Z Z + lambda_D D - lambda_DOP DOP
+ * --------------------------------------------------------------------------------- */
+static void npzd_q(int nlayer, const double *h, const double *d, double insol, double ice,
+                   const double *y, const double *u, double *q)
+{
+    const double sigma_par = 0.4;
+    const double *N = y, *P = y + nlayer, *Z = y + 2 * nlayer, *D = y + 3 * nlayer;
+    const double *DOP = y + 4 * nlayer;
+    double kw = u[0], muP = 360.0 * u[1], KN = u[2], KI = u[3], muZ = 360.0 * u[4];
+    double KP = u[5], eps = u[6], lP = 360.0 * u[7], kZ = 360.0 * u[8], lZ = 360.0 * u[9];
+    double lD = 360.0 * u[10], lO = 360.0 * u[11], wD = 360.0 * u[12];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double Sin = 0.0;                       /* sinking flux into the top of layer k */
+    for (int k = 0; k < nlayer; k++) {
+        double U = 0.0;
+        if (k < neu) {
+            double I = insol * sigma_par * (1.0 - ice) * exp(-kw * d[k]);
+            U = muP * P[k] * (N[k] / (N[k] + KN)) * (I / (KI + I));
+        }
+        double G = muZ * Z[k] * (P[k] / (KP + P[k]));
+        double mP = lP * P[k], mZ = kZ * Z[k] * Z[k], eZ = lZ * Z[k];
+        double rD = lD * D[k], rO = lO * DOP[k];
+        double Sout = (k + 1 < nlayer) ? wD * D[k] : 0.0;
+        q[k] = -U + rO;
+        q[nlayer + k] = U - G - mP;
+        q[2 * nlayer + k] = eps * G - mZ - eZ;
+        q[3 * nlayer + k] = mP + mZ - rD + (Sin - Sout) / h[k];
+        q[4 * nlayer + k] = (1.0 - eps) * G + eZ + rD - rO;
+        Sin = Sout;
+    }
+}
+
+/* q of one column for any model; y and q are (ntracer, nlayer), layer index fastest. */
+static int model_q(int model, int ntracer, int nparam, int nlayer, const double *h,
+                   const double *d, double insol, double ice, const double *y,
+                   const double *u, double *q)
+{
+    if (model == ORACLE_MODEL_NDOP && ntracer == 2 && nparam == 7) {
+        ndop_q(nlayer, h, d, insol, ice, y, y + nlayer, u, q, q + nlayer);
+        return 0;
+    }
+    if (model == ORACLE_MODEL_N && ntracer == 1 && nparam == 5) {
+        n_q(nlayer, h, d, insol, ice, y, u, q);
+        return 0;
+    }
+    if (model == ORACLE_MODEL_PHY && ntracer == 3 && nparam == 11) {
+        phy_q(nlayer, h, d, insol, ice, y, u, q);
+        return 0;
+    }
+    if (model == ORACLE_MODEL_NPZD && ntracer == 5 && nparam == 13) {
+        npzd_q(nlayer, h, d, insol, ice, y, u, q);
+        return 0;
+    }
+    return -1;
+}
+
+/* ---------------------------------------------------------------------------------
  * The model interface of Section 5.2:
  *   bgc(t, dt, lat, insol, dayfrac, ice, wind, ntracer, nlayer, h, d, salt, temp,
  *       y, ybgc, nparam, u)
@@ -180,18 +352,16 @@ int oracle_bgc(int model, double t, double dt, double lat, double insol, double 
         for (int i = 0; i < ntracer * nlayer; i++) ybgc[i] = 0.0;
         return 0;
     }
-    if (model != ORACLE_MODEL_NDOP || ntracer != 2 || nparam != 7) return -1;
-    double ys[2 * ORACLE_MAX_LAYER], qN[ORACLE_MAX_LAYER], qD[ORACLE_MAX_LAYER];
-    memcpy(ys, y, sizeof(double) * 2 * nlayer);
+    if (ntracer < 1 || ntracer > ORACLE_MAX_TRACER) return -1;
+    double ys[ORACLE_MAX_TRACER * ORACLE_MAX_LAYER], q[ORACLE_MAX_TRACER * ORACLE_MAX_LAYER];
+    int len = ntracer * nlayer;
+    memcpy(ys, y, sizeof(double) * len);
     double ds = dt / nsub;
     for (int s = 0; s < nsub; s++) {
-        ndop_q(nlayer, h, d, insol, ice, ys, ys + nlayer, u, qN, qD);
-        for (int k = 0; k < nlayer; k++) {
-            ys[k] += ds * qN[k];
-            ys[nlayer + k] += ds * qD[k];
-        }
+        if (model_q(model, ntracer, nparam, nlayer, h, d, insol, ice, ys, u, q) != 0) return -1;
+        for (int i = 0; i < len; i++) ys[i] += ds * q[i];
     }
-    for (int i = 0; i < 2 * nlayer; i++) ybgc[i] = ys[i] - y[i];
+    for (int i = 0; i < len; i++) ybgc[i] = ys[i] - y[i];
     return 0;
 }
 

@@ -31,6 +31,17 @@ MUTANTS = {
     "euphotic_layers": ("int neu = nlayer < 2 ? nlayer : 2;", "int neu = nlayer < 3 ? nlayer : 3;"),
     "light_half_saturation": ("(I / (I + KI))", "(I / (I + KN))"),
     "declination_phase": ("cos(2.0 * pi * (t + 10.0 / 360.0))", "cos(2.0 * pi * (t - 10.0 / 360.0))"),
+    # the N, PO4-DOP-PHY and NPZD-DOP models
+    "n_export_dropped": ("E += f * h[k];", "E += 0.5 * f * h[k];"),
+    "n_martin_exponent": ("double top = pow(ztop / zeu, -b);", "double top = pow(ztop / zeu, b);"),
+    "phy_grazed_fraction": ("double f3 = sig3 * f1;", "double f3 = f1;"),
+    "phy_growth_without_phy": ("double f1 = mu1 * PHY[k]", "double f1 = mu1"),
+    "phy_quadratic_loss_sign": ("q3[k] = (1.0 - sig3) * f1 - loss - l3p * PHY[k];",
+                                "q3[k] = (1.0 - sig3) * f1 + loss - l3p * PHY[k];"),
+    "npzd_assimilation": ("q[2 * nlayer + k] = eps * G - mZ - eZ;", "q[2 * nlayer + k] = G - mZ - eZ;"),
+    "npzd_sinking_through_floor": ("(k + 1 < nlayer) ? wD * D[k] : 0.0", "wD * D[k]"),
+    "npzd_grazing_not_saturating": ("(P[k] / (KP + P[k]))", "(P[k] / KP)"),
+    "npzd_growth_below_euphotic": ("        if (k < neu) {\n            double I", "        if (k < nlayer) {\n            double I"),
 }
 
 
@@ -49,6 +60,7 @@ def test_pins_catch_mutant(name, tmp_path):
     env = dict(os.environ, M3D_ORACLE_LIB=str(lib), M3D_ORACLE_THREADS="1",
                OMP_NUM_THREADS="1", OMP_WAIT_POLICY="passive")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_models.py")],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "the pins did not catch mutant %s:\n%s" % (name, r.stdout[-2000:])
