@@ -58,6 +58,85 @@ TRAFFIC_PER_LAUNCH = {("resident", True): 178585088 + 4218624}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+# FP64 flops per cell of the source terms, per member: (euphotic cell, aphotic cell).  A division
+# counts as one flop here (the algorithmic count, not the instruction cost).
+Q_FLOPS = {1: (12, 2), 2: (18, 6), 3: (30, 10), 5: (40, 30)}
+
+
+def ensemble_flops_per_step(prob, members):
+    """Algorithmic FP64 flops of one ensemble step: the interpolation of each explicit entry
+    once (2), one multiply-add per entry and tracer (2 W), the Thomas solves of both months
+    and their blend per cell and tracer (13 W), the source terms per member and cell, and the
+    increment added to each tracer (2 W per cell)."""
+    W = sum(m.ntracer for m in members)
+    L = prob.nlayer
+    n_eu = int(np.minimum(L, 2).sum())
+    q = sum(Q_FLOPS[m.ntracer][0] * n_eu + Q_FLOPS[m.ntracer][1] * (prob.n - n_eu) for m in members)
+    return prob.nnz * (2 + 2 * W) + 13 * prob.n * W + q + 2 * prob.n * W
+
+
+def run_ensemble(prob, t_single_ndop, flush):
+    """The batched 64-member ensemble (16 N, 32 N-DOP, 16 NPZD-DOP) against the same members
+    run one at a time: N-DOP members by the single-context year map, N and NPZD-DOP members
+    (which only ensembles run) as one-member ensembles."""
+    import torch
+    import paper_1410_0204_gb300 as m3d
+    members = mi.make_ensemble()
+    ens = m3d.Ensemble.from_problem(prob, members)
+    Y0 = torch.from_numpy(np.vstack([mi.initial_state(prob, m.ntracer, mi.model_initial_values(m.model))
+                                     for m in members])).cuda()
+    Y1 = torch.empty_like(Y0)
+    cpb, nw, ms_tune = ens.autotune(Y0, nsteps=20)
+
+    def year_time(e, Y, Yo, reps):
+        e.year_map(Y, Yo)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            e.year_map(Y, Yo)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return sum(ts) / len(ts)
+
+    t_ens = year_time(ens, Y0, Y1, 3)
+    launches = ens.last_launch_count()
+    ens.close()
+    singles = {}
+    for model in (mi.MODEL_N, mi.MODEL_NPZD):
+        one = m3d.Ensemble.from_problem(prob, [mi.Member(model, mi.default_params(model))])
+        y = torch.from_numpy(mi.initial_state(prob, one.width, mi.model_initial_values(model))).cuda()
+        one.autotune(y, nsteps=10)
+        singles[model] = year_time(one, y, torch.empty_like(y), 2)
+        one.close()
+    counts = {}
+    for m in members:
+        counts[m.model] = counts.get(m.model, 0) + 1
+    t_seq = counts[mi.MODEL_N] * singles[mi.MODEL_N] + counts[mi.MODEL_NDOP] * t_single_ndop + \
+        counts[mi.MODEL_NPZD] * singles[mi.MODEL_NPZD]
+    flops = ensemble_flops_per_step(prob, members) * prob.nstep
+    W = sum(m.ntracer for m in members)
+    return {
+        "workload": "64 members on %s: 16 N (1 tracer), 32 N-DOP (2), 16 NPZD-DOP (5), parameters within "
+                    "+-50%% of the defaults; W = %d tracers in 5 lane groups" % (WORKLOAD, W),
+        "member_years_per_s": len(members) / t_ens, "seconds_per_ensemble_year": t_ens,
+        "cell_tracer_steps_per_s": prob.n * W * prob.nstep / t_ens,
+        "tiling": {"cols_per_block": cpb, "warps_per_block": nw, "autotune_ms_per_step": ms_tune},
+        "launches_per_year": launches,
+        "roofline": {"bound": "alu", "achieved": flops / t_ens / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flops / t_ens / 1e12 / FP64_PEAK_TFLOPS, "kernel": "k_ens_step (one launch per TMM step)"},
+        "sequential_single_instance": {
+            "seconds": t_seq, "n_years_per_s": 1.0 / singles[mi.MODEL_N], "ndop_years_per_s": 1.0 / t_single_ndop,
+            "npzd_years_per_s": 1.0 / singles[mi.MODEL_NPZD],
+            "how": "N-DOP: single-context year map (resident kernel); N and NPZD-DOP: one-member ensembles"},
+        "speedup_vs_sequential": t_seq / t_ens,
+    }
+
+
 def algorithmic_per_step(prob, ntr=2, tridiagonal=False):
     """Algorithmic bytes and FP64 flops of one TMM step.
 
@@ -291,6 +370,10 @@ def run_ours(args):
                      "ckpt_every": 240, "repeats": k,
                      "adjoint_includes": "forward sweep keeping 12 checkpoints, recomputation of each 240-step segment, reverse sweep"}
 
+        ensemble = {}
+        if not args.no_ensemble:
+            ensemble = run_ensemble(prob, total / args.steps, flush)
+
         # Newton-Krylov periodic solve to ||phi(y) - y|| < 1e-8 from the constant initial state
         newton = {}
         if not args.no_newton:
@@ -346,6 +429,7 @@ def run_ours(args):
         "clocks": clock,
         "newton": newton,
         "adjoint": costs,
+        "ensemble": ensemble,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
@@ -382,6 +466,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-Krylov solve timing")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/tangent cost timing")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched ensemble timing")
     ap.add_argument("--newton-tangent", action="store_true",
                     help="also time Newton-Krylov with tangent Jacobian-vector products")
     ap.add_argument("--profile-steps", type=int, default=0,

@@ -42,10 +42,17 @@ typedef enum {
     M3D_ERR_UNSUPPORTED = -5    /* a valid request this build does not implement */
 } m3d_status;
 
-/* Biogeochemical models (Section 2.2). */
+/*
+ * Biogeochemical models (Section 2.2).  A single context (metos3d_init) runs NONE and NDOP;
+ * ensembles (metos3d_ensemble_init) run N, NDOP, PHY and NPZD members side by side.
+ */
 enum {
     M3D_MODEL_NONE = 0,         /* q = 0: pure transport, any number of tracers */
-    M3D_MODEL_NDOP = 2          /* PO4-DOP (Section 2.2.1): 2 tracers, 7 parameters */
+    M3D_MODEL_N = 1,            /* PO4 alone, all production exported: 1 tracer, 5 parameters */
+    M3D_MODEL_NDOP = 2,         /* PO4-DOP (Section 2.2.1): 2 tracers, 7 parameters */
+    M3D_MODEL_PHY = 3,          /* PO4-DOP-PHY (Section 2.2.2): 3 tracers, 11 parameters */
+    M3D_MODEL_NPZD = 5          /* NPZD-DOP: PO4-DOP-PHY with zooplankton grazing (Holling II) and
+                                   sinking detritus: 5 tracers, 13 parameters */
 };
 
 #define M3D_MAX_LAYERS 64       /* deepest water column accepted */
@@ -307,6 +314,102 @@ typedef struct {
 void metos3d_newton_default_options(m3d_newton_opts *opts);
 m3d_status metos3d_newton_solve(m3d_ctx *ctx, double *y, const double *u, const m3d_newton_opts *opts,
                                 m3d_newton_report *report);
+
+/*
+ * Batched ensembles.  The paper's parameter studies and optimisations (Sections 1 and 9) run the
+ * same transport for many parameter sets; an ensemble advances many members -- each with its
+ * own model and parameters -- through the same TMM steps at once, so that every matrix entry
+ * is read and interpolated once per step for all of them.  The members share the grid and the
+ * matrices and nothing else: member m's result equals its own year map.
+ *
+ * Parameters of each model (host arrays, this order; rates per day unless stated):
+ *   M3D_MODEL_N    (5):  k_w [1/m], alpha, K_N, K_I [W/m^2], b (Martin exponent)
+ *   M3D_MODEL_NDOP (7):  as metos3d_bgc (lambda per year)
+ *   M3D_MODEL_PHY  (11): mu_1, k_w, K_1, K_I, lambda'_2, sigma_2, lambda_3, kappa_3,
+ *                        lambda'_3, sigma_3, b  (the order of the paper's table, Section 2.2.2)
+ *   M3D_MODEL_NPZD (13): k_w, mu_P, K_N, K_I, mu_Z, K_P, epsilon, lambda_P, kappa_Z, lambda_Z,
+ *                        lambda_D, lambda_DOP, w_D [m/day]
+ * N is PO4-DOP without DOP (every production exported with Martin's law); NPZD-DOP grazes
+ * phytoplankton by zooplankton (mu_Z Z P/(K_P + P), a fraction epsilon assimilated, the rest to
+ * DOP), loses P (lambda_P) and Z (kappa_Z Z^2) to detritus, excretes Z to DOP (lambda_Z),
+ * remineralises detritus to DOP (lambda_D) and DOP to PO4 (lambda_DOP), grows P only in the
+ * two euphotic layers, and sinks detritus at w_D through the layer interfaces (not the floor).
+ *
+ * State: device [W][n], W = the members' tracer counts summed; member m's tracers are rows
+ * offset_m .. offset_m + ntracer_m - 1 (offsets from metos3d_ensemble_layout), each in the
+ * single-context layout.  Internally the tracers are packed into groups of 32 lanes (no
+ * member split between groups) and stored cell-major.
+ * The implicit matrices must be inverses of tridiagonal matrices (see M3D_IMPLICIT_TRIDIAGONAL);
+ * otherwise init returns M3D_ERR_UNSUPPORTED.
+ */
+typedef struct m3d_ensemble m3d_ensemble;   /* opaque; owned by the library */
+typedef struct {
+    int model_id;               /* M3D_MODEL_N, _NDOP, _PHY or _NPZD */
+    int nparam;                 /* the model's parameter count (above) */
+    const double *u;            /* host [nparam], copied */
+} m3d_member;
+
+/*
+ * Create an ensemble of nmember members (1 .. 4096) on the current device, bound to `stream`
+ * (a cudaStream_t).  grid and mats as for metos3d_init; nsub internal model steps per ocean
+ * step; nstep ocean steps per year.  Synchronous.  Chooses a default tiling; see
+ * metos3d_ensemble_autotune.
+ */
+m3d_status metos3d_ensemble_init(m3d_ensemble **ens, const m3d_grid *grid, const m3d_matrices *mats,
+                                 int nmember, const m3d_member *members, int nsub, int nstep,
+                                 void *stream);
+
+/*
+ * Sizes: members, W (total tracers), n, 32-lane groups.  offsets (may be NULL) receives
+ * nmember + 1 row offsets of the members in the [W][n] state.
+ */
+m3d_status metos3d_ensemble_layout(const m3d_ensemble *ens, int *nmember, int *width, int *n,
+                                   int *ngroup, int *offsets);
+
+/* Rebind the ensemble to another stream (a cudaStream_t). */
+m3d_status metos3d_ensemble_set_stream(m3d_ensemble *ens, void *stream);
+
+/* Replace member m's parameters (host [nparam]); takes effect for the next step. Synchronous. */
+m3d_status metos3d_ensemble_set_params(m3d_ensemble *ens, int member, const double *u_host);
+
+/*
+ * nsteps TMM steps (Section 3) of every member from step j0 (wrapping around the year):
+ * Y1 = steps(Y0); device [W][n] arrays, may be the same.  One kernel launch per step.
+ * Asynchronous.
+ */
+m3d_status metos3d_ensemble_steps(m3d_ensemble *ens, int j0, int nsteps, const double *Y0, double *Y1);
+
+/*
+ * The year map of every member (Section 4): nstep steps, one launch per step, the year
+ * captured once as a CUDA graph and replayed.  Y0, Y1: device [W][n] (may be the same).
+ * Asynchronous; the first call builds the graph (do it before any stream capture).
+ */
+m3d_status metos3d_ensemble_year_map(m3d_ensemble *ens, const double *Y0, double *Y1);
+
+/*
+ * Tiling of the step kernel: each CTA takes cols_per_block consecutive water columns (it
+ * interpolates their matrix rows once per step) and warps_per_block warps that take one
+ * (column, 32-lane group) at a time.  M3D_ERR_ARG when it does not fit in shared memory.
+ */
+m3d_status metos3d_ensemble_set_tiling(m3d_ensemble *ens, int cols_per_block, int warps_per_block);
+m3d_status metos3d_ensemble_get_tiling(const m3d_ensemble *ens, int *cols_per_block, int *warps_per_block);
+
+/*
+ * Autotuner: time nsteps steps from the state Y (device [W][n], not modified) for each
+ * candidate tiling (columns per block 1..32, warps per block 4..32, as shared memory allows),
+ * keep the fastest and return it with its time per step.  Synchronous.
+ */
+m3d_status metos3d_ensemble_autotune(m3d_ensemble *ens, const double *Y, int nsteps,
+                                     int *cols_per_block, int *warps_per_block, double *ms_per_step);
+
+/* Kernel launches of the last steps or year-map call. */
+long long metos3d_ensemble_last_launch_count(const m3d_ensemble *ens);
+
+/* Message for the last failure on ens, or on metos3d_ensemble_init when ens is NULL. */
+const char *metos3d_ensemble_last_error(const m3d_ensemble *ens);
+
+/* Release an ensemble and its device memory.  NULL is accepted. */
+void metos3d_ensemble_free(m3d_ensemble *ens);
 
 /* Sizes of a context: n, ncol, ntracer, nstep (any pointer may be NULL). */
 m3d_status metos3d_info(const m3d_ctx *ctx, int *n, int *ncol, int *ntracer, int *nstep);

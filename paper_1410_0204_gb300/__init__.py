@@ -10,4 +10,4 @@ from .binding import (Context, Metos3dError, bgc, declared_symbols, load, librar
                       OPT_WAIT_TIMEOUT_NS, OPT_TEST_WITHHOLD_TILE, OPT_NTILES, PLAN_PERSISTENT, PLAN_GRAPH,
                       PLAN_RESIDENT, OPT_IMPLICIT_FORM, IMPLICIT_DENSE, IMPLICIT_TRIDIAGONAL,
                       JV_FD, JV_TANGENT, NewtonOptions, NewtonReport,
-                      year_map_autograd)
+                      year_map_autograd, Ensemble, MODEL_N, MODEL_PHY, MODEL_NPZD, MODEL_NTRACER)

@@ -35,7 +35,11 @@ PLAN_GRAPH = 1
 PLAN_RESIDENT = 2
 
 MODEL_NONE = 0
+MODEL_N = 1
 MODEL_NDOP = 2
+MODEL_PHY = 3
+MODEL_NPZD = 5
+MODEL_NTRACER = {MODEL_N: 1, MODEL_NDOP: 2, MODEL_PHY: 3, MODEL_NPZD: 5}
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "metos3d.h")
 
@@ -83,6 +87,10 @@ class NewtonReport(C.Structure):
 
 JV_FD = 0
 JV_TANGENT = 1
+
+
+class _Member(C.Structure):
+    _fields_ = [("model_id", C.c_int), ("nparam", C.c_int), ("u", C.POINTER(C.c_double))]
 
 
 class _Model(C.Structure):
@@ -142,11 +150,28 @@ def load(build_if_missing: bool = False):
     L.metos3d_residual_static.argtypes = [vp, vp, C.c_longlong, vp, vp]
     L.metos3d_residual_static_error.argtypes = []
     L.metos3d_residual_static_error.restype = C.c_char_p
+    L.metos3d_ensemble_init.argtypes = [C.POINTER(vp), C.POINTER(_Grid), C.POINTER(_Matrices), C.c_int,
+                                        C.POINTER(_Member), C.c_int, C.c_int, vp]
+    L.metos3d_ensemble_layout.argtypes = [vp, ip, ip, ip, ip, ip]
+    L.metos3d_ensemble_set_stream.argtypes = [vp, vp]
+    L.metos3d_ensemble_set_params.argtypes = [vp, C.c_int, dp]
+    L.metos3d_ensemble_steps.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    L.metos3d_ensemble_year_map.argtypes = [vp, vp, vp]
+    L.metos3d_ensemble_set_tiling.argtypes = [vp, C.c_int, C.c_int]
+    L.metos3d_ensemble_get_tiling.argtypes = [vp, ip, ip]
+    L.metos3d_ensemble_autotune.argtypes = [vp, vp, C.c_int, ip, ip, dp]
+    L.metos3d_ensemble_last_launch_count.argtypes = [vp]
+    L.metos3d_ensemble_last_launch_count.restype = C.c_longlong
+    L.metos3d_ensemble_last_error.argtypes = [vp]
+    L.metos3d_ensemble_last_error.restype = C.c_char_p
+    L.metos3d_ensemble_free.argtypes = [vp]
+    L.metos3d_ensemble_free.restype = None
     for name in declared_symbols():
         fn = getattr(L, name)
         if name not in ("metos3d_last_error", "metos3d_free", "metos3d_last_launch_count",
                         "metos3d_residual_static_error", "metos3d_get_option",
-                        "metos3d_newton_default_options"):
+                        "metos3d_newton_default_options", "metos3d_ensemble_last_launch_count",
+                        "metos3d_ensemble_last_error", "metos3d_ensemble_free"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -412,3 +437,128 @@ def year_map_autograd(y0, u, ctx, ckpt_every=240):
     if _YearMap is None:
         _YearMap = _year_map_function()
     return _YearMap.apply(y0, u, ctx, ckpt_every)
+
+
+def _echeck(status, ens=None):
+    if status != M3D_OK:
+        msg = load().metos3d_ensemble_last_error(ens).decode(errors="replace")
+        raise Metos3dError(status, msg)
+    return status
+
+
+class Ensemble:
+    """Members -- (model id, parameters) -- advanced together on one grid (metos3d_ensemble_*).
+
+    ``members``: a sequence of (model_id, u) pairs or of objects with ``model`` and ``u``.
+    States are CUDA float64 tensors of shape (W, n): member m's tracers are rows
+    ``offsets[m]:offsets[m + 1]``.
+    """
+
+    def __init__(self, *, col_start, h, zc, vol, lat, exp_rowptr, exp_colidx, exp_val, imp_blk, members,
+                 nsub=1, nstep=2880, stream=None):
+        torch = _torch()
+        L = load()
+        self._L = L
+        cs = np.ascontiguousarray(col_start, dtype=np.int32)
+        n, ncol = int(cs[-1]), int(cs.shape[0] - 1)
+        h, zc, vol, lat = (np.ascontiguousarray(a, dtype=np.float64) for a in (h, zc, vol, lat))
+        rp = np.ascontiguousarray(exp_rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(exp_colidx, dtype=np.int32)
+        ev = np.ascontiguousarray(exp_val, dtype=np.float64)
+        ib = np.ascontiguousarray(imp_blk, dtype=np.float64)
+        g = _Grid(n, ncol, _ip(cs), _dp(h), _dp(zc), _dp(vol), _dp(lat))
+        m = _Matrices(ev.shape[0], ci.shape[0], _ip(rp), _ip(ci), _dp(ev), ib.shape[1], _dp(ib))
+        specs = [(int(getattr(x, "model", x[0] if isinstance(x, tuple) else 0)),
+                  np.ascontiguousarray(getattr(x, "u", x[1] if isinstance(x, tuple) else None), dtype=np.float64))
+                 for x in members]
+        mem = (_Member * len(specs))()
+        for i, (model, u) in enumerate(specs):
+            mem[i] = _Member(model, u.shape[0], _dp(u))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        e = C.c_void_p()
+        _echeck(L.metos3d_ensemble_init(C.byref(e), C.byref(g), C.byref(m), len(specs), mem, int(nsub), int(nstep),
+                                        C.c_void_p(stream.cuda_stream)))
+        self._e = e
+        self.models = [mdl for mdl, _ in specs]
+        self.nparams = [u.shape[0] for _, u in specs]
+        nm, W, nn, G = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        offs = (C.c_int * (len(specs) + 1))()
+        _echeck(L.metos3d_ensemble_layout(e, C.byref(nm), C.byref(W), C.byref(nn), C.byref(G), offs), e)
+        self.nmember, self.width, self.n, self.ngroup = nm.value, W.value, nn.value, G.value
+        self.offsets = [int(v) for v in offs]
+        self.nstep = int(nstep)
+
+    @classmethod
+    def from_problem(cls, prob, members, **kw):
+        return cls(col_start=prob.col_start, h=prob.h, zc=prob.zc, vol=prob.vol, lat=prob.lat,
+                   exp_rowptr=prob.exp_rowptr, exp_colidx=prob.exp_colidx, exp_val=prob.exp_val,
+                   imp_blk=prob.imp_blk, nstep=prob.nstep, members=members, **kw)
+
+    @property
+    def numel(self):
+        return self.width * self.n
+
+    def _sync_stream(self):
+        torch = _torch()
+        s = torch.cuda.current_stream()
+        if s.cuda_stream != self._stream.cuda_stream:
+            self._stream = s
+            _echeck(self._L.metos3d_ensemble_set_stream(self._e, C.c_void_p(s.cuda_stream)), self._e)
+
+    def new_state(self):
+        torch = _torch()
+        return torch.zeros((self.width, self.n), dtype=torch.float64, device="cuda")
+
+    def member(self, Y, m):
+        """Rows of member m in an ensemble state."""
+        return Y[self.offsets[m]:self.offsets[m + 1]]
+
+    def steps(self, j0, nsteps, Y0, Y1):
+        self._sync_stream()
+        _echeck(self._L.metos3d_ensemble_steps(self._e, int(j0), int(nsteps), _dev_ptr(Y0, self.numel, "Y0"),
+                                               _dev_ptr(Y1, self.numel, "Y1", True)), self._e)
+        return Y1
+
+    def year_map(self, Y0, Y1):
+        self._sync_stream()
+        _echeck(self._L.metos3d_ensemble_year_map(self._e, _dev_ptr(Y0, self.numel, "Y0"),
+                                                  _dev_ptr(Y1, self.numel, "Y1", True)), self._e)
+        return Y1
+
+    def set_params(self, m, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        if u.shape[0] != self.nparams[m]:
+            raise ValueError("member %d takes %d parameters" % (m, self.nparams[m]))
+        _echeck(self._L.metos3d_ensemble_set_params(self._e, int(m), _dp(u)), self._e)
+
+    def set_tiling(self, cols_per_block, warps_per_block):
+        _echeck(self._L.metos3d_ensemble_set_tiling(self._e, int(cols_per_block), int(warps_per_block)), self._e)
+
+    def get_tiling(self):
+        a, b = C.c_int(), C.c_int()
+        _echeck(self._L.metos3d_ensemble_get_tiling(self._e, C.byref(a), C.byref(b)), self._e)
+        return a.value, b.value
+
+    def autotune(self, Y, nsteps=10):
+        """Time the candidate tilings from state Y, keep the fastest; (cols, warps, ms per step)."""
+        self._sync_stream()
+        a, b, ms = C.c_int(), C.c_int(), C.c_double()
+        _echeck(self._L.metos3d_ensemble_autotune(self._e, _dev_ptr(Y, self.numel, "Y"), int(nsteps), C.byref(a),
+                                                  C.byref(b), C.byref(ms)), self._e)
+        return a.value, b.value, ms.value
+
+    def last_launch_count(self):
+        return int(self._L.metos3d_ensemble_last_launch_count(self._e))
+
+    def close(self):
+        if getattr(self, "_e", None):
+            self._L.metos3d_ensemble_free(self._e)
+            self._e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

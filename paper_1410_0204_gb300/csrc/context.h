@@ -102,3 +102,7 @@ m3d_status m3d_year_tangent_device(m3d_ctx *c, const double *y0, const double *v
 m3d_status m3d_prologue(m3d_ctx *c);
 // Device allocation owned by the context (freed by metos3d_free).
 cudaError_t m3d_alloc(m3d_ctx *c, void **p, size_t bytes);
+// Checks of a grid and its matrices (sizes, CSR order and range, block sizes, finiteness).
+m3d_status m3d_validate_inputs(const m3d_grid *g, const m3d_matrices *mt, std::string &why);
+// Thomas factors of M when the row-major L x L block B is M's inverse and M is tridiagonal.
+bool tridiagonal_factors(const double *B, int L, double *nl, double *rd, double *ne);

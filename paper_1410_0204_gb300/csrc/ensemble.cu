@@ -1,0 +1,951 @@
+// ensemble.cu -- batched ensembles: many members (model + parameters) advanced together through
+// the TMM steps of Metos3D (arXiv:1410.0204, Section 3), one kernel launch per step and one
+// CUDA graph per model year (Section 4).
+//
+// Layout.  The members' tracers are packed into groups of 32 lanes (no member split between
+// groups; first fit, members with more tracers first) and the state is stored cell-major,
+// X[cell][group * 32 + lane], so that a warp reading one cell of one group reads 256
+// contiguous bytes.  Lanes that hold no tracer stay zero.
+//
+// Step kernel.  A CTA takes a block of consecutive water columns.  It interpolates the
+// explicit matrix rows of its cells once per step into shared memory,
+// A(t_j) = A_m0 + w (A_m1 - A_m0), and stages the Thomas factors of both months of its cells;
+// every tracer of every member then reuses them.  Its warps take (column, group) items from a
+// shared counter; for its item a warp, one lane per tracer,
+//   1. reads y_j of the column and forms z = A_exp(t_j) y_j row by row (one FMA per entry);
+//   2. evaluates the members' source terms q(y_j) with the lanes re-dealt to (member, layer)
+//      pairs -- the models' per-cell work is then done once per member, not once per tracer --
+//      and adds dt q (or the nsub-step increment) to z;
+//   3. applies the interpolated implicit operator, z0 + w (z1 - z0) with z_h the Thomas solve of
+//      month h, and writes y_{j+1}.
+// Nothing waits on another CTA, so a step is one ordinary launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "metos3d.h"
+#include "tmm_kernels.cuh"
+#include "context.h"
+
+namespace {
+
+constexpr int kLanes = 32;
+constexpr int kParSlots = 16;             // derived model scalars per member
+constexpr int kMaxWarps = 16;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr double kSigmaPar = 0.4;         // photosynthetically available fraction of I_SWR
+
+// Slots of the derived member scalars (host-computed from the user's parameters).
+//   every model: [0] k_w, [1] b (Martin models)
+//   N:    [2] alpha', [3] K_N, [4] K_I
+//   NDOP: [2] alpha', [3] K_N, [4] K_I, [5] sigma, [6] lambda, [7] 1 - sigma
+//   PHY:  [2] mu_1', [3] K_1, [4] K_I, [5] lambda'_2, [6] sigma_2, [7] lambda_3', [8] kappa_3',
+//         [9] lambda'_3', [10] sigma_3, [11] 1 - sigma_3, [12] 1 - sigma_2
+//   NPZD: [2] mu_P', [3] K_N, [4] K_I, [5] mu_Z', [6] K_P, [7] epsilon, [8] lambda_P', [9] kappa_Z',
+//         [10] lambda_Z', [11] lambda_D', [12] lambda_DOP', [13] w_D', [14] 1 - epsilon
+// (primes: per year, the per-day rates times 360).
+
+struct EnsParams {
+    int n, ncol, nstep, nmonth, nsub, wp, ngroup, nulat, zmax;
+    int cpb, nnz_blk_max, cells_blk_max;
+    double ds;                            // internal model step (1 / nstep) / nsub
+    const int *m0tab;                     // [nstep]
+    const double *wtab;                   // [nstep]
+    const int *rowptr, *colidx;           // explicit pattern (CSR)
+    const double *ea, *ed;                // [nmonth][nnz]: A_m and A_{m+1} - A_m
+    long long e_mstride;
+    const double *tri;                    // [nmonth][3][n] Thomas factors (-l, 1/d, -e/d)
+    long long tri_mstride;
+    const int *col_start, *col_ulat;
+    const double *h;
+    const double *I0tab;                  // [nstep][nulat]
+    const int *grp_seg_off;               // [ngroup + 1] segments of each group
+    const int4 *segs;                     // (model, first member slot, end member slot, 0)
+    const int *mem_lane0, *mem_pidx;      // per member slot: first lane in its group, member index
+    const double *mpar;                   // [nmember][kParSlots]
+    const double *atten;                  // [nmember][ncol][2] sigma_PAR exp(-k_w d) of the euphotic cells
+    const double *mfrac;                  // [nmember][n] Martin deposition profile (Martin models)
+};
+
+__device__ __forceinline__ double michaelis(double x, double K) { return x / (x + K); }
+
+// Shared-memory layout of the step kernel (doubles first, then ints).
+__host__ __device__ inline size_t ens_warp_doubles(int zmax, bool sub1)
+{
+    return (size_t)(sub1 ? 2 : 4) * zmax * kLanes + kLanes;
+}
+__host__ __device__ inline size_t ens_smem_bytes(int nnz_blk_max, int cells_blk_max, int zmax, int nwarps, bool sub1)
+{
+    return sizeof(double) * ((size_t)nnz_blk_max + 6 * (size_t)cells_blk_max + nwarps * ens_warp_doubles(zmax, sub1)) +
+           sizeof(int) * ((size_t)nnz_blk_max + 4);
+}
+
+template <bool SUB1>
+__global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, int j, const double *__restrict__ X,
+                                                                 double *__restrict__ Xn)
+{
+    extern __shared__ double smem[];
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * E.cpb, c1 = min(c0 + E.cpb, E.ncol);
+    const int cell0 = E.col_start[c0], cell1 = E.col_start[c1];
+    const int p0 = E.rowptr[cell0], p1 = E.rowptr[cell1];
+    const int cbm = E.cells_blk_max, zm = E.zmax;
+
+    double *sval = smem;
+    double *stri = sval + E.nnz_blk_max;
+    double *wb = stri + 6 * cbm + (size_t)warp * ens_warp_doubles(zm, SUB1);
+    double *ys = wb, *zs = ys + zm * kLanes;
+    double *yw = SUB1 ? ys : zs + zm * kLanes;
+    double *qs = SUB1 ? zs : yw + zm * kLanes;
+    double *Es = wb + (SUB1 ? 2 : 4) * zm * kLanes;
+    int *scol = (int *)(stri + 6 * cbm + (size_t)nw * ens_warp_doubles(zm, SUB1));
+    int *counter = scol + E.nnz_blk_max;
+
+    const int m0 = E.m0tab[j], m1 = (m0 + 1) % E.nmonth;
+    const double w = E.wtab[j];
+    {
+        const double *a0 = E.ea + (size_t)m0 * E.e_mstride, *d0 = E.ed + (size_t)m0 * E.e_mstride;
+        for (int p = threadIdx.x; p < p1 - p0; p += blockDim.x) {
+            sval[p] = fma(w, d0[p0 + p], a0[p0 + p]);
+            scol[p] = E.colidx[p0 + p];
+        }
+        const double *t0 = E.tri + (size_t)m0 * E.tri_mstride, *t1 = E.tri + (size_t)m1 * E.tri_mstride;
+        for (int i = threadIdx.x; i < cell1 - cell0; i += blockDim.x)
+            for (int f = 0; f < 3; f++) {
+                stri[f * cbm + i] = t0[(size_t)f * E.n + cell0 + i];
+                stri[(3 + f) * cbm + i] = t1[(size_t)f * E.n + cell0 + i];
+            }
+        if (threadIdx.x == 0) *counter = 0;
+    }
+    __syncthreads();
+
+    const int nitems = (c1 - c0) * E.ngroup;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= nitems) break;
+        const int c = c0 + item / E.ngroup, g = item - (item / E.ngroup) * E.ngroup;
+        const int s0 = E.col_start[c], L = E.col_start[c + 1] - s0, sl = s0 - cell0;
+        const size_t gl = (size_t)g * kLanes + lane;
+
+        // 1. y_j of the column and z = A_exp(t_j) y_j
+        for (int k = 0; k < L; k++) ys[k * kLanes + lane] = X[(size_t)(s0 + k) * E.wp + gl];
+        for (int k = 0; k < L; k++) {
+            const int pb = E.rowptr[s0 + k] - p0, pe = E.rowptr[s0 + k + 1] - p0;
+            double za = 0.0, zb = 0.0;
+            int p = pb;
+            for (; p + 1 < pe; p += 2) {
+                const double xa = X[(size_t)scol[p] * E.wp + gl], xb = X[(size_t)scol[p + 1] * E.wp + gl];
+                za = fma(sval[p], xa, za);
+                zb = fma(sval[p + 1], xb, zb);
+            }
+            if (p < pe) za = fma(sval[p], X[(size_t)scol[p] * E.wp + gl], za);
+            zs[k * kLanes + lane] = za + zb;
+        }
+        if (!SUB1) {
+            for (int k = 0; k < L; k++) {
+                yw[k * kLanes + lane] = ys[k * kLanes + lane];
+                qs[k * kLanes + lane] = 0.0;
+            }
+        }
+        __syncwarp();
+
+        // 2. source terms, lanes over (member, layer) pairs
+        const double I0 = E.I0tab[(size_t)j * E.nulat + E.col_ulat[c]];
+        const int neu = L < 2 ? L : 2, na = L - neu;
+        const int sg0 = E.grp_seg_off[g], sg1 = E.grp_seg_off[g + 1];
+        for (int sub = 0; sub < (SUB1 ? 1 : E.nsub); sub++) {
+            const double *st = SUB1 ? ys : yw;
+            // emit q of tracer t of the member whose first lane is l0, layer k
+            auto emit = [&](int k, int l0, int t, double q) {
+                if (SUB1) zs[k * kLanes + l0 + t] = fma(E.ds, q, zs[k * kLanes + l0 + t]);
+                else qs[k * kLanes + l0 + t] = q;
+            };
+            for (int sg = sg0; sg < sg1; sg++) {
+                const int4 S = E.segs[sg];
+                const int model = S.x, nm = S.z - S.y;
+                if (model == M3D_MODEL_NPZD) {
+                    for (int base = 0; base < nm * L; base += kLanes) {
+                        const int p = base + lane;
+                        if (p >= nm * L) continue;
+                        const int ml = p / L, k = p - ml * L, mi = S.y + ml;
+                        const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
+                        const double *mp = E.mpar + (size_t)pid * kParSlots;
+                        const double N = st[k * kLanes + l0], P = st[k * kLanes + l0 + 1];
+                        const double Z = st[k * kLanes + l0 + 2], D = st[k * kLanes + l0 + 3];
+                        const double DOP = st[k * kLanes + l0 + 4];
+                        double U = 0.0;
+                        if (k < neu) {
+                            const double I = I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k];
+                            U = mp[2] * P * michaelis(N, mp[3]) * michaelis(I, mp[4]);
+                        }
+                        const double G = mp[5] * Z * michaelis(P, mp[6]);
+                        const double mP = mp[8] * P, mZ = mp[9] * Z * Z, eZ = mp[10] * Z;
+                        const double rD = mp[11] * D, rO = mp[12] * DOP;
+                        const double Sin = k > 0 ? mp[13] * st[(k - 1) * kLanes + l0 + 3] : 0.0;
+                        const double Sout = k + 1 < L ? mp[13] * D : 0.0;
+                        const double hk = E.h[s0 + k];
+                        emit(k, l0, 0, -U + rO);
+                        emit(k, l0, 1, U - G - mP);
+                        emit(k, l0, 2, mp[7] * G - mZ - eZ);
+                        emit(k, l0, 3, mP + mZ - rD + (Sin - Sout) / hk);
+                        emit(k, l0, 4, mp[14] * G + eZ + rD - rO);
+                    }
+                    continue;
+                }
+                // Martin models (N, NDOP, PHY): euphotic pairs, export E reduced over the member's
+                // euphotic layers (adjacent lanes), then the aphotic pairs
+                for (int base = 0; base < nm * neu; base += kLanes) {
+                    const int p = base + lane;
+                    const bool act = p < nm * neu;
+                    const int ml = act ? p / neu : 0, k = act ? p - ml * neu : 0, mi = S.y + ml;
+                    double e = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0;
+                    int l0 = 0, pid = 0;
+                    if (act) {
+                        l0 = E.mem_lane0[mi];
+                        pid = E.mem_pidx[mi];
+                        const double *mp = E.mpar + (size_t)pid * kParSlots;
+                        const double I = I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k];
+                        const double hk = E.h[s0 + k];
+                        const double N = st[k * kLanes + l0];
+                        if (model == M3D_MODEL_N) {
+                            const double f = mp[2] * michaelis(N, mp[3]) * michaelis(I, mp[4]);
+                            q0 = -f;
+                            e = f * hk;
+                        } else if (model == M3D_MODEL_NDOP) {
+                            const double DOP = st[k * kLanes + l0 + 1];
+                            const double f = mp[2] * michaelis(N, mp[3]) * michaelis(I, mp[4]);
+                            q0 = -f + mp[6] * DOP;
+                            q1 = mp[5] * f - mp[6] * DOP;
+                            e = mp[7] * f * hk;
+                        } else {                                   // PHY
+                            const double DOP = st[k * kLanes + l0 + 1], PHY = st[k * kLanes + l0 + 2];
+                            const double f1 = mp[2] * PHY * michaelis(N, mp[3]) * michaelis(I, mp[4]);
+                            const double f3 = mp[10] * f1;
+                            const double loss = mp[7] * PHY + mp[8] * PHY * PHY;
+                            q0 = -f1 + mp[5] * DOP;
+                            q1 = mp[6] * f3 + loss - mp[5] * DOP + mp[9] * PHY;
+                            q2 = mp[11] * f1 - loss - mp[9] * PHY;
+                            e = mp[12] * f3 * hk;
+                        }
+                    }
+                    double Eg = e;
+                    if (neu == 2) Eg += __shfl_xor_sync(kFull, e, 1);
+                    if (act) {
+                        if (L <= 2 && k == L - 1) q0 = fma(Eg, E.mfrac[(size_t)pid * E.n + s0 + k], q0);
+                        if (k == 0) Es[ml] = Eg;
+                        emit(k, l0, 0, q0);
+                        if (model != M3D_MODEL_N) emit(k, l0, 1, q1);
+                        if (model == M3D_MODEL_PHY) emit(k, l0, 2, q2);
+                    }
+                }
+                __syncwarp();
+                for (int base = 0; base < nm * na; base += kLanes) {
+                    const int p = base + lane;
+                    if (p >= nm * na) continue;
+                    const int ml = p / na, k = neu + (p - ml * na), mi = S.y + ml;
+                    const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
+                    const double *mp = E.mpar + (size_t)pid * kParSlots;
+                    const double dep = Es[ml] * E.mfrac[(size_t)pid * E.n + s0 + k];
+                    if (model == M3D_MODEL_N) {
+                        emit(k, l0, 0, dep);
+                    } else if (model == M3D_MODEL_NDOP) {
+                        const double DOP = st[k * kLanes + l0 + 1];
+                        emit(k, l0, 0, dep + mp[6] * DOP);
+                        emit(k, l0, 1, -mp[6] * DOP);
+                    } else {
+                        const double DOP = st[k * kLanes + l0 + 1], PHY = st[k * kLanes + l0 + 2];
+                        emit(k, l0, 0, dep + mp[5] * DOP);
+                        emit(k, l0, 1, -mp[5] * DOP + mp[9] * PHY);
+                        emit(k, l0, 2, -mp[9] * PHY);
+                    }
+                }
+                __syncwarp();
+            }
+            if (!SUB1) {
+                __syncwarp();
+                for (int k = 0; k < L; k++) yw[k * kLanes + lane] = fma(E.ds, qs[k * kLanes + lane], yw[k * kLanes + lane]);
+                __syncwarp();
+            }
+        }
+        if (!SUB1) {
+            for (int k = 0; k < L; k++) zs[k * kLanes + lane] += yw[k * kLanes + lane] - ys[k * kLanes + lane];
+        }
+        __syncwarp();
+
+        // 3. implicit part: Thomas solves of both months, then z0 + w (z1 - z0)
+        {
+            const double *nl0 = stri + sl, *rd0 = stri + cbm + sl, *ne0 = stri + 2 * cbm + sl;
+            const double *nl1 = stri + 3 * cbm + sl, *rd1 = stri + 4 * cbm + sl, *ne1 = stri + 5 * cbm + sl;
+            double g0 = 0.0, g1 = 0.0;
+            for (int k = 0; k < L; k++) {
+                const double z = zs[k * kLanes + lane];
+                g0 = fma(nl0[k], g0, z);
+                g1 = fma(nl1[k], g1, z);
+                ys[k * kLanes + lane] = g0;
+                zs[k * kLanes + lane] = g1;
+            }
+            double v0 = 0.0, v1 = 0.0;
+            for (int k = L - 1; k >= 0; k--) {
+                v0 = fma(ne0[k], v0, ys[k * kLanes + lane] * rd0[k]);
+                v1 = fma(ne1[k], v1, zs[k * kLanes + lane] * rd1[k]);
+                Xn[(size_t)(s0 + k) * E.wp + gl] = fma(w, v1 - v0, v0);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Per-member tables from the derived scalars: light attenuation of the euphotic cells and the
+// Martin deposition profile (F(z_top) - F(z_bot)) / (E h) of the aphotic cells, with the
+// sea-floor rule (nothing leaves the bottom interface; a column without aphotic layers keeps
+// its export in its bottom layer, 1/h there).
+__global__ void k_ens_tables(int nmember, int ncol, int n, const int *col_start, const double *h,
+                             const double *zc, const int *mem_model, const double *mpar, double *atten,
+                             double *mfrac)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nmember * ncol) return;
+    const int m = (int)(idx / ncol), c = (int)(idx % ncol);
+    const int model = mem_model[m];
+    const double kw = mpar[(size_t)m * kParSlots + 0], b = mpar[(size_t)m * kParSlots + 1];
+    const int s0 = col_start[c], L = col_start[c + 1] - s0, neu = L < 2 ? L : 2;
+    for (int k = 0; k < 2; k++)
+        atten[((size_t)m * ncol + c) * 2 + k] = k < neu ? kSigmaPar * exp(-kw * zc[s0 + k]) : 0.0;
+    if (model == M3D_MODEL_NPZD) return;
+    double zeu = 0.0;
+    for (int k = 0; k < neu; k++) zeu += h[s0 + k];
+    for (int k = 0; k < neu; k++) mfrac[(size_t)m * n + s0 + k] = (L <= 2 && k == L - 1) ? 1.0 / h[s0 + k] : 0.0;
+    double ztop = zeu;
+    for (int k = neu; k < L; k++) {
+        const double zbot = ztop + h[s0 + k];
+        const double top = pow(ztop / zeu, -b);
+        const double bot = k + 1 < L ? pow(zbot / zeu, -b) : 0.0;
+        mfrac[(size_t)m * n + s0 + k] = (top - bot) / h[s0 + k];
+        ztop = zbot;
+    }
+}
+
+// [W][n] (members' rows) <-> X[n][wp] (cell-major, packed lanes; empty lanes zero).
+__global__ void k_ens_pack(int n, int wp, const int *lane_tracer, const double *Y, double *X)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * wp) return;
+    const int i = (int)(idx / wp), l = (int)(idx % wp), t = lane_tracer[l];
+    X[idx] = t >= 0 ? Y[(size_t)t * n + i] : 0.0;
+}
+__global__ void k_ens_unpack(int n, int width, const int *tracer_lane, const double *X, int wp, double *Y)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * width) return;
+    const int t = (int)(idx / n), i = (int)(idx % n);
+    Y[idx] = X[(size_t)i * wp + tracer_lane[t]];
+}
+
+__global__ void k_ens_insolation(int nstep, int nulat, const double *ulat, double *I0)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nstep * nulat) return;
+    const int jj = (int)(i / nulat), l = (int)(i % nulat);
+    I0[i] = m3d::insolation(ulat[l], (double)jj / nstep);
+}
+
+thread_local std::string g_ens_init_error;
+
+int model_ntracer(int model)
+{
+    switch (model) {
+    case M3D_MODEL_N: return 1;
+    case M3D_MODEL_NDOP: return 2;
+    case M3D_MODEL_PHY: return 3;
+    case M3D_MODEL_NPZD: return 5;
+    default: return 0;
+    }
+}
+int model_nparam(int model)
+{
+    switch (model) {
+    case M3D_MODEL_N: return 5;
+    case M3D_MODEL_NDOP: return 7;
+    case M3D_MODEL_PHY: return 11;
+    case M3D_MODEL_NPZD: return 13;
+    default: return -1;
+    }
+}
+
+// Derived scalars of one member (slot layout above).
+void derive_params(int model, const double *u, double *mp)
+{
+    for (int i = 0; i < kParSlots; i++) mp[i] = 0.0;
+    switch (model) {
+    case M3D_MODEL_N:
+        mp[0] = u[0]; mp[1] = u[4]; mp[2] = u[1] * 360.0; mp[3] = u[2]; mp[4] = u[3];
+        break;
+    case M3D_MODEL_NDOP:
+        mp[0] = u[0]; mp[1] = u[6]; mp[2] = u[1] * 360.0; mp[3] = u[4]; mp[4] = u[5];
+        mp[5] = u[2]; mp[6] = u[3]; mp[7] = 1.0 - u[2];
+        break;
+    case M3D_MODEL_PHY:
+        mp[0] = u[1]; mp[1] = u[10]; mp[2] = 360.0 * u[0]; mp[3] = u[2]; mp[4] = u[3];
+        mp[5] = 360.0 * u[4]; mp[6] = u[5]; mp[7] = 360.0 * u[6]; mp[8] = 360.0 * u[7]; mp[9] = 360.0 * u[8];
+        mp[10] = u[9]; mp[11] = 1.0 - u[9]; mp[12] = 1.0 - u[5];
+        break;
+    case M3D_MODEL_NPZD:
+        mp[0] = u[0]; mp[1] = 0.0; mp[2] = 360.0 * u[1]; mp[3] = u[2]; mp[4] = u[3];
+        mp[5] = 360.0 * u[4]; mp[6] = u[5]; mp[7] = u[6]; mp[8] = 360.0 * u[7]; mp[9] = 360.0 * u[8];
+        mp[10] = 360.0 * u[9]; mp[11] = 360.0 * u[10]; mp[12] = 360.0 * u[11]; mp[13] = 360.0 * u[12];
+        mp[14] = 1.0 - u[6];
+        break;
+    }
+}
+
+}  // namespace
+
+struct m3d_ensemble {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int n = 0, ncol = 0, nstep = 0, nmonth = 0, nsub = 1, nmember = 0, width = 0, ngroup = 0, wp = 0, zmax = 0;
+    int cpb = 0, nwarps = 0, nblocks = 0;
+    size_t smem = 0, smem_optin = 0;
+    std::vector<int> col_start;
+    std::vector<int> rowptr;
+    std::vector<int> models, offsets;          // per member (offsets: nmember + 1)
+    std::vector<double> u_host;                // [nmember][16] user parameters (copied)
+    std::vector<double> mpar_host;             // [nmember][kParSlots]
+    std::vector<void *> allocs;
+    EnsParams P{};
+    int *mem_model_dev = nullptr;
+    double *mpar_dev = nullptr, *atten_dev = nullptr, *mfrac_dev = nullptr;
+    int *lane_tracer = nullptr, *tracer_lane = nullptr;
+    double *xbuf[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph = nullptr;
+    long long last_launches = 0;
+    std::string err;
+};
+
+namespace {
+
+m3d_status efail(m3d_ensemble *e, m3d_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (e) e->err = buf;
+    else g_ens_init_error = buf;
+    return s;
+}
+
+#define ENS_CUDA(e, call)                                                                     \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return efail((e), M3D_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+template <typename T>
+cudaError_t ens_upload(m3d_ensemble *e, T **dst, const T *src, size_t count)
+{
+    *dst = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t r = cudaMalloc((void **)dst, sizeof(T) * count);
+    if (r != cudaSuccess) return r;
+    e->allocs.push_back(*dst);
+    if (src) return cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice);
+    return cudaSuccess;
+}
+
+void ens_release(m3d_ensemble *e)
+{
+    if (!e) return;
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    e->graph = nullptr;
+    for (void *p : e->allocs) cudaFree(p);
+    e->allocs.clear();
+}
+
+// Block sizes for cpb columns per block: largest entry and cell counts of a block.
+void block_extents(const m3d_ensemble *e, int cpb, int *nnz_max, int *cells_max, int *nblocks)
+{
+    int nb = (e->ncol + cpb - 1) / cpb, a = 0, b = 0;
+    for (int blk = 0; blk < nb; blk++) {
+        int c0 = blk * cpb, c1 = std::min(c0 + cpb, e->ncol);
+        int s = e->col_start[c0], t = e->col_start[c1];
+        a = std::max(a, e->rowptr[t] - e->rowptr[s]);
+        b = std::max(b, t - s);
+    }
+    *nnz_max = a;
+    *cells_max = b;
+    *nblocks = nb;
+}
+
+m3d_status apply_tiling(m3d_ensemble *e, int cpb, int nwarps)
+{
+    if (cpb < 1 || cpb > e->ncol || nwarps < 1 || nwarps > kMaxWarps)
+        return efail(e, M3D_ERR_ARG, "tiling: columns per block must be 1..%d and warps 1..%d", e->ncol, kMaxWarps);
+    int nnz_max, cells_max, nb;
+    block_extents(e, cpb, &nnz_max, &cells_max, &nb);
+    const bool sub1 = e->nsub == 1;
+    size_t smem = ens_smem_bytes(nnz_max, cells_max, e->zmax, nwarps, sub1);
+    if (smem > e->smem_optin)
+        return efail(e, M3D_ERR_ARG, "tiling: %d columns x %d warps needs %zu bytes of shared memory (%zu available)",
+                     cpb, nwarps, smem, e->smem_optin);
+    const void *fn = sub1 ? (const void *)k_ens_step<true> : (const void *)k_ens_step<false>;
+    ENS_CUDA(e, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    e->cpb = cpb;
+    e->nwarps = nwarps;
+    e->nblocks = nb;
+    e->smem = smem;
+    e->P.cpb = cpb;
+    e->P.nnz_blk_max = nnz_max;
+    e->P.cells_blk_max = cells_max;
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    return M3D_OK;
+}
+
+m3d_status launch_step(m3d_ensemble *e, int j, const double *X, double *Xn)
+{
+    if (e->nsub == 1)
+        k_ens_step<true><<<e->nblocks, e->nwarps * kLanes, e->smem, e->stream>>>(e->P, j, X, Xn);
+    else
+        k_ens_step<false><<<e->nblocks, e->nwarps * kLanes, e->smem, e->stream>>>(e->P, j, X, Xn);
+    ENS_CUDA(e, cudaGetLastError());
+    return M3D_OK;
+}
+
+m3d_status launch_tables(m3d_ensemble *e)
+{
+    long long tot = (long long)e->nmember * e->ncol;
+    k_ens_tables<<<(unsigned)((tot + 255) / 256), 256, 0, e->stream>>>(
+        e->nmember, e->ncol, e->n, e->P.col_start, e->P.h, e->P.h + e->n, e->mem_model_dev, e->mpar_dev, e->atten_dev,
+        e->mfrac_dev);
+    ENS_CUDA(e, cudaGetLastError());
+    return M3D_OK;
+}
+
+m3d_status pack(m3d_ensemble *e, const double *Y, double *X)
+{
+    long long tot = (long long)e->n * e->wp;
+    k_ens_pack<<<(unsigned)((tot + 255) / 256), 256, 0, e->stream>>>(e->n, e->wp, e->lane_tracer, Y, X);
+    ENS_CUDA(e, cudaGetLastError());
+    return M3D_OK;
+}
+
+m3d_status unpack(m3d_ensemble *e, const double *X, double *Y)
+{
+    long long tot = (long long)e->n * e->width;
+    k_ens_unpack<<<(unsigned)((tot + 255) / 256), 256, 0, e->stream>>>(e->n, e->width, e->tracer_lane, X, e->wp, Y);
+    ENS_CUDA(e, cudaGetLastError());
+    return M3D_OK;
+}
+
+m3d_status build_graph(m3d_ensemble *e)
+{
+    cudaStream_t s = e->stream;
+    bool own = false;
+    if (!s) {
+        ENS_CUDA(e, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        own = true;
+    }
+    cudaStream_t saved = e->stream;
+    e->stream = s;
+    cudaGraph_t graph = nullptr;
+    cudaError_t r = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    m3d_status st = M3D_OK;
+    if (r == cudaSuccess) {
+        for (int j = 0; j < e->nstep && st == M3D_OK; j++) st = launch_step(e, j, e->xbuf[j & 1], e->xbuf[(j + 1) & 1]);
+        r = cudaStreamEndCapture(s, &graph);
+    }
+    e->stream = saved;
+    if (own) cudaStreamDestroy(s);
+    if (st != M3D_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (r != cudaSuccess) return efail(e, M3D_ERR_CUDA, "ensemble year graph capture: %s", cudaGetErrorString(r));
+    r = cudaGraphInstantiate(&e->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (r != cudaSuccess) return efail(e, M3D_ERR_CUDA, "ensemble year graph instantiate: %s", cudaGetErrorString(r));
+    return M3D_OK;
+}
+
+m3d_status upload_params(m3d_ensemble *e)
+{
+    ENS_CUDA(e, cudaMemcpyAsync(e->mpar_dev, e->mpar_host.data(), sizeof(double) * e->mpar_host.size(),
+                                cudaMemcpyHostToDevice, e->stream));
+    m3d_status st = launch_tables(e);
+    if (st != M3D_OK) return st;
+    ENS_CUDA(e, cudaStreamSynchronize(e->stream));
+    return M3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+m3d_status metos3d_ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3d_matrices *mt, int nmember,
+                                 const m3d_member *members, int nsub, int nstep, void *stream)
+{
+    if (!out) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_init: out is null");
+    *out = nullptr;
+    std::string why;
+    if (m3d_validate_inputs(g, mt, why) != M3D_OK) return efail(nullptr, M3D_ERR_ARG, "%s", why.c_str());
+    if (nmember < 1 || nmember > 4096 || !members)
+        return efail(nullptr, M3D_ERR_ARG, "ensemble: 1..4096 members needed");
+    if (nsub < 1 || nstep < 1) return efail(nullptr, M3D_ERR_ARG, "ensemble: nsub and nstep must be positive");
+    for (int m = 0; m < nmember; m++) {
+        const int model = members[m].model_id;
+        if (model_ntracer(model) == 0)
+            return efail(nullptr, M3D_ERR_UNSUPPORTED, "ensemble: member %d has unknown model %d", m, model);
+        if (members[m].nparam != model_nparam(model) || !members[m].u)
+            return efail(nullptr, M3D_ERR_ARG, "ensemble: member %d needs %d parameters", m, model_nparam(model));
+        for (int i = 0; i < members[m].nparam; i++)
+            if (!std::isfinite(members[m].u[i]))
+                return efail(nullptr, M3D_ERR_ARG, "ensemble: member %d has a non-finite parameter", m);
+    }
+    m3d_ensemble *e = new (std::nothrow) m3d_ensemble();
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "out of host memory");
+    auto bail = [&](m3d_status s) {
+        g_ens_init_error = e->err;
+        ens_release(e);
+        delete e;
+        return s;
+    };
+#define ENS_UP(call)                                                                              \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            efail(e, M3D_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));               \
+            return bail(M3D_ERR_CUDA);                                                            \
+        }                                                                                         \
+    } while (0)
+    cudaGetDevice(&e->device);
+    e->stream = (cudaStream_t)stream;
+    e->n = g->n;
+    e->ncol = g->ncol;
+    e->nstep = nstep;
+    e->nmonth = mt->nmonth;
+    e->nsub = nsub;
+    e->nmember = nmember;
+    e->col_start.assign(g->col_start, g->col_start + g->ncol + 1);
+    e->rowptr.assign(mt->exp_rowptr, mt->exp_rowptr + g->n + 1);
+    for (int c = 0; c < g->ncol; c++) e->zmax = std::max(e->zmax, g->col_start[c + 1] - g->col_start[c]);
+
+    // ---- members: tracer offsets, packing into 32-lane groups (more tracers first, first fit)
+    e->models.resize(nmember);
+    e->offsets.assign(nmember + 1, 0);
+    e->mpar_host.assign((size_t)nmember * kParSlots, 0.0);
+    for (int m = 0; m < nmember; m++) {
+        e->models[m] = members[m].model_id;
+        e->offsets[m + 1] = e->offsets[m] + model_ntracer(members[m].model_id);
+        derive_params(members[m].model_id, members[m].u, &e->mpar_host[(size_t)m * kParSlots]);
+    }
+    e->width = e->offsets[nmember];
+    std::vector<int> order(nmember);
+    for (int m = 0; m < nmember; m++) order[m] = m;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return model_ntracer(e->models[a]) > model_ntracer(e->models[b]); });
+    std::vector<int> fill;                       // lanes used per group
+    std::vector<int> grp(nmember), lane0(nmember);
+    for (int m : order) {
+        int nt = model_ntracer(e->models[m]), gsel = -1;
+        for (int gi = 0; gi < (int)fill.size() && gsel < 0; gi++)
+            if (fill[gi] + nt <= kLanes) gsel = gi;
+        if (gsel < 0) {
+            gsel = (int)fill.size();
+            fill.push_back(0);
+        }
+        grp[m] = gsel;
+        lane0[m] = fill[gsel];
+        fill[gsel] += nt;
+    }
+    e->ngroup = (int)fill.size();
+    e->wp = e->ngroup * kLanes;
+    // member slots grouped by group, then by model; one segment per (group, model)
+    std::vector<int> slots(nmember);
+    for (int m = 0; m < nmember; m++) slots[m] = m;
+    std::stable_sort(slots.begin(), slots.end(), [&](int a, int b) {
+        if (grp[a] != grp[b]) return grp[a] < grp[b];
+        return e->models[a] < e->models[b];
+    });
+    std::vector<int> mem_lane0(nmember), mem_pidx(nmember), seg_off(e->ngroup + 1, 0);
+    std::vector<int4> segs;
+    for (int s = 0; s < nmember; s++) {
+        int m = slots[s];
+        mem_lane0[s] = lane0[m];
+        mem_pidx[s] = m;
+        if (s == 0 || grp[slots[s - 1]] != grp[m] || e->models[slots[s - 1]] != e->models[m])
+            segs.push_back(make_int4(e->models[m], s, s, 0));
+        segs.back().z = s + 1;
+        seg_off[grp[m] + 1] = (int)segs.size();
+    }
+    for (int gi = 1; gi <= e->ngroup; gi++) seg_off[gi] = std::max(seg_off[gi], seg_off[gi - 1]);
+    std::vector<int> lane_tracer(e->wp, -1), tracer_lane(e->width);
+    for (int m = 0; m < nmember; m++)
+        for (int t = 0; t < model_ntracer(e->models[m]); t++) {
+            int l = grp[m] * kLanes + lane0[m] + t;
+            lane_tracer[l] = e->offsets[m] + t;
+            tracer_lane[e->offsets[m] + t] = l;
+        }
+
+    // ---- Thomas factors of every monthly implicit block (required)
+    std::vector<double> tri((size_t)mt->nmonth * 3 * g->n);
+    {
+        std::vector<long long> blk_off(g->ncol + 1, 0);
+        for (int c = 0; c < g->ncol; c++) {
+            long long L = g->col_start[c + 1] - g->col_start[c];
+            blk_off[c + 1] = blk_off[c] + L * L;
+        }
+        for (int m = 0; m < mt->nmonth; m++)
+            for (int c = 0; c < g->ncol; c++) {
+                int L = g->col_start[c + 1] - g->col_start[c], s0 = g->col_start[c];
+                double *base = tri.data() + (size_t)m * 3 * g->n;
+                if (!tridiagonal_factors(mt->imp_blk + (size_t)m * mt->s_imp + blk_off[c], L, base + s0,
+                                         base + g->n + s0, base + 2 * (size_t)g->n + s0)) {
+                    efail(e, M3D_ERR_UNSUPPORTED,
+                          "ensemble: the implicit block of column %d, month %d is not the inverse of a tridiagonal matrix",
+                          c, m);
+                    return bail(M3D_ERR_UNSUPPORTED);
+                }
+            }
+    }
+    // ---- explicit values and month differences
+    const size_t nnz = (size_t)mt->nnz;
+    std::vector<double> ed((size_t)mt->nmonth * nnz);
+    for (int m = 0; m < mt->nmonth; m++) {
+        const double *a = mt->exp_val + (size_t)m * nnz, *b = mt->exp_val + (size_t)((m + 1) % mt->nmonth) * nnz;
+        for (size_t p = 0; p < nnz; p++) ed[(size_t)m * nnz + p] = b[p] - a[p];
+    }
+    // ---- step tables, latitudes
+    std::vector<int> m0tab(nstep);
+    std::vector<double> wtab(nstep);
+    for (int j = 0; j < nstep; j++) m3d::month_weights(j, nstep, mt->nmonth, m0tab[j], wtab[j]);
+    std::vector<double> ulat(g->lat, g->lat + g->ncol);
+    std::sort(ulat.begin(), ulat.end());
+    ulat.erase(std::unique(ulat.begin(), ulat.end()), ulat.end());
+    std::vector<int> col_ulat(g->ncol);
+    for (int c = 0; c < g->ncol; c++)
+        col_ulat[c] = (int)(std::lower_bound(ulat.begin(), ulat.end(), g->lat[c]) - ulat.begin());
+
+    cudaDeviceProp prop;
+    ENS_UP(cudaGetDeviceProperties(&prop, e->device));
+    e->smem_optin = prop.sharedMemPerBlockOptin;
+
+    EnsParams &P = e->P;
+    P.n = g->n;
+    P.ncol = g->ncol;
+    P.nstep = nstep;
+    P.nmonth = mt->nmonth;
+    P.nsub = nsub;
+    P.wp = e->wp;
+    P.ngroup = e->ngroup;
+    P.nulat = (int)ulat.size();
+    P.zmax = e->zmax;
+    P.ds = (1.0 / nstep) / nsub;
+    P.e_mstride = (long long)nnz;
+    P.tri_mstride = 3LL * g->n;
+    {
+        int *ip;
+        double *dp;
+        ENS_UP(ens_upload(e, &ip, m0tab.data(), m0tab.size())); P.m0tab = ip;
+        ENS_UP(ens_upload(e, &dp, wtab.data(), wtab.size())); P.wtab = dp;
+        ENS_UP(ens_upload(e, &ip, mt->exp_rowptr, (size_t)g->n + 1)); P.rowptr = ip;
+        ENS_UP(ens_upload(e, &ip, mt->exp_colidx, nnz)); P.colidx = ip;
+        ENS_UP(ens_upload(e, &dp, mt->exp_val, (size_t)mt->nmonth * nnz)); P.ea = dp;
+        ENS_UP(ens_upload(e, &dp, ed.data(), ed.size())); P.ed = dp;
+        ENS_UP(ens_upload(e, &dp, tri.data(), tri.size())); P.tri = dp;
+        ENS_UP(ens_upload(e, &ip, g->col_start, (size_t)g->ncol + 1)); P.col_start = ip;
+        ENS_UP(ens_upload(e, &ip, col_ulat.data(), col_ulat.size())); P.col_ulat = ip;
+        std::vector<double> hz(g->h, g->h + g->n);
+        hz.insert(hz.end(), g->zc, g->zc + g->n);
+        ENS_UP(ens_upload(e, &dp, hz.data(), hz.size())); P.h = dp;     // h, then zc
+        double *ulat_dev, *I0;
+        ENS_UP(ens_upload(e, &ulat_dev, ulat.data(), ulat.size()));
+        ENS_UP(ens_upload(e, &I0, (const double *)nullptr, (size_t)nstep * ulat.size()));
+        long long tot = (long long)nstep * (long long)ulat.size();
+        k_ens_insolation<<<(unsigned)((tot + 255) / 256), 256>>>(nstep, (int)ulat.size(), ulat_dev, I0);
+        ENS_UP(cudaGetLastError());
+        P.I0tab = I0;
+        ENS_UP(ens_upload(e, &ip, seg_off.data(), seg_off.size())); P.grp_seg_off = ip;
+        int4 *sp;
+        ENS_UP(ens_upload(e, &sp, segs.data(), segs.size())); P.segs = sp;
+        ENS_UP(ens_upload(e, &ip, mem_lane0.data(), mem_lane0.size())); P.mem_lane0 = ip;
+        ENS_UP(ens_upload(e, &ip, mem_pidx.data(), mem_pidx.size())); P.mem_pidx = ip;
+        ENS_UP(ens_upload(e, &e->mem_model_dev, e->models.data(), e->models.size()));
+        ENS_UP(ens_upload(e, &e->mpar_dev, e->mpar_host.data(), e->mpar_host.size())); P.mpar = e->mpar_dev;
+        ENS_UP(ens_upload(e, &e->atten_dev, (const double *)nullptr, (size_t)nmember * g->ncol * 2)); P.atten = e->atten_dev;
+        ENS_UP(ens_upload(e, &e->mfrac_dev, (const double *)nullptr, (size_t)nmember * g->n)); P.mfrac = e->mfrac_dev;
+        ENS_UP(cudaMemset(e->mfrac_dev, 0, sizeof(double) * (size_t)nmember * g->n));
+        ENS_UP(ens_upload(e, &e->lane_tracer, lane_tracer.data(), lane_tracer.size()));
+        ENS_UP(ens_upload(e, &e->tracer_lane, tracer_lane.data(), tracer_lane.size()));
+        double *xb;
+        ENS_UP(ens_upload(e, &xb, (const double *)nullptr, 2 * (size_t)g->n * e->wp));
+        ENS_UP(cudaMemset(xb, 0, sizeof(double) * 2 * (size_t)g->n * e->wp));
+        e->xbuf[0] = xb;
+        e->xbuf[1] = xb + (size_t)g->n * e->wp;
+    }
+    ENS_UP(cudaDeviceSynchronize());
+    m3d_status st = upload_params(e);
+    if (st != M3D_OK) return bail(st);
+    // default tiling: 4 columns and 8 warps per block, or the largest that fits
+    st = M3D_ERR_ARG;
+    for (int cpb = 4; cpb >= 1 && st != M3D_OK; cpb /= 2)
+        for (int nw = 8; nw >= 1 && st != M3D_OK; nw /= 2) st = apply_tiling(e, std::min(cpb, e->ncol), nw);
+    if (st != M3D_OK) return bail(st);
+    e->err.clear();
+    *out = e;
+    return M3D_OK;
+#undef ENS_UP
+}
+
+m3d_status metos3d_ensemble_layout(const m3d_ensemble *e, int *nmember, int *width, int *n, int *ngroup, int *offsets)
+{
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_layout: null ensemble");
+    if (nmember) *nmember = e->nmember;
+    if (width) *width = e->width;
+    if (n) *n = e->n;
+    if (ngroup) *ngroup = e->ngroup;
+    if (offsets) std::copy(e->offsets.begin(), e->offsets.end(), offsets);
+    return M3D_OK;
+}
+
+m3d_status metos3d_ensemble_set_stream(m3d_ensemble *e, void *stream)
+{
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_set_stream: null ensemble");
+    e->stream = (cudaStream_t)stream;
+    return M3D_OK;
+}
+
+m3d_status metos3d_ensemble_set_params(m3d_ensemble *e, int member, const double *u)
+{
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_set_params: null ensemble");
+    if (member < 0 || member >= e->nmember || !u) return efail(e, M3D_ERR_ARG, "set_params: bad member or null u");
+    const int np = model_nparam(e->models[member]);
+    for (int i = 0; i < np; i++)
+        if (!std::isfinite(u[i])) return efail(e, M3D_ERR_ARG, "set_params: non-finite parameter");
+    derive_params(e->models[member], u, &e->mpar_host[(size_t)member * kParSlots]);
+    return upload_params(e);
+}
+
+m3d_status metos3d_ensemble_steps(m3d_ensemble *e, int j0, int nsteps, const double *Y0, double *Y1)
+{
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_steps: null ensemble");
+    if (!Y0 || !Y1 || nsteps < 0 || j0 < 0) return efail(e, M3D_ERR_ARG, "steps: null state or negative count");
+    m3d_status st = pack(e, Y0, e->xbuf[0]);
+    for (int s = 0; s < nsteps && st == M3D_OK; s++)
+        st = launch_step(e, (j0 + s) % e->nstep, e->xbuf[s & 1], e->xbuf[(s + 1) & 1]);
+    if (st == M3D_OK) st = unpack(e, e->xbuf[nsteps & 1], Y1);
+    e->last_launches = nsteps + 2;
+    return st;
+}
+
+m3d_status metos3d_ensemble_year_map(m3d_ensemble *e, const double *Y0, double *Y1)
+{
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_year_map: null ensemble");
+    if (!Y0 || !Y1) return efail(e, M3D_ERR_ARG, "year_map: null state");
+    if (!e->graph) {
+        m3d_status st = build_graph(e);
+        if (st != M3D_OK) return st;
+    }
+    m3d_status st = pack(e, Y0, e->xbuf[0]);
+    if (st != M3D_OK) return st;
+    ENS_CUDA(e, cudaGraphLaunch(e->graph, e->stream));
+    st = unpack(e, e->xbuf[e->nstep & 1], Y1);
+    e->last_launches = e->nstep + 2;
+    return st;
+}
+
+m3d_status metos3d_ensemble_set_tiling(m3d_ensemble *e, int cpb, int nwarps)
+{
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_set_tiling: null ensemble");
+    return apply_tiling(e, cpb, nwarps);
+}
+
+m3d_status metos3d_ensemble_get_tiling(const m3d_ensemble *e, int *cpb, int *nwarps)
+{
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_get_tiling: null ensemble");
+    if (cpb) *cpb = e->cpb;
+    if (nwarps) *nwarps = e->nwarps;
+    return M3D_OK;
+}
+
+m3d_status metos3d_ensemble_autotune(m3d_ensemble *e, const double *Y, int nsteps, int *cpb_out, int *nw_out,
+                                     double *ms_out)
+{
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_autotune: null ensemble");
+    if (!Y || nsteps < 1) return efail(e, M3D_ERR_ARG, "autotune: null state or no steps");
+    const int cpbs[] = {1, 2, 4, 8, 16, 32};
+    const int nws[] = {4, 8, 16};
+    int best_c = e->cpb, best_w = e->nwarps;
+    float best = -1.0f;
+    cudaEvent_t a, b;
+    ENS_CUDA(e, cudaEventCreate(&a));
+    ENS_CUDA(e, cudaEventCreate(&b));
+    m3d_status st = M3D_OK;
+    for (int cpb : cpbs) {
+        if (cpb > e->ncol) continue;
+        for (int nw : nws) {
+            if (apply_tiling(e, cpb, nw) != M3D_OK) continue;     // does not fit
+            st = pack(e, Y, e->xbuf[0]);
+            for (int s = 0; s < 2 && st == M3D_OK; s++) st = launch_step(e, s, e->xbuf[s & 1], e->xbuf[(s + 1) & 1]);
+            if (st != M3D_OK) break;
+            cudaEventRecord(a, e->stream);
+            for (int s = 0; s < nsteps && st == M3D_OK; s++)
+                st = launch_step(e, s, e->xbuf[s & 1], e->xbuf[(s + 1) & 1]);
+            cudaEventRecord(b, e->stream);
+            if (st != M3D_OK) break;
+            if (cudaEventSynchronize(b) != cudaSuccess) { st = efail(e, M3D_ERR_CUDA, "autotune: timing failed"); break; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, a, b);
+            ms /= nsteps;
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                best_c = cpb;
+                best_w = nw;
+            }
+        }
+        if (st != M3D_OK) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != M3D_OK) return st;
+    if (best < 0.0f) return efail(e, M3D_ERR_ARG, "autotune: no tiling fits in shared memory");
+    st = apply_tiling(e, best_c, best_w);
+    if (st != M3D_OK) return st;
+    if (cpb_out) *cpb_out = best_c;
+    if (nw_out) *nw_out = best_w;
+    if (ms_out) *ms_out = best;
+    return M3D_OK;
+}
+
+long long metos3d_ensemble_last_launch_count(const m3d_ensemble *e) { return e ? e->last_launches : -1; }
+
+const char *metos3d_ensemble_last_error(const m3d_ensemble *e)
+{
+    return e ? e->err.c_str() : g_ens_init_error.c_str();
+}
+
+void metos3d_ensemble_free(m3d_ensemble *e)
+{
+    if (!e) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(e->device);
+    ens_release(e);
+    cudaSetDevice(cur);
+    delete e;
+}
+
+}  // extern "C"

@@ -391,6 +391,47 @@ bool tridiagonal_factors(const double *B, int L, double *nl, double *rd, double 
     return true;
 }
 
+// Checks of a grid and its matrices shared by metos3d_init and metos3d_ensemble_init.
+m3d_status m3d_validate_inputs(const m3d_grid *g, const m3d_matrices *mt, std::string &why)
+{
+    char buf[256];
+    auto bad = [&](const char *fmt, auto... args) {
+        snprintf(buf, sizeof buf, fmt, args...);
+        why = buf;
+        return M3D_ERR_ARG;
+    };
+    if (!g || !mt) return bad("%s", "null grid or matrices");
+    if (g->n <= 0 || g->ncol <= 0 || !g->col_start || !g->h || !g->zc || !g->vol || !g->lat)
+        return bad("%s", "grid: bad sizes or null arrays");
+    if (g->col_start[0] != 0 || g->col_start[g->ncol] != g->n)
+        return bad("%s", "grid: col_start must run from 0 to n");
+    long long s_imp = 0;
+    for (int c = 0; c < g->ncol; c++) {
+        int L = g->col_start[c + 1] - g->col_start[c];
+        if (L < 1 || L > M3D_MAX_LAYERS) return bad("grid: column %d has %d layers (1..%d allowed)", c, L, M3D_MAX_LAYERS);
+        if (!(g->lat[c] >= -90.0 && g->lat[c] <= 90.0)) return bad("grid: latitude of column %d out of range", c);
+        s_imp += (long long)L * L;
+    }
+    for (int i = 0; i < g->n; i++)
+        if (!(g->h[i] > 0.0) || !std::isfinite(g->h[i]) || !std::isfinite(g->zc[i]) || !std::isfinite(g->vol[i]))
+            return bad("grid: bad h, zc or vol at cell %d", i);
+    if (mt->nmonth < 1 || mt->nnz < g->n || !mt->exp_rowptr || !mt->exp_colidx || !mt->exp_val || !mt->imp_blk)
+        return bad("%s", "matrices: bad sizes or null arrays");
+    if (mt->s_imp != s_imp) return bad("matrices: s_imp is %lld, the columns need %lld", mt->s_imp, s_imp);
+    const int *rp = mt->exp_rowptr, *ci = mt->exp_colidx;
+    if (rp[0] != 0 || rp[g->n] != mt->nnz) return bad("%s", "matrices: rowptr must run from 0 to nnz");
+    for (int i = 0; i < g->n; i++) {
+        if (rp[i + 1] < rp[i]) return bad("matrices: rowptr decreases at row %d", i);
+        for (int p = rp[i]; p < rp[i + 1]; p++) {
+            if (ci[p] < 0 || ci[p] >= g->n) return bad("matrices: column index out of range in row %d", i);
+            if (p > rp[i] && ci[p] <= ci[p - 1]) return bad("matrices: row %d is not sorted or has duplicates", i);
+        }
+    }
+    if (!all_finite(mt->exp_val, (size_t)mt->nmonth * mt->nnz) || !all_finite(mt->imp_blk, (size_t)mt->nmonth * s_imp))
+        return bad("%s", "matrices: non-finite values");
+    return M3D_OK;
+}
+
 // ------------------------------------------------------------------------------ C ABI
 extern "C" {
 
@@ -438,22 +479,10 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     *out = nullptr;
     if (!g || !mt || !md) return fail(nullptr, M3D_ERR_ARG, "metos3d_init: null grid, matrices or model");
     // ---- validation
-    if (g->n <= 0 || g->ncol <= 0 || !g->col_start || !g->h || !g->zc || !g->vol || !g->lat)
-        return fail(nullptr, M3D_ERR_ARG, "grid: bad sizes or null arrays");
-    if (g->col_start[0] != 0 || g->col_start[g->ncol] != g->n)
-        return fail(nullptr, M3D_ERR_ARG, "grid: col_start must run from 0 to n");
-    long long s_imp = 0;
-    for (int c = 0; c < g->ncol; c++) {
-        int L = g->col_start[c + 1] - g->col_start[c];
-        if (L < 1 || L > M3D_MAX_LAYERS)
-            return fail(nullptr, M3D_ERR_ARG, "grid: column %d has %d layers (1..%d allowed)", c, L, M3D_MAX_LAYERS);
-        if (!(g->lat[c] >= -90.0 && g->lat[c] <= 90.0))
-            return fail(nullptr, M3D_ERR_ARG, "grid: latitude of column %d out of range", c);
-        s_imp += (long long)L * L;
-    }
-    for (int i = 0; i < g->n; i++)
-        if (!(g->h[i] > 0.0) || !std::isfinite(g->h[i]) || !std::isfinite(g->zc[i]) || !std::isfinite(g->vol[i]))
-            return fail(nullptr, M3D_ERR_ARG, "grid: bad h, zc or vol at cell %d", i);
+    std::string why;
+    if (m3d_validate_inputs(g, mt, why) != M3D_OK) return fail(nullptr, M3D_ERR_ARG, "%s", why.c_str());
+    long long s_imp = mt->s_imp;
+    const int *rp = mt->exp_rowptr, *ci = mt->exp_colidx;
     if (md->nstep <= 0 || md->nsub < 1)
         return fail(nullptr, M3D_ERR_ARG, "model: nstep and nsub must be positive");
     if (md->model_id == M3D_MODEL_NDOP) {
@@ -463,26 +492,9 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
         if (md->ntracer < 1 || md->ntracer > M3D_MAX_TRACERS || md->nparam < 0)
             return fail(nullptr, M3D_ERR_ARG, "model: 1..%d tracers for the transport-only model", M3D_MAX_TRACERS);
     } else {
-        return fail(nullptr, M3D_ERR_UNSUPPORTED, "model: unknown model_id %d", md->model_id);
+        return fail(nullptr, M3D_ERR_UNSUPPORTED, "model: model_id %d is not available for a single context "
+                    "(ensembles run it)", md->model_id);
     }
-    if (mt->nmonth < 1 || mt->nnz < g->n || !mt->exp_rowptr || !mt->exp_colidx || !mt->exp_val || !mt->imp_blk)
-        return fail(nullptr, M3D_ERR_ARG, "matrices: bad sizes or null arrays");
-    if (mt->s_imp != s_imp)
-        return fail(nullptr, M3D_ERR_ARG, "matrices: s_imp is %lld, the columns need %lld", mt->s_imp, s_imp);
-    const int *rp = mt->exp_rowptr, *ci = mt->exp_colidx;
-    if (rp[0] != 0 || rp[g->n] != mt->nnz)
-        return fail(nullptr, M3D_ERR_ARG, "matrices: rowptr must run from 0 to nnz");
-    for (int i = 0; i < g->n; i++) {
-        if (rp[i + 1] < rp[i]) return fail(nullptr, M3D_ERR_ARG, "matrices: rowptr decreases at row %d", i);
-        for (int p = rp[i]; p < rp[i + 1]; p++) {
-            if (ci[p] < 0 || ci[p] >= g->n)
-                return fail(nullptr, M3D_ERR_ARG, "matrices: column index out of range in row %d", i);
-            if (p > rp[i] && ci[p] <= ci[p - 1])
-                return fail(nullptr, M3D_ERR_ARG, "matrices: row %d is not sorted or has duplicates", i);
-        }
-    }
-    if (!all_finite(mt->exp_val, (size_t)mt->nmonth * mt->nnz) || !all_finite(mt->imp_blk, (size_t)mt->nmonth * s_imp))
-        return fail(nullptr, M3D_ERR_ARG, "matrices: non-finite values");
 
     m3d_ctx *c = new (std::nothrow) m3d_ctx();
     if (!c) return fail(nullptr, M3D_ERR_ARG, "out of host memory");

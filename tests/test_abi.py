@@ -2,6 +2,7 @@
 import ctypes
 import os
 
+import numpy as np
 import pytest
 
 import paper_1410_0204_gb300 as m3d
@@ -38,3 +39,20 @@ def test_init_rejects_bad_grid_without_gpu_work(lib):
     ctx = ctypes.c_void_p()
     assert L.metos3d_init(ctypes.byref(ctx), None, None, None, None) == m3d.M3D_ERR_ARG
     assert b"null" in L.metos3d_last_error(None)
+
+
+def test_ensemble_init_rejects_bad_members_without_gpu_work(lib):
+    # member checks happen before any device call
+    import types
+    import m3d_inputs as mi
+    p = mi.make_problem("tiny_4x3x3")
+    fake_stream = types.SimpleNamespace(cuda_stream=0)
+    with pytest.raises(m3d.Metos3dError) as ei:
+        m3d.Ensemble.from_problem(p, [(mi.MODEL_NDOP, mi.default_params(mi.MODEL_NDOP)[:5])], stream=fake_stream)
+    assert ei.value.status == m3d.M3D_ERR_ARG and "parameters" in str(ei.value)
+    with pytest.raises(m3d.Metos3dError) as ei:
+        m3d.Ensemble.from_problem(p, [(4, np.zeros(4))], stream=fake_stream)
+    assert ei.value.status == m3d.M3D_ERR_UNSUPPORTED
+    with pytest.raises(m3d.Metos3dError) as ei:
+        m3d.Ensemble.from_problem(p, [], stream=fake_stream)
+    assert ei.value.status == m3d.M3D_ERR_ARG

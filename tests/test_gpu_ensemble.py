@@ -1,0 +1,208 @@
+"""Parity of the batched ensemble (metos3d_ensemble_*, through the C ABI) with the CPU oracle.
+
+The oracle of an ensemble is every member's own year map (members share only the transport).
+Tolerance as for the single year map: 1e-10 in max_i |g_i - o_i| / max(|o_i|, 1e-6 max|o|) per
+model year, per member, in FP64.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import m3d_inputs as mi
+import oracle
+from tests._util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+YEAR_TOL = 1e-10
+STEP_TOL = 1e-12
+
+# every model, several groups of 32 lanes (W = 2*1 + 3*2 + 2*3 + 5*5 = 39: two groups)
+SMALL_MIX = ((mi.MODEL_N, 2), (mi.MODEL_NDOP, 3), (mi.MODEL_PHY, 2), (mi.MODEL_NPZD, 5))
+
+
+@pytest.fixture(scope="module")
+def m3d():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1410_0204_gb300 as m
+    m.load()
+    oracle.set_threads(min(16, os.cpu_count() or 1))
+    yield m
+    oracle.set_threads(1)
+
+
+_problems = {}
+
+
+def problem(name):
+    if name not in _problems:
+        p = mi.make_problem(name)
+        _problems[name] = (p, oracle.Problem(p))
+    return _problems[name]
+
+
+def initial_states(prob, members, seed=None):
+    """Member states: the models' constant initial values, or seeded positive fields."""
+    out = []
+    for i, m in enumerate(members):
+        vals = mi.model_initial_values(m.model)
+        if seed is None:
+            out.append(mi.initial_state(prob, m.ntracer, vals))
+        else:
+            y = mi.random_state(prob, m.ntracer, seed=seed + i, scale=tuple(2.0 * v + 0.05 for v in vals))
+            out.append(y)
+    return out
+
+
+def stack(states):
+    return torch.from_numpy(np.ascontiguousarray(np.vstack(states))).cuda()
+
+
+def split(ens, Y):
+    Yh = Y.cpu().numpy()
+    return [Yh[ens.offsets[m]:ens.offsets[m + 1]] for m in range(ens.nmember)]
+
+
+def test_year_map_matches_oracle_every_model(m3d):
+    p, P = problem("ndop_64x32x8")
+    members = mi.make_ensemble(SMALL_MIX, seed=11)
+    ens = m3d.Ensemble.from_problem(p, members)
+    assert ens.width == 39 and ens.ngroup == 2
+    ys = initial_states(p, members)
+    Y1 = ens.year_map(stack(ys), torch.empty((ens.width, p.n), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert ens.last_launch_count() == p.nstep + 2
+    want = oracle.ensemble_year_map(P, ys, members)
+    for m, (g, o) in enumerate(zip(split(ens, Y1), want)):
+        assert rel_err(g, o) <= YEAR_TOL, (m, members[m].model, rel_err(g, o))
+    ens.close()
+
+
+def test_year_map_conserves_each_members_mass(m3d):
+    p, _ = problem("ndop_64x32x8")
+    members = mi.make_ensemble(SMALL_MIX, seed=12)
+    ens = m3d.Ensemble.from_problem(p, members)
+    ys = initial_states(p, members, seed=40)
+    Y1 = ens.year_map(stack(ys), torch.empty((ens.width, p.n), dtype=torch.float64, device="cuda"))
+    for y0, y1 in zip(ys, split(ens, Y1)):
+        m0 = float((y0.sum(axis=0) * p.vol).sum())
+        m1 = float((y1.sum(axis=0) * p.vol).sum())
+        assert abs(m1 - m0) <= 1e-12 * m0
+        assert np.all(np.isfinite(y1))
+    ens.close()
+
+
+def test_full_mix_steps_match_oracle_on_the_full_grid(m3d):
+    # the 64-member ensemble (16 N, 32 N-DOP, 16 NPZD-DOP; five full groups) on 128 x 64 x 15,
+    # a ragged sample of steps across a month boundary, varying states
+    p, P = problem("ndop_128x64x15")
+    members = mi.make_ensemble()
+    ens = m3d.Ensemble.from_problem(p, members)
+    assert ens.width == 160 and ens.ngroup == 5
+    ys = initial_states(p, members, seed=7)
+    j0, nsteps = 235, 13
+    Y1 = ens.steps(j0, nsteps, stack(ys), torch.empty((ens.width, p.n), dtype=torch.float64, device="cuda"))
+    want = oracle.ensemble_steps(P, j0, nsteps, ys, members)
+    for m, (g, o) in enumerate(zip(split(ens, Y1), want)):
+        assert rel_err(g, o) <= STEP_TOL, (m, members[m].model, rel_err(g, o))
+    ens.close()
+
+
+@pytest.mark.parametrize("nsub", [2, 8])
+def test_internal_model_steps_match_oracle(m3d, nsub):
+    p, P = problem("ndop_64x32x8")
+    members = mi.make_ensemble(SMALL_MIX, seed=13)
+    ens = m3d.Ensemble.from_problem(p, members, nsub=nsub)
+    ys = initial_states(p, members, seed=3)
+    Y1 = ens.steps(1000, 40, stack(ys), torch.empty((ens.width, p.n), dtype=torch.float64, device="cuda"))
+    for m, (g, y, mem) in enumerate(zip(split(ens, Y1), ys, members)):
+        o = oracle.steps(P, 1000, 40, y, mem.u, model=mem.model, nsub=nsub)
+        # 40 ocean steps of up to 320 nonlinear substeps whose multiply-adds the two sides
+        # round differently (the oracle never fuses them): a looser bar than one step's,
+        # still far inside the per-year 1e-10
+        assert rel_err(g, o) <= 1e-11, (m, mem.model, rel_err(g, o))
+    ens.close()
+
+
+def test_results_do_not_depend_on_tiling_or_neighbours(m3d):
+    # each lane runs the same arithmetic whatever the tiling and the other members
+    p, _ = problem("ndop_64x32x8")
+    members = mi.make_ensemble(SMALL_MIX, seed=14)
+    ens = m3d.Ensemble.from_problem(p, members)
+    Y0 = stack(initial_states(p, members, seed=5))
+    ref = ens.steps(700, 25, Y0, torch.empty_like(Y0)).clone()
+    for cpb, nw in ((1, 4), (2, 16), (8, 8), (32, 4)):
+        ens.set_tiling(cpb, nw)
+        assert ens.get_tiling() == (cpb, nw)
+        assert torch.equal(ens.steps(700, 25, Y0, torch.empty_like(Y0)), ref)
+    cpb, nw, ms = ens.autotune(Y0, nsteps=5)
+    assert ens.get_tiling() == (cpb, nw) and ms > 0.0
+    assert torch.equal(ens.steps(700, 25, Y0, torch.empty_like(Y0)), ref)
+    # one member alone gives bit for bit the same result
+    for m in (0, 3, 7, len(members) - 1):
+        alone = m3d.Ensemble.from_problem(p, [members[m]])
+        ym = Y0[ens.offsets[m]:ens.offsets[m + 1]].contiguous()
+        got = alone.steps(700, 25, ym, torch.empty_like(ym))
+        assert torch.equal(got, ref[ens.offsets[m]:ens.offsets[m + 1]]), m
+        alone.close()
+    ens.close()
+
+
+def test_year_graph_equals_single_launches(m3d):
+    p, _ = problem("ndop_64x32x8")
+    members = mi.make_ensemble(SMALL_MIX, seed=15)
+    ens = m3d.Ensemble.from_problem(p, members)
+    Y0 = stack(initial_states(p, members, seed=9))
+    a = ens.year_map(Y0, torch.empty_like(Y0)).clone()
+    b = ens.steps(0, p.nstep, Y0, torch.empty_like(Y0))
+    assert torch.equal(a, b)
+    # in place
+    Y = Y0.clone()
+    ens.year_map(Y, Y)
+    assert torch.equal(Y, a)
+    ens.close()
+
+
+def test_set_params_takes_effect(m3d):
+    p, P = problem("ndop_64x32x8")
+    members = mi.make_ensemble(((mi.MODEL_NDOP, 2), (mi.MODEL_NPZD, 1)), seed=16)
+    ens = m3d.Ensemble.from_problem(p, members)
+    ys = initial_states(p, members, seed=21)
+    Y0 = stack(ys)
+    before = split(ens, ens.steps(0, 30, Y0, torch.empty_like(Y0)))
+    u_new = members[2].u * 1.3
+    u_new[6] = min(u_new[6], 1.0)
+    ens.set_params(2, u_new)
+    after = split(ens, ens.steps(0, 30, Y0, torch.empty_like(Y0)))
+    assert np.array_equal(before[0], after[0]) and not np.array_equal(before[2], after[2])
+    o = oracle.steps(P, 0, 30, ys[2], u_new, model=mi.MODEL_NPZD)
+    assert rel_err(after[2], o) <= STEP_TOL
+    ens.close()
+
+
+def test_ndop_member_matches_single_context(m3d):
+    # an N-DOP member of an ensemble and the single-context year map (resident kernel) agree
+    p, _ = problem("ndop_64x32x8")
+    members = mi.make_ensemble(((mi.MODEL_NDOP, 1), (mi.MODEL_NPZD, 1)), seed=17)
+    ens = m3d.Ensemble.from_problem(p, members)
+    ys = initial_states(p, members, seed=33)
+    Y1 = ens.year_map(stack(ys), torch.empty((ens.width, p.n), dtype=torch.float64, device="cuda"))
+    ctx = m3d.Context.from_problem(p, model=m3d.MODEL_NDOP, ntracer=2, nparam=7)
+    y0 = torch.from_numpy(ys[0]).cuda()
+    y1 = ctx.year_map(y0, torch.empty_like(y0), torch.from_numpy(members[0].u).cuda())
+    assert rel_err(split(ens, Y1)[0], y1.cpu().numpy()) <= 1e-12
+    ctx.close()
+    ens.close()
+
+
+def test_rejects_oversized_tiling(m3d):
+    p, _ = problem("ndop_128x64x15")
+    ens = m3d.Ensemble.from_problem(p, mi.make_ensemble(((mi.MODEL_N, 1),), seed=1))
+    with pytest.raises(m3d.Metos3dError) as ei:
+        ens.set_tiling(4000, 16)
+    assert ei.value.status == m3d.M3D_ERR_ARG
+    ens.close()
