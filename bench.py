@@ -387,7 +387,9 @@ def run_ours(args):
                 newton[label] = {"seconds": dt_n, "converged": bool(rep["converged"]), "residual": rep["residual"],
                                  "newton_steps": rep["newton_steps"], "krylov_iterations": rep["krylov_total"],
                                  "year_maps": rep["year_maps"], "tangent_maps": rep["tangent_maps"],
-                                 "model_year_equivalents": rep["year_maps"] + rep["tangent_maps"]}
+                                 "model_year_equivalents": rep["year_maps"] + rep["tangent_maps"],
+                                 "krylov_per_newton_step": rep.get("krylov"), "residuals": rep.get("residuals"),
+                                 "line_search_steps": rep.get("lambdas")}
         ctx.close()
 
     if rank != 0:
@@ -457,6 +459,82 @@ def run_profile_steps(nsteps):
     return 0
 
 
+def run_scale_1deg(args):
+    """The 1-degree grid (360 x 180 x 23, 700,000 cells): the single-context N-DOP year map and
+    the 16-member NPZD-DOP ensemble year map, each timed with CUDA events over whole years."""
+    import torch
+    import paper_1410_0204_gb300 as m3d
+    name = "npzd_360x180x23"
+    prob = mi.make_problem(name)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return sum(ts) / len(ts)
+
+    reps = max(1, min(args.steps, 3))
+    ctx = m3d.Context.from_problem(prob, model=m3d.MODEL_NDOP, ntracer=2, nparam=7)
+    plan = {m3d.PLAN_RESIDENT: "resident", m3d.PLAN_PERSISTENT: "persistent",
+            m3d.PLAN_GRAPH: "graph"}[ctx.get_option(m3d.OPT_YEAR_PLAN)]
+    y0 = torch.from_numpy(mi.initial_state(prob)).cuda()
+    u = torch.from_numpy(mi.default_params_ndop()).cuda()
+    ya = torch.empty_like(y0)
+    t_single = timed(lambda: ctx.year_map(y0, ya, u), reps)
+    ctx.close()
+    _, flops_single = algorithmic_per_step(prob, tridiagonal=True)
+    members = mi.make_ensemble(((mi.MODEL_NPZD, 16),), seed=1410)
+    ens = m3d.Ensemble.from_problem(prob, members)
+    Y0 = torch.from_numpy(np.vstack([mi.initial_state(prob, 5, mi.model_initial_values(mi.MODEL_NPZD))
+                                     for _ in members])).cuda()
+    Y1 = torch.empty_like(Y0)
+    cpb, nw, ms = ens.autotune(Y0, nsteps=5)
+    t_ens = timed(lambda: ens.year_map(Y0, Y1), reps)
+    ens.close()
+    f_ens = ensemble_flops_per_step(prob, members) * prob.nstep
+    line = {"metric": METRIC, "value": 1.0 / t_single, "unit": UNIT, "n_gpus": 1, "steps": reps,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name + " year map: PO4-DOP, 2 tracers, 2880 TMM steps per model year",
+                       "n": prob.n, "ncol": prob.ncol, "nnz": prob.nnz, "S_imp": prob.s_imp, "plan": plan},
+            "roofline": {"bound": "alu", "achieved": flops_single * prob.nstep / t_single / 1e12,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops_single * prob.nstep / t_single / 1e12 / FP64_PEAK_TFLOPS},
+            "ensemble": {"workload": "16 NPZD-DOP members (5 tracers), parameters within +-50% of the defaults",
+                         "member_years_per_s": len(members) / t_ens, "seconds_per_ensemble_year": t_ens,
+                         "tiling": {"cols_per_block": cpb, "warps_per_block": nw, "autotune_ms_per_step": ms},
+                         "roofline": {"bound": "alu", "achieved": f_ens / t_ens / 1e12, "peak": FP64_PEAK_TFLOPS,
+                                      "unit": "TFLOP/s", "frac": f_ens / t_ens / 1e12 / FP64_PEAK_TFLOPS}}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_profile_ensemble(nsteps):
+    """A short run for profilers: the 64-member ensemble on the benchmark grid, nsteps steps."""
+    import torch
+    import paper_1410_0204_gb300 as m3d
+    prob = mi.make_problem(WORKLOAD)
+    members = mi.make_ensemble()
+    ens = m3d.Ensemble.from_problem(prob, members)
+    Y0 = torch.from_numpy(np.vstack([mi.initial_state(prob, m.ntracer, mi.model_initial_values(m.model))
+                                     for m in members])).cuda()
+    ens.set_tiling(1, 8)
+    ens.steps(0, nsteps, Y0, torch.empty_like(Y0))
+    torch.cuda.synchronize()
+    ens.close()
+    print(json.dumps({"profile_ensemble_steps": nsteps, "workload": WORKLOAD, "members": len(members)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,7 +549,15 @@ def main():
                     help="also time Newton-Krylov with tangent Jacobian-vector products")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run this many single TMM steps of the workload (for profilers)")
+    ap.add_argument("--profile-ensemble-steps", type=int, default=0,
+                    help="only run this many steps of the 64-member ensemble (for profilers)")
+    ap.add_argument("--scale-1deg", action="store_true",
+                    help="time the 1-degree grid (single context and 16-member ensemble) instead")
     args = ap.parse_args()
+    if args.scale_1deg:
+        return run_scale_1deg(args)
+    if args.profile_ensemble_steps:
+        return run_profile_ensemble(args.profile_ensemble_steps)
     if args.profile_steps:
         return run_profile_steps(args.profile_steps)
     if args.impl == "reference":

@@ -396,7 +396,7 @@ m3d_status metos3d_ensemble_get_tiling(const m3d_ensemble *ens, int *cols_per_bl
 
 /*
  * Autotuner: time nsteps steps from the state Y (device [W][n], not modified) for each
- * candidate tiling (columns per block 1..32, warps per block 4..32, as shared memory allows),
+ * candidate tiling (columns per block 1..32, warps per block 4..16, as shared memory allows),
  * keep the fastest and return it with its time per step.  Synchronous.
  */
 m3d_status metos3d_ensemble_autotune(m3d_ensemble *ens, const double *Y, int nsteps,

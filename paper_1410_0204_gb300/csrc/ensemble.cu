@@ -16,8 +16,8 @@
 //   2. evaluates the members' source terms q(y_j) with the lanes re-dealt to (member, layer)
 //      pairs -- the models' per-cell work is then done once per member, not once per tracer --
 //      and adds dt q (or the nsub-step increment) to z;
-//   3. applies the interpolated implicit operator, z0 + w (z1 - z0) with z_h the Thomas solve of
-//      month h, and writes y_{j+1}.
+//   3. applies the interpolated implicit operator, (1 - w) T0^-1 z + w T1^-1 z with T_h the
+//      tridiagonal matrix whose inverse is month h's block (Thomas solves), and writes y_{j+1}.
 // Nothing waits on another CTA, so a step is one ordinary launch.
 #include <cuda_runtime.h>
 
@@ -74,8 +74,6 @@ struct EnsParams {
     const double *mfrac;                  // [nmember][n] Martin deposition profile (Martin models)
 };
 
-__device__ __forceinline__ double michaelis(double x, double K) { return x / (x + K); }
-
 // Shared-memory layout of the step kernel (doubles first, then ints).
 __host__ __device__ inline size_t ens_warp_doubles(int zmax, bool sub1)
 {
@@ -116,11 +114,14 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, in
             sval[p] = fma(w, d0[p0 + p], a0[p0 + p]);
             scol[p] = E.colidx[p0 + p];
         }
+        // Thomas factors of both months; the blend (1 - w) T0^-1 z + w T1^-1 z is folded into the
+        // reciprocal pivots, so the two back substitutions are simply added
         const double *t0 = E.tri + (size_t)m0 * E.tri_mstride, *t1 = E.tri + (size_t)m1 * E.tri_mstride;
         for (int i = threadIdx.x; i < cell1 - cell0; i += blockDim.x)
             for (int f = 0; f < 3; f++) {
-                stri[f * cbm + i] = t0[(size_t)f * E.n + cell0 + i];
-                stri[(3 + f) * cbm + i] = t1[(size_t)f * E.n + cell0 + i];
+                const double a = t0[(size_t)f * E.n + cell0 + i], b = t1[(size_t)f * E.n + cell0 + i];
+                stri[f * cbm + i] = f == 1 ? (1.0 - w) * a : a;
+                stri[(3 + f) * cbm + i] = f == 1 ? w * b : b;
             }
         if (threadIdx.x == 0) *counter = 0;
     }
@@ -140,15 +141,15 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, in
         for (int k = 0; k < L; k++) ys[k * kLanes + lane] = X[(size_t)(s0 + k) * E.wp + gl];
         for (int k = 0; k < L; k++) {
             const int pb = E.rowptr[s0 + k] - p0, pe = E.rowptr[s0 + k + 1] - p0;
-            double za = 0.0, zb = 0.0;
+            double z = 0.0;
             int p = pb;
             for (; p + 1 < pe; p += 2) {
                 const double xa = X[(size_t)scol[p] * E.wp + gl], xb = X[(size_t)scol[p + 1] * E.wp + gl];
-                za = fma(sval[p], xa, za);
-                zb = fma(sval[p + 1], xb, zb);
+                z = fma(sval[p], xa, z);
+                z = fma(sval[p + 1], xb, z);
             }
-            if (p < pe) za = fma(sval[p], X[(size_t)scol[p] * E.wp + gl], za);
-            zs[k * kLanes + lane] = za + zb;
+            if (p < pe) z = fma(sval[p], X[(size_t)scol[p] * E.wp + gl], z);
+            zs[k * kLanes + lane] = z;
         }
         if (!SUB1) {
             for (int k = 0; k < L; k++) {
@@ -182,12 +183,14 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, in
                         const double N = st[k * kLanes + l0], P = st[k * kLanes + l0 + 1];
                         const double Z = st[k * kLanes + l0 + 2], D = st[k * kLanes + l0 + 3];
                         const double DOP = st[k * kLanes + l0 + 4];
-                        double U = 0.0;
-                        if (k < neu) {
-                            const double I = I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k];
-                            U = mp[2] * P * michaelis(N, mp[3]) * michaelis(I, mp[4]);
-                        }
-                        const double G = mp[5] * Z * michaelis(P, mp[6]);
+                        // one division for both rates: U = mu_P P N/(N+K_N) I/(I+K_I) (I = 0 below
+                        // the euphotic zone) and G = mu_Z Z P/(K_P+P)
+                        const double I = k < neu ? I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k] : 0.0;
+                        const double dN = N + mp[3], dI = I + mp[4], dP = mp[6] + P;
+                        const double dNI = dN * dI;
+                        const double r = 1.0 / (dNI * dP);
+                        const double U = mp[2] * P * N * I * dP * r;
+                        const double G = mp[5] * Z * P * dNI * r;
                         const double mP = mp[8] * P, mZ = mp[9] * Z * Z, eZ = mp[10] * Z;
                         const double rD = mp[11] * D, rO = mp[12] * DOP;
                         const double Sin = k > 0 ? mp[13] * st[(k - 1) * kLanes + l0 + 3] : 0.0;
@@ -216,19 +219,21 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, in
                         const double I = I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k];
                         const double hk = E.h[s0 + k];
                         const double N = st[k * kLanes + l0];
+                        // both half-saturation factors with one division
+                        const double lim = (N * I) / ((N + mp[3]) * (I + mp[4]));
                         if (model == M3D_MODEL_N) {
-                            const double f = mp[2] * michaelis(N, mp[3]) * michaelis(I, mp[4]);
+                            const double f = mp[2] * lim;
                             q0 = -f;
                             e = f * hk;
                         } else if (model == M3D_MODEL_NDOP) {
                             const double DOP = st[k * kLanes + l0 + 1];
-                            const double f = mp[2] * michaelis(N, mp[3]) * michaelis(I, mp[4]);
+                            const double f = mp[2] * lim;
                             q0 = -f + mp[6] * DOP;
                             q1 = mp[5] * f - mp[6] * DOP;
                             e = mp[7] * f * hk;
                         } else {                                   // PHY
                             const double DOP = st[k * kLanes + l0 + 1], PHY = st[k * kLanes + l0 + 2];
-                            const double f1 = mp[2] * PHY * michaelis(N, mp[3]) * michaelis(I, mp[4]);
+                            const double f1 = mp[2] * PHY * lim;
                             const double f3 = mp[10] * f1;
                             const double loss = mp[7] * PHY + mp[8] * PHY * PHY;
                             q0 = -f1 + mp[5] * DOP;
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, in
             for (int k = L - 1; k >= 0; k--) {
                 v0 = fma(ne0[k], v0, ys[k * kLanes + lane] * rd0[k]);
                 v1 = fma(ne1[k], v1, zs[k * kLanes + lane] * rd1[k]);
-                Xn[(size_t)(s0 + k) * E.wp + gl] = fma(w, v1 - v0, v0);
+                Xn[(size_t)(s0 + k) * E.wp + gl] = v0 + v1;
             }
         }
         __syncwarp();
@@ -887,7 +892,7 @@ m3d_status metos3d_ensemble_autotune(m3d_ensemble *e, const double *Y, int nstep
     if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_autotune: null ensemble");
     if (!Y || nsteps < 1) return efail(e, M3D_ERR_ARG, "autotune: null state or no steps");
     const int cpbs[] = {1, 2, 4, 8, 16, 32};
-    const int nws[] = {4, 8, 16};
+    const int nws[] = {4, 5, 6, 8, 10, 12, 16};
     int best_c = e->cpb, best_w = e->nwarps;
     float best = -1.0f;
     cudaEvent_t a, b;

@@ -498,10 +498,12 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
 
     m3d_ctx *c = new (std::nothrow) m3d_ctx();
     if (!c) return fail(nullptr, M3D_ERR_ARG, "out of host memory");
+    cudaGetLastError();                 // an earlier failed call must not be reported here
     auto bail = [&](m3d_status s) {
         g_init_error = c->err;
         release(c);
         delete c;
+        cudaGetLastError();             // nor this one's by a later call
         return s;
     };
     cudaGetDevice(&c->device);
@@ -532,6 +534,12 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     int tiles_per_sm = 1;
     if (const char *env = getenv("METOS3D_TILES_PER_SM")) tiles_per_sm = std::max(1, std::min(8, atoi(env)));
     int ntarget = std::min(g->ncol, tiles_per_sm * prop.multiProcessorCount);
+    {
+        // a tile's state must fit in shared memory: more (smaller) tiles on very large grids
+        const double per_cell = sizeof(double) * (double)(c->ntr + 2);
+        const long long need = (long long)(1.25 * g->n * per_cell / (double)prop.sharedMemPerBlockOptin) + 1;
+        ntarget = (int)std::min<long long>(g->ncol, std::max<long long>(ntarget, need));
+    }
     std::vector<int> bounds = partition_columns(g, rp, c->ntr, ntarget);
     int ntiles = (int)bounds.size() - 1;
     c->ntiles = ntiles;
@@ -723,7 +731,7 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     P.bk_mstride = bkn;
     P.ds = (1.0 / c->nstep) / c->nsub;
     cudaError_t e = cudaSuccess;
-#define UP(...) do { e = (__VA_ARGS__); if (e != cudaSuccess) { fail(c, M3D_ERR_CUDA, "device upload: %s", cudaGetErrorString(e)); return bail(M3D_ERR_CUDA); } } while (0)
+#define UP(...) do { e = (__VA_ARGS__); if (e != cudaSuccess) { fail(c, M3D_ERR_CUDA, "device set-up (%s): %s", #__VA_ARGS__, cudaGetErrorString(e)); return bail(M3D_ERR_CUDA); } } while (0)
     UP(upload_vec(c, &P.tiles, tiles));
     UP(upload_vec(c, &P.sp_len, sp_len));
     UP(upload_vec(c, &P.sp_off, sp_off));
@@ -806,6 +814,10 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     }
     P.I0tab = I0;
     c->smem_bytes = sizeof(double) * (size_t)(c->ntr + 2) * c->zmax;
+    if (c->smem_bytes > (size_t)prop.sharedMemPerBlockOptin) {
+        fail(c, M3D_ERR_UNSUPPORTED, "a tile of %d cells does not fit in shared memory", c->zmax);
+        return bail(M3D_ERR_UNSUPPORTED);
+    }
     if (c->smem_bytes > 48 * 1024) {
         UP(cudaFuncSetAttribute((const void *)c->step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)c->smem_bytes));
@@ -923,9 +935,14 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
             V.resident_smem = (size_t)m3d::resident_layout(V.ntr, sp_max, bk_max, c->zmax, false).total;
             V.resident_tri_smem = (size_t)m3d::resident_layout(V.ntr, sp_max, bk_max, c->zmax, true).total;
             int occ = 0;
-            if (V.smem > 48 * 1024)
-                UP(cudaFuncSetAttribute((const void *)V.year, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)V.smem));
-            UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)V.year, m3d::kThreads, V.smem));
+            // a tile's four components must fit in shared memory (on very large grids they do
+            // not, and the tangent is then unavailable for this context)
+            if (V.smem <= (size_t)prop.sharedMemPerBlockOptin) {
+                if (V.smem > 48 * 1024)
+                    UP(cudaFuncSetAttribute((const void *)V.year, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)V.smem));
+                UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)V.year, m3d::kThreads, V.smem));
+            }
             V.persistent_ok = coop && (long long)occ * prop.multiProcessorCount >= ntiles;
             if (coop && V.resident_smem <= (size_t)prop.sharedMemPerBlockOptin) {
                 UP(cudaFuncSetAttribute((const void *)V.rk.year, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -119,12 +119,18 @@ def test_internal_model_steps_match_oracle(m3d, nsub):
     ens = m3d.Ensemble.from_problem(p, members, nsub=nsub)
     ys = initial_states(p, members, seed=3)
     Y1 = ens.steps(1000, 40, stack(ys), torch.empty((ens.width, p.n), dtype=torch.float64, device="cuda"))
+    r = np.random.default_rng(0)
     for m, (g, y, mem) in enumerate(zip(split(ens, Y1), ys, members)):
         o = oracle.steps(P, 1000, 40, y, mem.u, model=mem.model, nsub=nsub)
-        # 40 ocean steps of up to 320 nonlinear substeps whose multiply-adds the two sides
-        # round differently (the oracle never fuses them): a looser bar than one step's,
-        # still far inside the per-year 1e-10
-        assert rel_err(g, o) <= 1e-11, (m, mem.model, rel_err(g, o))
+        # The two sides round differently (fused multiply-adds, one shared division), and
+        # 40 ocean steps of a grazing model from random states amplify rounding-level input
+        # differences by up to ~1e4.  The bar is the oracle's own response to a perturbation
+        # of its input by a few units in the last place, with headroom, and never above the
+        # per-year 1e-10.
+        o_pert = oracle.steps(P, 1000, 40, y * (1.0 + 4e-16 * r.standard_normal(y.shape)), mem.u,
+                              model=mem.model, nsub=nsub)
+        bar = min(1e-10, max(STEP_TOL, 20.0 * rel_err(o_pert, o)))
+        assert rel_err(g, o) <= bar, (m, mem.model, rel_err(g, o), bar)
     ens.close()
 
 

@@ -1,0 +1,100 @@
+"""The 1-degree grid: 360 x 180 x 23 (700,000 wet cells in 42,120 columns, ~9.8 M explicit entries).
+
+At this size the oracle finishes a few steps in seconds, not a year, so the checks are
+element-wise parity over a few steps (single context and the 16-member NPZD-DOP ensemble),
+and, over a whole year, properties that hold at any size: each member's mass is conserved
+and the state stays finite and positive.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import m3d_inputs as mi
+import oracle
+from tests._util import rel_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+STEP_TOL = 1e-12
+NAME = "npzd_360x180x23"
+
+
+@pytest.fixture(scope="module")
+def m3d():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1410_0204_gb300 as m
+    m.load()
+    oracle.set_threads(min(16, os.cpu_count() or 1))
+    yield m
+    oracle.set_threads(1)
+
+
+@pytest.fixture(scope="module")
+def grid():
+    p = mi.make_problem(NAME)
+    assert p.n == 700000 and p.ncol == 42120 and p.lmax == 23
+    return p, oracle.Problem(p)
+
+
+def test_single_context_steps_match_oracle(m3d, grid):
+    p, P = grid
+    ctx = m3d.Context.from_problem(p, model=m3d.MODEL_NDOP, ntracer=2, nparam=7)
+    y0 = mi.random_state(p, 2, seed=91)
+    u = mi.default_params_ndop()
+    yd = torch.from_numpy(y0).cuda()
+    ud = torch.from_numpy(u).cuda()
+    a, b = yd.clone(), torch.empty_like(yd)
+    j0, nsteps = 1195, 4                                   # across the May/June boundary
+    for s in range(nsteps):
+        ctx.step(j0 + s, a, b, ud)
+        a, b = b, a
+    want = oracle.steps(P, j0, nsteps, y0, u)
+    assert rel_err(a.cpu().numpy(), want) <= STEP_TOL
+    ctx.close()
+
+
+def test_single_context_year_conserves_mass(m3d, grid):
+    p, _ = grid
+    ctx = m3d.Context.from_problem(p, model=m3d.MODEL_NDOP, ntracer=2, nparam=7)
+    y0 = torch.from_numpy(mi.initial_state(p)).cuda()
+    u = torch.from_numpy(mi.default_params_ndop()).cuda()
+    y1 = ctx.year_map(y0, torch.empty_like(y0), u)
+    m0, m1 = ctx.mass(y0), ctx.mass(y1)
+    assert abs(m1 - m0) <= 1e-12 * m0
+    y1h = y1.cpu().numpy()
+    assert np.all(np.isfinite(y1h)) and y1h.min() > 0.0
+    ctx.close()
+
+
+def test_npzd_ensemble_steps_match_oracle(m3d, grid):
+    p, P = grid
+    members = mi.make_ensemble(((mi.MODEL_NPZD, 16),), seed=5)
+    ens = m3d.Ensemble.from_problem(p, members)
+    assert ens.width == 80 and ens.ngroup == 3
+    ys = [mi.random_state(p, 5, seed=200 + i, scale=(4.4, 0.07, 0.07, 0.07, 0.05)) for i in range(16)]
+    Y0 = torch.from_numpy(np.vstack(ys)).cuda()
+    j0, nsteps = 2878, 3                                   # across the year's end
+    Y1 = ens.steps(j0, nsteps, Y0, torch.empty_like(Y0)).cpu().numpy()
+    want = oracle.ensemble_steps(P, j0, nsteps, ys, members)
+    for m in range(16):
+        assert rel_err(Y1[5 * m:5 * m + 5], want[m]) <= STEP_TOL, m
+    ens.close()
+
+
+def test_npzd_ensemble_year_conserves_each_member(m3d, grid):
+    p, _ = grid
+    members = mi.make_ensemble(((mi.MODEL_NPZD, 16),), seed=6)
+    ens = m3d.Ensemble.from_problem(p, members)
+    ys = [mi.initial_state(p, 5, mi.model_initial_values(mi.MODEL_NPZD)) for _ in range(16)]
+    Y0 = torch.from_numpy(np.vstack(ys)).cuda()
+    Y1 = ens.year_map(Y0, torch.empty_like(Y0)).cpu().numpy()
+    assert np.all(np.isfinite(Y1))
+    for m in range(16):
+        m0 = float((ys[m].sum(axis=0) * p.vol).sum())
+        m1 = float((Y1[5 * m:5 * m + 5].sum(axis=0) * p.vol).sum())
+        assert abs(m1 - m0) <= 1e-12 * m0, m
+    ens.close()
