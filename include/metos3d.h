@@ -159,8 +159,10 @@ m3d_status metos3d_year_tangent(m3d_ctx *ctx, const double *y0, const double *v,
  * ubar = phi_u(y0; u)^T ybar1 (host [nparam], may be NULL), the gradient of <ybar1, y1>
  * with respect to the state and the model parameters.  The forward sweep keeps one
  * checkpoint every ckpt_every steps (<= 0: 240) and recomputes each segment before its
- * reverse sweep: about three year maps of work and ckpt_every + 1 states of memory,
- * allocated for the call.  PO4-DOP with one internal step and the resident plan only
+ * reverse sweep: about four year maps of work and ckpt_every + 1 states of memory,
+ * allocated for the call.  ckpt_every >= nstep keeps the whole trajectory (nstep + 1
+ * states; 2.4 GB for 52,749 cells and two tracers) and recomputes nothing, about three year
+ * maps of work.  PO4-DOP with one internal step and the resident plan only
  * (M3D_ERR_UNSUPPORTED otherwise).  Synchronous.
  */
 m3d_status metos3d_year_adjoint(m3d_ctx *ctx, const double *y0, const double *u, const double *ybar1,
