@@ -745,14 +745,18 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     UP(upload_vec(c, &P.bk_cb, bk_cb));
     UP(upload_vec(c, &P.bk_L, bk_L));
     {
-        std::vector<int> spw, spwo, bkw, bkwo;
+        std::vector<int> spw, spwo, bkw, bkwo, spwg, spwog;
         const int nwarps = m3d::kThreads / 32;
         for (int t = 0; t < ntiles; t++) {
             deal_slices(tiles[t].sp0, tiles[t].sp1, sp_len, nwarps, spw, spwo);
             deal_slices(tiles[t].bk0, tiles[t].bk1, bk_len, nwarps, bkw, bkwo);
+            // the resident kernel's explicit group (its other warps evaluate the source term)
+            deal_slices(tiles[t].sp0, tiles[t].sp1, sp_len, m3d::kSpThreads / 32, spwg, spwog);
         }
         UP(upload_vec(c, &P.sp_wlist, spw));
         UP(upload_vec(c, &P.sp_woff, spwo));
+        UP(upload_vec(c, &P.sp_wlist_g, spwg));
+        UP(upload_vec(c, &P.sp_woff_g, spwog));
         UP(upload_vec(c, &P.bk_wlist, bkw));
         UP(upload_vec(c, &P.bk_woff, bkwo));
     }

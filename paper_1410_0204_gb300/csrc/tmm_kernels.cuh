@@ -21,6 +21,12 @@ namespace m3d {
 #define M3D_THREADS 512
 #endif
 constexpr int kThreads = M3D_THREADS; // threads per tile CTA (512: 16 warps, 4 per SM sub-partition)
+// The resident year kernel splits its CTA: the last kQWarps warps evaluate the source term
+// while the others wait for the neighbouring tiles and apply the explicit matrix.
+constexpr int kQWarps = 4;
+constexpr int kQThreads = kQWarps * 32;
+constexpr int kSpThreads = kThreads - kQThreads;
+static_assert(kSpThreads % 128 == 0, "the explicit group must span the four SM sub-partitions evenly");
 constexpr int kModelNone = 0;
 constexpr int kModelNdop = 2;
 constexpr int kModelNdopTangent = 102;   // PO4-DOP with its tangent: state (N, DOP, dN, dDOP)
@@ -61,6 +67,9 @@ struct StepParams {
     // on sub-partition w mod 4, each with its own FP64 unit) get equal FP64 work: the slices
     // of warp w of tile t are wlist[woff[t*(nwarps+1) + w] .. woff[t*(nwarps+1) + w + 1])
     const int *sp_wlist, *sp_woff, *bk_wlist, *bk_woff;
+    // the same explicit slices dealt to the kSpThreads / 32 warps of the resident kernel's
+    // explicit group: sp_wlist_g[sp_woff_g[t*(ng+1) + w] .. sp_woff_g[t*(ng+1) + w + 1])
+    const int *sp_wlist_g, *sp_woff_g;
     const double *bk_b, *bk_d;             // [nmonth][...]: B_m and B_{m+1} - B_m
     long long bk_mstride;
     // biogeochemistry
@@ -259,11 +268,14 @@ struct StateView {
     }
 };
 
-// Barrier over the first kThreads - 32 threads of the CTA (named barrier 1), or the whole CTA.
+// Barriers: 0, the whole CTA; 1, its first kThreads - 32 threads; 2, its last kQThreads
+// threads (the source-term group); 3, its first kSpThreads threads (the explicit group).
 __device__ __forceinline__ void barrier_sub(int id)
 {
     if (id == 0) __syncthreads();
-    else asm volatile("bar.sync 1, %0;" :: "n"(kThreads - 32) : "memory");
+    else if (id == 1) asm volatile("bar.sync 1, %0;" :: "n"(kThreads - 32) : "memory");
+    else if (id == 2) asm volatile("bar.sync 2, %0;" :: "n"(kQThreads) : "memory");
+    else asm volatile("bar.sync 3, %0;" :: "n"(kSpThreads) : "memory");
 }
 
 // Access to the model state of one cell as a scalar (N or DOP) or, for the tangent, as a
@@ -304,17 +316,17 @@ template <> struct ModelState<Dual> {
 
 // The source-minus-sink increment of the PO4-DOP model (Section 2.2.1) for every cell of a
 // tile, computed from y_j and written to dq[t * zmax + i].  Reads only the tile's own cells.
-// Run by threads [0, nthr) of the CTA, which synchronise on named barrier `bar`:
+// Run by threads [tid0, tid0 + nthr) of the CTA, which synchronise on barrier `bar`:
 // euphotic cells first, then aphotic cells (which need their column's export) and the
 // export kept in the bottom layer of shallow columns.  With several internal steps a
 // shallow column runs whole on one thread, since its cells then couple at every step.
 // T = double: the model; T = Dual: the model and its tangent (ek then holds 2 * zmax).
 template <class T, class SV>
 __device__ __forceinline__ void ndop_source_tile(const StepParams &P, const Tile &T_, int j, const SV &Y,
-                                                 double *dq, double *ek, int nthr, int bar)
+                                                 double *dq, double *ek, int nthr, int bar, int tid0 = 0)
 {
     typedef ModelState<T> MS;
-    const int tid = threadIdx.x;
+    const int tid = (int)threadIdx.x - tid0;
     const int zmax = P.zmax;
     const double alpha = __ldg(P.qpar + kQAlpha), sigma = __ldg(P.qpar + kQSigma);
     const double lambda = __ldg(P.qpar + kQLambda), KN = __ldg(P.qpar + kQKN);

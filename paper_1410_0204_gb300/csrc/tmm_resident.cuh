@@ -43,7 +43,7 @@ __host__ __device__ inline int pack_chain(int cb, int L, int t, int h) { return 
 
 // Shared memory layout of one tile, in bytes from the dynamic shared memory base.
 struct ResidentLayout {
-    int sa, sd, sb, sbd, si, tri, yt, z, ek, aux, total;
+    int sa, sd, sb, sbd, si, tri, yt, z, dq, ek, aux, total;
 };
 
 __host__ __device__ inline ResidentLayout resident_layout(int ntr, int sp_max, int bk_max, int zmax, bool tri)
@@ -59,6 +59,7 @@ __host__ __device__ inline ResidentLayout resident_layout(int ntr, int sp_max, i
     L.si = o;  o += sp_max * 4;
     o = (o + 15) & ~15;
     L.z = o;   o += ntr * zmax * 8;
+    L.dq = o;  o += ntr * zmax * 8;                  // source increment (written while z is)
     L.ek = o;  o += 2 * zmax * 8;
     L.aux = o; o += zmax * 8;
     L.total = (o + 15) & ~15;
@@ -82,7 +83,7 @@ __device__ __forceinline__ void copy_to_shared_int(int *dst, const int *__restri
 
 // Shared memory views of one tile.
 struct TileSmem {
-    double *sa, *sd, *sb, *sbd, *tl, *yt, *z, *ek, *aux;
+    double *sa, *sd, *sb, *sbd, *tl, *yt, *z, *dq, *ek, *aux;
     int *si;
     int sp_first, bk_first;     // first slot of the tile's explicit / implicit slices
 };
@@ -98,6 +99,7 @@ __device__ __forceinline__ TileSmem tile_smem(unsigned char *dsm, const Resident
     M.tl = reinterpret_cast<double *>(dsm + Ly.tri);
     M.yt = reinterpret_cast<double *>(dsm + Ly.yt);
     M.z = reinterpret_cast<double *>(dsm + Ly.z);
+    M.dq = reinterpret_cast<double *>(dsm + Ly.dq);
     M.ek = reinterpret_cast<double *>(dsm + Ly.ek);
     M.aux = reinterpret_cast<double *>(dsm + Ly.aux);
     M.si = reinterpret_cast<int *>(dsm + Ly.si);
@@ -135,17 +137,18 @@ __device__ __forceinline__ void load_implicit_month(const StepParams &P, const R
 }
 
 // Explicit part from shared memory: z[t][row] = (A_m0 + w D_m0) y for the tile's rows, plus
-// z[t][row] when ADD (z then holds the source increment).  Neighbour state from L2.
+// z[t][row] when ADD (z then holds the source increment).  Neighbour state from L2.  Run by
+// warp `warp` of `nwarps` warps that share the tile's slices as the deal (wlist, woff) gives.
 template <int NTR, bool ADD>
 __device__ __forceinline__ void spmv_resident(const StepParams &P, const Tile &T, double w,
-                                              const double *__restrict__ y, const TileSmem &M)
+                                              const double *__restrict__ y, const TileSmem &M,
+                                              const int *wlist, const int *woff, int nwarps, int warp)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int zmax = P.zmax;
     const StateView<NTR, true, true> Y{y, P.n};
-    const int *wl = P.sp_wlist + __ldg(P.sp_woff + blockIdx.x * (nwarps + 1) + warp);
-    const int wn = __ldg(P.sp_woff + blockIdx.x * (nwarps + 1) + warp + 1) -
-                   __ldg(P.sp_woff + blockIdx.x * (nwarps + 1) + warp);
+    const int *wl = wlist + __ldg(woff + blockIdx.x * (nwarps + 1) + warp);
+    const int wn = __ldg(woff + blockIdx.x * (nwarps + 1) + warp + 1) - __ldg(woff + blockIdx.x * (nwarps + 1) + warp);
     for (int ws = 0; ws < wn; ws++) {
         const int s = __ldg(wl + ws);
         const int len = __ldg(P.sp_len + s);
@@ -168,6 +171,14 @@ __device__ __forceinline__ void spmv_resident(const StepParams &P, const Tile &T
             for (int t = 0; t < NTR; t++) M.z[t * zmax + row] = ADD ? acc[t] + M.z[t * zmax + row] : acc[t];
         }
     }
+}
+
+// The explicit part by all warps of the CTA.
+template <int NTR, bool ADD>
+__device__ __forceinline__ void spmv_resident(const StepParams &P, const Tile &T, double w,
+                                              const double *__restrict__ y, const TileSmem &M)
+{
+    spmv_resident<NTR, ADD>(P, T, w, y, M, P.sp_wlist, P.sp_woff, (int)(blockDim.x >> 5), (int)(threadIdx.x >> 5));
 }
 
 // Write the tile's values v[t] of one cell into the interleaved state.
@@ -296,23 +307,41 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
             load_explicit_month(P, RT, P.sp_a, P.sp_d, m0, M);
             load_implicit_month<TRI>(P, R, RT, T, R.tri, P.bk_b, P.bk_d, m0, M);
             cur_month = m0;
+            __syncthreads();
         }
-        // The source term needs only this tile's own cells: the last warp waits for the
-        // neighbouring tiles while the other warps compute it.
-        const int nwork = blockDim.x - 32;
-        if ((int)threadIdx.x < nwork) {
+        // Two groups work at once.  The source term needs only this tile's own cells, so the
+        // last kQWarps warps compute it into dq straight away; the explicit group waits for
+        // the neighbouring tiles (warp 0 polls, the others at a named barrier) and then
+        // forms z = A_exp y.  The source term's divisions and sums are latency-bound and the
+        // explicit part is FP64-throughput-bound, so together they keep the FP64 pipes busier.
+        if ((int)threadIdx.x >= kSpThreads) {
             if (ModelTraits<MODEL>::has_q) {
                 const StateView<NTR, true, true> Y{y, P.n};
-                ndop_source_tile<typename ModelTraits<MODEL>::scalar>(P, T, j, Y, M.z, M.ek, nwork, 1);
+                ndop_source_tile<typename ModelTraits<MODEL>::scalar>(P, T, j, Y, M.dq, M.ek, kQThreads, 2,
+                                                                      kSpThreads);
             }
-        } else if (s > 0) {
-            bool ok = wait_neighbours(S, tile, s, s);
-            if (threadIdx.x == nwork) abort_flag = ok ? 0 : 1;
+        } else {
+            if (s > 0) {
+                if (threadIdx.x < 32) {
+                    const bool ok = wait_neighbours(S, tile, s, s);
+                    if (threadIdx.x == 0) abort_flag = ok ? 0 : 1;
+                }
+                barrier_sub(3);
+            }
+            if (s == 0 || !abort_flag)
+                spmv_resident<NTR, false>(P, T, w, y, M, P.sp_wlist_g, P.sp_woff_g, kSpThreads / 32,
+                                          (int)(threadIdx.x >> 5));
         }
         __syncthreads();
         if (s > 0 && abort_flag) return;
-        spmv_resident<NTR, ModelTraits<MODEL>::has_q>(P, T, w, y, M);
-        __syncthreads();
+        if (ModelTraits<MODEL>::has_q) {
+            const int nc = T.ncell, zmax = P.zmax;
+            for (int e = threadIdx.x; e < NTR * nc; e += blockDim.x) {
+                const int t = e / nc, i = e - t * nc;
+                M.z[t * zmax + i] += M.dq[t * zmax + i];
+            }
+            __syncthreads();
+        }
         implicit_resident<NTR, TRI>(P, R, T, w, M, yn);
         // the CTA barrier orders every thread's stores of y_{j+1} before thread 0's release
         __syncthreads();
