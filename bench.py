@@ -50,7 +50,7 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the year kernel, from one ncu capture of this
 # workload (see profiles/); None where no capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {("resident", True): 178585088 + 4218624}
+TRAFFIC_PER_LAUNCH = {("resident", True): 178737664 + 3484416}
 
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz maximum SM clock.
 # (A DFMA throughput probe on this GPU measured 1.20 TFLOP/s, 1.92 FMA/clock/SM at the
@@ -233,6 +233,21 @@ def cpu_baseline(prob, seconds=12.0, max_steps=2880):
                       % (steps, WORKLOAD, threads, dt)}
 
 
+def max_over_ranks(seconds, pg, device):
+    """The slowest rank's time (every rank gets it); seconds unchanged without a process group."""
+    if pg is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, seconds):
+    """Units of all ranks per second of the slowest rank (weak scaling: every rank does the same work)."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -319,12 +334,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
-        total = sum(times)
-        if pg:
-            t = torch.tensor([total], dtype=torch.float64, device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            total = float(t.item())
-        value = world * args.steps / total
+        total = max_over_ranks(sum(times), pg, "cuda")
+        value = whole_job_rate(world, args.steps, total)
 
         # end to end through the C ABI with host buffers (pinned), copies inside the timed region
         y0_pin = torch.from_numpy(y0_h).pin_memory()
@@ -335,12 +346,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             ctx.year_map_host_ptr(y0_pin.data_ptr(), y1_pin.data_ptr(), u_pin.data_ptr())
-        e2e_dt = time.perf_counter() - t0
-        e2e_value = world * e2e_steps / e2e_dt if world == 1 else None
-        if pg:
-            t = torch.tensor([e2e_dt], dtype=torch.float64, device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_value = world * e2e_steps / float(t.item())
+        e2e_dt = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
+        e2e_value = whole_job_rate(world, e2e_steps, e2e_dt)
 
         # cost of the adjoint year map (checkpoint every 240 steps) and of the tangent year map,
         # each relative to one year map, wall clock with the device synchronised on both sides

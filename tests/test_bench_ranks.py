@@ -1,0 +1,58 @@
+"""The multi-rank path of bench.py on the CPU: two gloo ranks on 127.0.0.1.
+
+Each rank runs its own replica; the job's time is the slowest rank's (every rank must learn
+it), and the whole-job rate counts the units of all ranks over that time.
+"""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    assert bench.dist_env() == (world, rank, rank)
+    t = bench.max_over_ranks(1.0 + rank, dist, "cpu")          # rank r "took" 1 + r seconds
+    rate = bench.whole_job_rate(world, 10, t)
+    dist.barrier()
+    out.put((rank, t, rate))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_take_the_slowest_time():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [g[1] for g in got] == [2.0, 2.0]
+    assert [g[2] for g in got] == [10.0, 10.0]               # 2 ranks x 10 units / 2 s
+
+
+def test_single_process_needs_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+    assert bench.whole_job_rate(1, 7, 3.5) == 2.0

@@ -131,3 +131,65 @@ def test_autograd_function(m3d):
     assert torch.equal(y0.grad, ybar0)
     assert np.array_equal(u.grad.cpu().numpy(), ubar)
     ctx.close()
+
+
+@pytest.mark.slow
+def test_adjoint_matches_oracle_full_grid(m3d):
+    # the benchmark's 128 x 64 x 15 grid, seeded state and cotangent, checkpoint every 240 steps
+    import os
+    oracle.set_threads(min(16, os.cpu_count() or 1))
+    p = mi.make_problem("ndop_128x64x15")
+    P = oracle.Problem(p)
+    u = mi.default_params_ndop()
+    y0 = mi.random_state(p, seed=21)
+    wbar = mi.random_state(p, seed=22) - 1.0
+    ctx = m3d.Context.from_problem(p)
+    ybar0 = torch.empty((2, p.n), dtype=torch.float64, device="cuda")
+    ubar = ctx.year_adjoint(cuda(y0), cuda(u), cuda(wbar), ybar0, 240)
+    want_y, want_u = oracle.year_adjoint(P, y0, u, wbar)
+    oracle.set_threads(1)
+    assert rel(ybar0.cpu().numpy(), want_y) < 1e-10
+    assert np.abs(ubar - want_u).max() <= 1e-9 * np.abs(want_u).max()
+    ctx.close()
+
+
+@pytest.mark.slow
+def test_misfit_gradient_at_the_periodic_solution_full_grid(m3d):
+    """The parameter-optimisation gradient on the benchmark grid: observations are the periodic
+    solution at seeded perturbed parameters plus 5 % Gaussian noise on a random 10 % of the
+    wet cells; J(u) = 1/2 |M (phi(y*; u) - obs)|^2 from the periodic solution y* of the
+    default parameters (held fixed).  The adjoint's gradient (checkpoint every 240 steps) must
+    match central differences with h = 1e-6 relative."""
+    p = mi.make_problem("ndop_128x64x15")
+    r = mi.rng(1410, "observations")
+    u0 = mi.default_params_ndop()
+    u_true = u0 * r.uniform(0.9, 1.1, 7)
+    ctx = m3d.Context.from_problem(p)
+    periodic = {}
+    for name, uu in (("true", u_true), ("default", u0)):
+        y = cuda(mi.initial_state(p))
+        st, rep = ctx.newton_solve(y, cuda(uu), tol=1e-8)
+        assert rep["converged"], name
+        periodic[name] = y
+    mask = cuda((r.random((2, p.n)) < 0.1).astype(np.float64))
+    obs = periodic["true"] * cuda(1.0 + 0.05 * r.standard_normal((2, p.n)))
+    ystar = periodic["default"]
+
+    def J(uu):
+        y1 = torch.empty_like(ystar)
+        ctx.year_map(ystar, y1, cuda(uu))
+        return 0.5 * float(torch.sum((mask * (y1 - obs)) ** 2))
+
+    y1 = torch.empty_like(ystar)
+    ctx.year_map(ystar, y1, cuda(u0))
+    ybar1 = mask * mask * (y1 - obs)
+    grad = ctx.year_adjoint(ystar, cuda(u0), ybar1, torch.empty_like(ystar), 240)
+    J0 = J(u0)
+    for k in range(7):
+        e = 1e-6 * u0[k]
+        up, um = u0.copy(), u0.copy()
+        up[k] += e
+        um[k] -= e
+        fd = (J(up) - J(um)) / (2 * e)
+        assert abs(grad[k] - fd) <= 1e-5 * abs(fd) + 1e-9 * J0, (k, grad[k], fd)
+    ctx.close()
