@@ -342,7 +342,8 @@ m3d_status metos3d_newton_solve(m3d_ctx *ctx, double *y, const double *u, const 
  * single-context layout.  Internally the tracers are packed into groups of 32 lanes (no
  * member split between groups) and stored cell-major.
  * The implicit matrices must be inverses of tridiagonal matrices (see M3D_IMPLICIT_TRIDIAGONAL);
- * otherwise init returns M3D_ERR_UNSUPPORTED.
+ * otherwise init returns M3D_ERR_UNSUPPORTED.  An ensemble is bound to one device and one
+ * stream and is not thread-safe.
  */
 typedef struct m3d_ensemble m3d_ensemble;   /* opaque; owned by the library */
 typedef struct {
