@@ -50,7 +50,7 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the year kernel, from one ncu capture of this
 # workload (see profiles/); None where no capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {("resident", True): 178737664 + 3484416}
+TRAFFIC_PER_LAUNCH = {("resident", True): 178786304 + 4192256}
 
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz maximum SM clock.
 # (A DFMA throughput probe on this GPU measured 1.20 TFLOP/s, 1.92 FMA/clock/SM at the

@@ -147,6 +147,8 @@ m3d_status setup_adjoint(m3d_ctx *c, const AdjointSetup &in)
                 ok = tridiagonal_factors(blk.data(), L, base + s0, base + n + s0, base + 2 * (size_t)n + s0);
             }
         if (ok) {
+            for (int m = 0; m < c->nmonth; m++)
+                thomas_backsubstitution_form(tri.data() + (size_t)m * 3 * n, n, g->col_start, g->ncol);
             const double *tri_dev = nullptr;
             e = upload_vec(c, &tri_dev, tri);
             RT.tri = tri_dev;

@@ -106,3 +106,5 @@ cudaError_t m3d_alloc(m3d_ctx *c, void **p, size_t bytes);
 m3d_status m3d_validate_inputs(const m3d_grid *g, const m3d_matrices *mt, std::string &why);
 // Thomas factors of M when the row-major L x L block B is M's inverse and M is tridiagonal.
 bool tridiagonal_factors(const double *B, int L, double *nl, double *rd, double *ne);
+// The resident kernels' form of one month of factors [3][n]: -e_k/d_k becomes -e_k/d_{k+1}.
+void thomas_backsubstitution_form(double *tri_month, int n, const int *col_start, int ncol);

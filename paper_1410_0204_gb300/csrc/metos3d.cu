@@ -345,7 +345,7 @@ void deal_slices(int s0, int s1, const std::vector<int> &len, int nwarps, std::v
 }  // namespace
 
 // If the L x L row-major block B is the inverse of a tridiagonal matrix M (to 1e-11 relative),
-// write the Thomas factors of M: nl[k] = -l_k, rd[k] = 1/d_k, ne[k] = -e_k, and return true.
+// write the Thomas factors of M: nl[k] = -l_k, rd[k] = 1/d_k, ne[k] = -e_k / d_k, and return true.
 bool tridiagonal_factors(const double *B, int L, double *nl, double *rd, double *ne)
 {
     std::vector<double> a(B, B + (size_t)L * L), inv((size_t)L * L, 0.0);
@@ -430,6 +430,17 @@ m3d_status m3d_validate_inputs(const m3d_grid *g, const m3d_matrices *mt, std::s
     if (!all_finite(mt->exp_val, (size_t)mt->nmonth * mt->nnz) || !all_finite(mt->imp_blk, (size_t)mt->nmonth * s_imp))
         return bad("%s", "matrices: non-finite values");
     return M3D_OK;
+}
+
+// Rewrite the third Thomas factor of every column from -e_k/d_k to -e_k/d_{k+1} (0 at the
+// bottom): the resident kernels back-substitute u_k = d_k y_k, u_k = g_k - (e_k/d_{k+1}) u_{k+1},
+// one multiply-add per layer, and scale by 1/d_k when they blend the months.
+void thomas_backsubstitution_form(double *tri_month, int n, const int *col_start, int ncol)
+{
+    const double *rd = tri_month + n;
+    double *ne = tri_month + 2 * (size_t)n;
+    for (int c = 0; c < ncol; c++)
+        for (int i = col_start[c]; i + 1 < col_start[c + 1]; i++) ne[i] = ne[i] * rd[i + 1] / rd[i];
 }
 
 // ------------------------------------------------------------------------------ C ABI
@@ -877,6 +888,8 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
                 }
             c->tri_ok = ok;
             if (ok) {
+                for (int m = 0; m < c->nmonth; m++)
+                    thomas_backsubstitution_form(tri.data() + (size_t)m * 3 * c->n, c->n, g->col_start, g->ncol);
                 const double *tri_dev = nullptr;
                 UP(upload_vec(c, &tri_dev, tri));
                 c->R.tri = tri_dev;

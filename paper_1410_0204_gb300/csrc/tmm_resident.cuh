@@ -31,7 +31,8 @@ struct ResidentParams {
     // Tridiagonal form of the implicit matrices, when every monthly block is the inverse of
     // a tridiagonal matrix M = I - dt K (vertical diffusion): per month and cell the Thomas
     // factors of M, tri[m][f][cell] with f = 0: -l_k (sub-diagonal multiplier, 0 at the top),
-    // 1: 1/d_k (inverse pivot), 2: -e_k / d_k (scaled super-diagonal, 0 at the bottom).
+    // 1: 1/d_k (inverse pivot), 2: -e_k / d_{k+1} (super-diagonal over the next pivot, 0 at the
+    // bottom; the back substitution runs in u_k = d_k y_k).
     const double *tri;
     long long tri_mstride; // 3 n
     const int *chains;     // per tile: chains (column, tracer, month) sorted by depth
@@ -227,46 +228,57 @@ __device__ __forceinline__ void implicit_dense_resident(const StepParams &P, con
     }
 }
 
-// Implicit part in tridiagonal form: yn = z0 + w (z1 - z0) with z_h = M_{m_h}^{-1} z solved by
-// Thomas' algorithm, one thread per (column, tracer, month) chain, then one combining pass.
-// Equal to (B_m0 + w (B_m1 - B_m0)) z up to rounding, because the monthly blocks are the
-// inverses B_m = M_m^{-1}.
+// Implicit part in tridiagonal form: yn = (1 - w) M0^{-1} z + w M1^{-1} z, each solve by
+// Thomas' algorithm, one thread per (column, tracer, month) chain.  The chains back-substitute
+// the unknowns u_k = d_k y_k with the factors (-l_k, 1/d_k, -e_k/d_{k+1}) -- two multiply-adds
+// per layer, the serial part of the phase -- while the threads without a chain form the blend
+// weights (1 - w)/d_k and w/d_k of every cell; one combining pass then writes
+// (1 - w)/d0_k u0_k + w/d1_k u1_k.  Equal to (B_m0 + w (B_m1 - B_m0)) z up to rounding,
+// because the monthly blocks are the inverses B_m = M_m^{-1}.
 template <int NTR>
 __device__ __forceinline__ void implicit_tri_resident(const StepParams &P, const ResidentParams &R, const Tile &T,
                                                       double w, const TileSmem &M, double *__restrict__ yn)
 {
     const int zmax = P.zmax;
     const int ch0 = __ldg(R.chain_off + blockIdx.x), ch1 = __ldg(R.chain_off + blockIdx.x + 1);
-    for (int c = ch0 + (int)threadIdx.x; c < ch1; c += blockDim.x) {
-        const int pc = __ldg(R.chains + c);
-        const int cb = pc & 0xffff, L = (pc >> 16) & 0x7f, t = (pc >> 23) & 0xf, h = (pc >> 27) & 1;
-        const double *nl = M.tl + (3 * h + 0) * zmax + cb;
-        const double *rd = M.tl + (3 * h + 1) * zmax + cb;
-        const double *ne = M.tl + (3 * h + 2) * zmax + cb;
-        const double *zc = M.z + t * zmax + cb;
-        double *x = M.yt + (h * NTR + t) * zmax + cb;
-        // forward: x_k = z_k - l_k x_{k-1}, stored as x_k / d_k
-        double xk = zc[0];
-        x[0] = xk * rd[0];
-        for (int k = 1; k < L; k++) {
-            xk = fma(nl[k], xk, zc[k]);
-            x[k] = xk * rd[k];
+    const int nthreads = (int)blockDim.x, tid = (int)threadIdx.x;
+    const int chain_threads = min(nthreads, ((ch1 - ch0 + 31) / 32) * 32);
+    double *c0 = M.ek, *c1 = M.ek + zmax;     // blend weights (the source term's scratch is free now)
+    if (tid < chain_threads) {
+        for (int c = ch0 + tid; c < ch1; c += chain_threads) {
+            const int pc = __ldg(R.chains + c);
+            const int cb = pc & 0xffff, L = (pc >> 16) & 0x7f, t = (pc >> 23) & 0xf, h = (pc >> 27) & 1;
+            const double *nl = M.tl + (3 * h + 0) * zmax + cb;
+            const double *ne = M.tl + (3 * h + 2) * zmax + cb;
+            const double *zc = M.z + t * zmax + cb;
+            double *x = M.yt + (h * NTR + t) * zmax + cb;
+            // forward: g_k = z_k - l_k g_{k-1} (l_0 = 0)
+            double g = 0.0;
+            for (int k = 0; k < L; k++) {
+                g = fma(nl[k], g, zc[k]);
+                x[k] = g;
+            }
+            // back: u_k = g_k - (e_k / d_{k+1}) u_{k+1} (nothing below the bottom layer)
+            double u = 0.0;
+            for (int k = L - 1; k >= 0; k--) {
+                u = fma(ne[k], u, x[k]);
+                x[k] = u;
+            }
         }
-        // back: y_k = x_k / d_k - (e_k / d_k) y_{k+1}
-        double yk = x[L - 1];
-        for (int k = L - 2; k >= 0; k--) {
-            yk = fma(ne[k], yk, x[k]);
-            x[k] = yk;
+    }
+    if (tid >= chain_threads || chain_threads == nthreads) {
+        const int t0 = chain_threads == nthreads ? 0 : chain_threads;
+        for (int i = tid - t0; i < T.ncell; i += nthreads - t0) {
+            c0[i] = (1.0 - w) * M.tl[1 * zmax + i];
+            c1[i] = w * M.tl[4 * zmax + i];
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < T.ncell; i += blockDim.x) {
+    for (int i = tid; i < T.ncell; i += nthreads) {
         double v[NTR];
+        const double a = c0[i], b = c1[i];
 #pragma unroll
-        for (int t = 0; t < NTR; t++) {
-            const double a = M.yt[t * zmax + i], b = M.yt[(NTR + t) * zmax + i];
-            v[t] = fma(w, b - a, a);
-        }
+        for (int t = 0; t < NTR; t++) v[t] = fma(a, M.yt[t * zmax + i], b * M.yt[(NTR + t) * zmax + i]);
         store_cell<NTR>(yn, T.cell0 + i, v);
     }
 }
