@@ -61,7 +61,7 @@ struct EnsParams {
     const int *rowptr, *colidx;           // explicit pattern (CSR)
     const double *ea, *ed;                // [nmonth][nnz]: A_m and A_{m+1} - A_m
     long long e_mstride;
-    const double *tri;                    // [nmonth][3][n] Thomas factors (-l, 1/d, -e/d)
+    const double *tri;                    // [nmonth][3][n] Thomas factors (-l_k, 1/d_k, -e_k/d_{k+1})
     long long tri_mstride;
     const int *col_start, *col_ulat;
     const double *h;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, in
             scol[p] = E.colidx[p0 + p];
         }
         // Thomas factors of both months; the blend (1 - w) T0^-1 z + w T1^-1 z is folded into the
-        // reciprocal pivots, so the two back substitutions are simply added
+        // reciprocal pivots, which scale the two back substitutions' unknowns u_k = d_k y_k
         const double *t0 = E.tri + (size_t)m0 * E.tri_mstride, *t1 = E.tri + (size_t)m1 * E.tri_mstride;
         for (int i = threadIdx.x; i < cell1 - cell0; i += blockDim.x)
             for (int f = 0; f < 3; f++) {
@@ -298,11 +298,13 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, in
                 ys[k * kLanes + lane] = g0;
                 zs[k * kLanes + lane] = g1;
             }
-            double v0 = 0.0, v1 = 0.0;
+            // back substitution in u_k = d_k y_k (third factor -e_k/d_{k+1}); the staged pivots
+            // carry the blend weights, (1 - w)/d_k and w/d_k
+            double u0 = 0.0, u1 = 0.0;
             for (int k = L - 1; k >= 0; k--) {
-                v0 = fma(ne0[k], v0, ys[k * kLanes + lane] * rd0[k]);
-                v1 = fma(ne1[k], v1, zs[k * kLanes + lane] * rd1[k]);
-                Xn[(size_t)(s0 + k) * E.wp + gl] = v0 + v1;
+                u0 = fma(ne0[k], u0, ys[k * kLanes + lane]);
+                u1 = fma(ne1[k], u1, zs[k * kLanes + lane]);
+                Xn[(size_t)(s0 + k) * E.wp + gl] = fma(rd0[k], u0, rd1[k] * u1);
             }
         }
         __syncwarp();
@@ -725,6 +727,8 @@ m3d_status metos3d_ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3
                     return bail(M3D_ERR_UNSUPPORTED);
                 }
             }
+        for (int m = 0; m < mt->nmonth; m++)
+            thomas_backsubstitution_form(tri.data() + (size_t)m * 3 * g->n, g->n, g->col_start, g->ncol);
     }
     // ---- explicit values and month differences
     const size_t nnz = (size_t)mt->nnz;
