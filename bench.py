@@ -502,6 +502,17 @@ def run_scale_1deg(args):
     u = torch.from_numpy(mi.default_params_ndop()).cuda()
     ya = torch.empty_like(y0)
     t_single = timed(lambda: ctx.year_map(y0, ya, u), reps)
+    # the adjoint (streaming sweep on this grid), checkpoint every 480 steps, wall clock
+    yb0 = torch.empty_like(y0)
+    ybar1 = torch.ones_like(y0)
+    ctx.year_adjoint(y0, u, ybar1, yb0, 480)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.year_adjoint(y0, u, ybar1, yb0, 480)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    adj_plan = {m3d.PLAN_RESIDENT: "resident", m3d.PLAN_PERSISTENT: "streaming"}.get(
+        ctx.get_option(m3d.OPT_ADJOINT_PLAN), "none")
     ctx.close()
     _, flops_single = algorithmic_per_step(prob, tridiagonal=True)
     members = mi.make_ensemble(((mi.MODEL_NPZD, 16),), seed=1410)
@@ -520,6 +531,8 @@ def run_scale_1deg(args):
             "roofline": {"bound": "alu", "achieved": flops_single * prob.nstep / t_single / 1e12,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": flops_single * prob.nstep / t_single / 1e12 / FP64_PEAK_TFLOPS},
+            "adjoint": {"seconds": t_adj, "adjoint_over_forward": t_adj / t_single, "ckpt_every": 480,
+                        "sweep": adj_plan},
             "ensemble": {"workload": "16 NPZD-DOP members (5 tracers), parameters within +-50% of the defaults",
                          "member_years_per_s": len(members) / t_ens, "seconds_per_ensemble_year": t_ens,
                          "tiling": {"cols_per_block": cpb, "warps_per_block": nw, "autotune_ms_per_step": ms},

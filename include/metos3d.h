@@ -162,8 +162,8 @@ m3d_status metos3d_year_tangent(m3d_ctx *ctx, const double *y0, const double *v,
  * reverse sweep: about four year maps of work and ckpt_every + 1 states of memory,
  * allocated for the call.  ckpt_every >= nstep keeps the whole trajectory (nstep + 1
  * states; 2.4 GB for 52,749 cells and two tracers) and recomputes nothing, about three year
- * maps of work.  PO4-DOP with one internal step and the resident plan only
- * (M3D_ERR_UNSUPPORTED otherwise).  Synchronous.
+ * maps of work.  PO4-DOP with one internal step and a structurally symmetric explicit pattern
+ * only (M3D_ERR_UNSUPPORTED otherwise); see M3D_OPT_ADJOINT_PLAN.  Synchronous.
  */
 m3d_status metos3d_year_adjoint(m3d_ctx *ctx, const double *y0, const double *u, const double *ybar1,
                                 double *ybar0, double *ubar_host, int ckpt_every);
@@ -242,6 +242,11 @@ m3d_status metos3d_sync(m3d_ctx *ctx);
  *   M3D_OPT_TEST_WITHHOLD_TILE: for tests of the timeout path only: the given tile never
  *       announces its progress, so its neighbours' waits run out (-1: off, the default).
  *   M3D_OPT_NTILES (read only): number of tiles (CTAs) of a step.
+ *   M3D_OPT_ADJOINT_PLAN: how metos3d_year_adjoint runs: M3D_PLAN_RESIDENT (default when it
+ *       fits: the tiles' months of transposed operators in shared memory), or
+ *       M3D_PLAN_PERSISTENT (default otherwise, e.g. on a 1-degree grid): a streaming sweep that
+ *       reads the transposed operators from HBM every step and applies dense implicit blocks,
+ *       its forward segments recomputed one step launch at a time; -1 when neither fits.
  *   M3D_OPT_IMPLICIT_FORM (resident plan): M3D_IMPLICIT_TRIDIAGONAL (default when every
  *       monthly implicit block is, to 1e-11 relative, the inverse of a tridiagonal matrix,
  *       as a vertical diffusion (I - dt K)^{-1} is): the interpolated implicit part is
@@ -255,7 +260,8 @@ enum {
     M3D_OPT_WAIT_TIMEOUT_NS = 2,
     M3D_OPT_TEST_WITHHOLD_TILE = 3,
     M3D_OPT_NTILES = 4,
-    M3D_OPT_IMPLICIT_FORM = 5
+    M3D_OPT_IMPLICIT_FORM = 5,
+    M3D_OPT_ADJOINT_PLAN = 6
 };
 enum { M3D_IMPLICIT_DENSE = 0, M3D_IMPLICIT_TRIDIAGONAL = 1 };
 enum { M3D_PLAN_PERSISTENT = 0, M3D_PLAN_GRAPH = 1, M3D_PLAN_RESIDENT = 2 };

@@ -28,6 +28,7 @@ OPT_WAIT_TIMEOUT_NS = 2
 OPT_TEST_WITHHOLD_TILE = 3
 OPT_NTILES = 4
 OPT_IMPLICIT_FORM = 5
+OPT_ADJOINT_PLAN = 6
 IMPLICIT_DENSE = 0
 IMPLICIT_TRIDIAGONAL = 1
 PLAN_PERSISTENT = 0

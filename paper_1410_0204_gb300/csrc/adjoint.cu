@@ -25,6 +25,17 @@ __global__ void __launch_bounds__(m3d::kThreads, 1) k_year_adjoint(StepParams PT
     m3d::year_adjoint_resident<2, TRI>(PT, RT, S, A, traj, stride, ybar_in, out, zb0, zb1, j0, nsteps);
 }
 
+// The same sweep reading the operators from global memory (grids whose tiles' months do not
+// fit in shared memory).
+__global__ void __launch_bounds__(m3d::kThreads, 1) k_year_adjoint_stream(StepParams PT, m3d::ResidentParams RT,
+                                                                       m3d::SyncParams S, m3d::AdjointParams A,
+                                                                       const double *traj, long long stride,
+                                                                       const double *ybar_in, double *out,
+                                                                       double *zb0, double *zb1, int j0, int nsteps)
+{
+    m3d::year_adjoint_resident<2, false, true>(PT, RT, S, A, traj, stride, ybar_in, out, zb0, zb1, j0, nsteps);
+}
+
 // d mfrac / d b on aphotic cells (the parameter gradient of the Martin profile).
 __global__ void k_martin_b(int n, const int *cell_kl, const double *h, const double *u, double *mfrac_b)
 {
@@ -68,7 +79,8 @@ void free_owned(m3d_ctx *c, void *p)
 m3d_status setup_adjoint(m3d_ctx *c, const AdjointSetup &in)
 {
     c->adj_ok = 0;
-    if (c->model != M3D_MODEL_NDOP || c->nsub != 1 || !c->resident_ok) return M3D_OK;
+    c->adj_stream_ok = 0;
+    if (c->model != M3D_MODEL_NDOP || c->nsub != 1) return M3D_OK;
     const m3d_grid *g = in.g;
     const m3d_matrices *mt = in.mt;
     const int n = g->n;
@@ -195,11 +207,22 @@ m3d_status setup_adjoint(m3d_ctx *c, const AdjointSetup &in)
               (long long)occ * prop.multiProcessorCount >= c->ntiles))
             c->adj_tri_ok = 0;
     }
+    // streaming sweep: operators from global memory; in shared memory the tile's cotangent
+    // (2 components), the export scratch (2) and the per-column scratch (1)
+    {
+        const void *ks = (const void *)k_year_adjoint_stream;
+        c->adj_smem_stream = sizeof(double) * 5 * (size_t)c->zmax;
+        occ = 0;
+        if (c->adj_smem_stream <= (size_t)prop.sharedMemPerBlockOptin &&
+            cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->adj_smem_stream) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks, m3d::kThreads, c->adj_smem_stream) == cudaSuccess)
+            c->adj_stream_ok = (long long)occ * prop.multiProcessorCount >= c->ntiles;
+    }
     cudaGetLastError();
     c->PT = PT;
     c->RTadj = RT;
     c->A = A;
-    c->adj_ok = c->adj_dense_ok || c->adj_tri_ok;
+    c->adj_ok = (c->adj_dense_ok || c->adj_tri_ok) && c->resident_ok;
     return M3D_OK;
 }
 
@@ -220,6 +243,39 @@ m3d_status forward_segment(m3d_ctx *c, bool tri, double *traj, long long len, in
     CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)(tri ? c->rk.year_tri : c->rk.year), dim3(c->ntiles),
                                                 dim3(m3d::kThreads), args,
                                                 tri ? c->resident_tri_smem : c->resident_smem, c->stream));
+    return M3D_OK;
+}
+
+// The forward segment without the resident kernel: one step launch per step in the caller's
+// layout, each state interleaved into the trajectory (traj[0] holds the segment's start).
+m3d_status forward_segment_stream(m3d_ctx *c, double *traj, long long len, int j0, int ns)
+{
+    const int nb = (c->n + 255) / 256;
+    double *ya = c->ybuf[0], *yb = c->ybuf[1];
+    for (int s = 0; s < ns; s++) {
+        c->rk.from_interleaved<<<nb, 256, 0, c->stream>>>(c->n, traj + (size_t)s * len, ya);
+        CUDA_OR_FAIL(c, cudaGetLastError());
+        m3d_status st = m3d_step_device(c, (j0 + s) % c->nstep, ya, yb);
+        if (st != M3D_OK) return st;
+        c->rk.to_interleaved<<<nb, 256, 0, c->stream>>>(c->n, yb, traj + (size_t)(s + 1) * len);
+        CUDA_OR_FAIL(c, cudaGetLastError());
+    }
+    return M3D_OK;
+}
+
+m3d_status adjoint_segment_stream(m3d_ctx *c, const double *traj, long long len, const double *ybar_in, double *out,
+                                  double *zb0, double *zb1, int j0, int ns)
+{
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.flags, 0, sizeof(int) * c->ntiles, c->stream));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.status, 0, sizeof(int) * 4, c->stream));
+    StepParams PT = c->PT;
+    m3d::ResidentParams RT = c->RTadj;
+    m3d::SyncParams S = c->S;
+    m3d::AdjointParams A = c->A;
+    long long stride = len;
+    void *args[] = {&PT, &RT, &S, &A, &traj, &stride, &ybar_in, &out, &zb0, &zb1, &j0, &ns};
+    CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)k_year_adjoint_stream, dim3(c->ntiles),
+                                                dim3(m3d::kThreads), args, c->adj_smem_stream, c->stream));
     return M3D_OK;
 }
 
@@ -247,14 +303,16 @@ extern "C" m3d_status metos3d_year_adjoint(m3d_ctx *c, const double *y0, const d
 {
     if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_adjoint: null context");
     if (!y0 || !u || !ybar1 || !ybar0) return fail(c, M3D_ERR_ARG, "metos3d_year_adjoint: null pointer");
-    if (!c->adj_ok)
+    const bool stream = c->adj_stream_ok && (!c->adj_ok || c->adj_force_stream);
+    if (!c->adj_ok && !stream)
         return fail(c, M3D_ERR_UNSUPPORTED,
                     "metos3d_year_adjoint: needs the PO4-DOP model with one internal step, a structurally "
-                    "symmetric explicit pattern and the resident plan");
+                    "symmetric explicit pattern, and a tile that fits on the GPU");
     const int K = ckpt_every > 0 ? std::min(ckpt_every, c->nstep) : std::min(240, c->nstep);
     const int nseg = (c->nstep + K - 1) / K;
-    const bool tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && c->adj_tri_ok && c->tri_resident_ok;
-    if (!tri && !c->adj_dense_ok) return fail(c, M3D_ERR_UNSUPPORTED, "metos3d_year_adjoint: the dense form does not fit");
+    const bool tri = !stream && c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && c->adj_tri_ok && c->tri_resident_ok;
+    if (!stream && !tri && !c->adj_dense_ok)
+        return fail(c, M3D_ERR_UNSUPPORTED, "metos3d_year_adjoint: the dense form does not fit");
     const long long len = (long long)c->ntr * c->n;
     const size_t vb = sizeof(double) * (size_t)len;
     void *p = nullptr;
@@ -280,7 +338,7 @@ extern "C" m3d_status metos3d_year_adjoint(m3d_ctx *c, const double *y0, const d
     for (int seg = 0; seg < nseg; seg++) {
         const int j0 = seg * K, ns = std::min(K, c->nstep - j0);
         CUDA_OR_FAIL(c, cudaMemcpyAsync(traj, chk + (size_t)seg * len, vb, cudaMemcpyDeviceToDevice, c->stream));
-        TRY(forward_segment(c, tri, traj, len, j0, ns));
+        TRY(stream ? forward_segment_stream(c, traj, len, j0, ns) : forward_segment(c, tri, traj, len, j0, ns));
         CUDA_OR_FAIL(c, cudaMemcpyAsync(chk + (size_t)(seg + 1) * len, traj + (size_t)ns * len, vb,
                                         cudaMemcpyDeviceToDevice, c->stream));
     }
@@ -294,9 +352,10 @@ extern "C" m3d_status metos3d_year_adjoint(m3d_ctx *c, const double *y0, const d
         const int j0 = seg * K, ns = std::min(K, c->nstep - j0);
         if (seg != nseg - 1) {
             CUDA_OR_FAIL(c, cudaMemcpyAsync(traj, chk + (size_t)seg * len, vb, cudaMemcpyDeviceToDevice, c->stream));
-            TRY(forward_segment(c, tri, traj, len, j0, ns));
+            TRY(stream ? forward_segment_stream(c, traj, len, j0, ns) : forward_segment(c, tri, traj, len, j0, ns));
         }
-        TRY(adjoint_segment(c, tri, traj, len, ya, ybn, zb, zb + len, j0, ns));
+        TRY(stream ? adjoint_segment_stream(c, traj, len, ya, ybn, zb, zb + len, j0, ns)
+                   : adjoint_segment(c, tri, traj, len, ya, ybn, zb, zb + len, j0, ns));
         CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
         CUDA_OR_FAIL(c, cudaMemcpyAsync(part.data(), c->A.ubar_part, sizeof(double) * part.size(),
                                         cudaMemcpyDeviceToHost, c->stream));
@@ -310,7 +369,11 @@ extern "C" m3d_status metos3d_year_adjoint(m3d_ctx *c, const double *y0, const d
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     if (ubar_host)
         for (int k = 0; k < 7; k++) ubar_host[k] = ub[k];
-    c->last_launches = 3 + 2 * nseg + (nseg - 1);
+    // prologue, Martin gradient and two layout passes; per segment a forward (one launch, or
+    // three per step when streaming) and a reverse launch; the last segment is not recomputed
+    const long long fwd = stream ? 3LL * c->nstep : nseg;
+    const long long refwd = stream ? 3LL * (c->nstep - std::min(K, c->nstep - (nseg - 1) * K)) : nseg - 1;
+    c->last_launches = 4 + fwd + refwd + nseg;
     cleanup();
     return M3D_OK;
 #undef TRY

@@ -58,6 +58,9 @@ struct m3d_ctx {
     size_t resident_smem = 0, resident_tri_smem = 0;
     // adjoint: transposed operators (same layouts), its tables and kernels' shared memory
     int adj_ok = 0, adj_tri_ok = 0, adj_dense_ok = 0;
+    int adj_stream_ok = 0;              // the streaming reverse sweep fits (operators read from HBM)
+    int adj_force_stream = 0;           // M3D_OPT_ADJOINT_PLAN = M3D_PLAN_PERSISTENT
+    size_t adj_smem_stream = 0;
     StepParams PT{};
     m3d::ResidentParams RTadj{};
     m3d::AdjointParams A{};
@@ -98,6 +101,9 @@ m3d_status m3d_year_device(m3d_ctx *c, const double *y0, double *y1);
 m3d_status m3d_set_params(m3d_ctx *c, const double *u, cudaMemcpyKind kind);
 // phi(y0) and phi'(y0) v with the parameters already in c->u_dev.
 m3d_status m3d_year_tangent_device(m3d_ctx *c, const double *y0, const double *v, double *phi, double *jv);
+// One TMM step j in the caller's layout (the step kernel; parameters already in c->u_dev and
+// the per-call tables made).
+m3d_status m3d_step_device(m3d_ctx *c, int j, const double *y, double *yn);
 // The per-call model tables (attenuation, Martin profile, model scalars) from c->u_dev.
 m3d_status m3d_prologue(m3d_ctx *c);
 // Device allocation owned by the context (freed by metos3d_free).

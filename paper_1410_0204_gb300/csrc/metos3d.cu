@@ -1263,6 +1263,14 @@ m3d_status metos3d_set_option(m3d_ctx *c, int option, long long value)
         if (value < -1 || value >= c->ntiles) return fail(c, M3D_ERR_ARG, "tile out of range");
         c->S.withhold_tile = (int)value;
         return M3D_OK;
+    case M3D_OPT_ADJOINT_PLAN:
+        if (value == M3D_PLAN_PERSISTENT && !c->adj_stream_ok)
+            return fail(c, M3D_ERR_UNSUPPORTED, "the streaming adjoint sweep does not fit on this GPU");
+        if (value == M3D_PLAN_RESIDENT && !c->adj_ok)
+            return fail(c, M3D_ERR_UNSUPPORTED, "the resident adjoint sweep does not fit on this GPU");
+        if (value != M3D_PLAN_PERSISTENT && value != M3D_PLAN_RESIDENT) return fail(c, M3D_ERR_ARG, "bad adjoint plan");
+        c->adj_force_stream = value == M3D_PLAN_PERSISTENT;
+        return M3D_OK;
     default:
         return fail(c, M3D_ERR_ARG, "unknown option %d", option);
     }
@@ -1277,6 +1285,9 @@ long long metos3d_get_option(const m3d_ctx *c, int option)
     case M3D_OPT_TEST_WITHHOLD_TILE: return c->S.withhold_tile;
     case M3D_OPT_NTILES: return c->ntiles;
     case M3D_OPT_IMPLICIT_FORM: return c->implicit_form;
+    case M3D_OPT_ADJOINT_PLAN:
+        if (c->adj_stream_ok && (!c->adj_ok || c->adj_force_stream)) return M3D_PLAN_PERSISTENT;
+        return c->adj_ok ? M3D_PLAN_RESIDENT : -1;
     default: return -1;
     }
 }
@@ -1393,3 +1404,5 @@ extern "C" m3d_status metos3d_year_tangent(m3d_ctx *c, const double *y0, const d
 }
 
 m3d_status m3d_prologue(m3d_ctx *c) { return launch_prologue(c, c->u_dev); }
+
+m3d_status m3d_step_device(m3d_ctx *c, int j, const double *y, double *yn) { return launch_step(c, j, y, yn); }

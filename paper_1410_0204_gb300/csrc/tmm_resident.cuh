@@ -468,7 +468,7 @@ __device__ __forceinline__ void ndop_source_adjoint_tile(const StepParams &P, co
 // states y_{j0} .. y_{j0+nsteps-1} (stride apart); ybar_in: cotangent of y_{j0+nsteps}; out:
 // cotangent of y_{j0}.  zb0, zb1: the interleaved ping-pong of zbar.  PT and RTp carry the
 // transposed operators (same layouts as the forward ones).
-template <int NTR, bool TRI>
+template <int NTR, bool TRI, bool STREAM = false>
 __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, const ResidentParams &RTp,
                                                       const SyncParams &S, const AdjointParams &A,
                                                       const double *traj, long long stride,
@@ -481,18 +481,51 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
     const int tile = blockIdx.x;
     const Tile T = PT.tiles[tile];
     const ResidentTile RT = RTp.rt[tile];
-    const ResidentLayout Ly = resident_layout(NTR, RTp.sp_max, RTp.bk_max, PT.zmax, TRI);
-    const TileSmem M = tile_smem(dsm, Ly, PT, T);
     const int zmax = PT.zmax;
+    // STREAM: the operators are read from global memory where they lie (the month's slices of
+    // the tile), only the tile's cotangent and the source term's scratch sit in shared memory,
+    // and the implicit part uses the dense form (TRI must be false)
+    static_assert(!(STREAM && TRI), "the streaming sweep applies dense implicit blocks");
+    TileSmem M;
+    if (STREAM) {
+        double *base = reinterpret_cast<double *>(dsm);
+        M.z = base;
+        M.ek = base + NTR * zmax;
+        M.aux = M.ek + 2 * zmax;
+        M.dq = M.tl = M.yt = nullptr;
+        M.sa = M.sd = M.sb = M.sbd = nullptr;
+        M.si = const_cast<int *>(PT.sp_col) + RT.sp_base;
+        M.sp_first = T.sp0 < T.sp1 ? __ldg(PT.sp_off + T.sp0) : 0;
+        M.bk_first = T.bk0 < T.bk1 ? __ldg(PT.bk_off + T.bk0) : 0;
+    } else {
+        const ResidentLayout Ly = resident_layout(NTR, RTp.sp_max, RTp.bk_max, PT.zmax, TRI);
+        M = tile_smem(dsm, Ly, PT, T);
+        copy_to_shared_int(M.si, PT.sp_col + RT.sp_base, RT.sp_n);
+    }
     double ub[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-
-    copy_to_shared_int(M.si, PT.sp_col + RT.sp_base, RT.sp_n);
+    // the month's operators: staged in shared memory, or pointed at where they lie
+    auto explicit_month = [&](int m) {
+        if (STREAM) {
+            M.sa = const_cast<double *>(PT.sp_a) + (long long)m * PT.sp_mstride + RT.sp_base;
+            M.sd = const_cast<double *>(PT.sp_d) + (long long)m * PT.sp_mstride + RT.sp_base;
+        } else {
+            load_explicit_month(PT, RT, PT.sp_a, PT.sp_d, m, M);
+        }
+    };
+    auto implicit_month = [&](int m) {
+        if (STREAM) {
+            M.sb = const_cast<double *>(PT.bk_b) + (long long)m * PT.bk_mstride + RT.bk_base;
+            M.sbd = const_cast<double *>(PT.bk_d) + (long long)m * PT.bk_mstride + RT.bk_base;
+        } else {
+            load_implicit_month<TRI>(PT, RTp, RT, T, RTp.tri, PT.bk_b, PT.bk_d, m, M);
+        }
+    };
     int exp_month = -1, imp_month = -1;
     // zbar_{last} = B_last^T ybar_in on the tile's own cells
     {
         const int j = (j0 + nsteps - 1) % PT.nstep;
         const int m = __ldg(PT.m0tab + j);
-        load_implicit_month<TRI>(PT, RTp, RT, T, RTp.tri, PT.bk_b, PT.bk_d, m, M);
+        implicit_month(m);
         imp_month = m;
         for (int i = threadIdx.x; i < T.ncell; i += blockDim.x)
             for (int t = 0; t < NTR; t++) M.z[t * zmax + i] = __ldcg(ybar_in + (size_t)(T.cell0 + i) * NTR + t);
@@ -509,7 +542,7 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
         const double *y = traj + (long long)(nsteps - 1 - s) * stride;
         const int m = __ldg(PT.m0tab + j);
         if (m != exp_month) {
-            load_explicit_month(PT, RT, PT.sp_a, PT.sp_d, m, M);
+            explicit_month(m);
             exp_month = m;
         }
         if (threadIdx.x < 32) {
@@ -526,7 +559,7 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
             const int jm = (j + PT.nstep - 1) % PT.nstep;
             const int mm = __ldg(PT.m0tab + jm);
             if (mm != imp_month) {
-                load_implicit_month<TRI>(PT, RTp, RT, T, RTp.tri, PT.bk_b, PT.bk_d, mm, M);
+                implicit_month(mm);
                 imp_month = mm;
                 __syncthreads();
             }

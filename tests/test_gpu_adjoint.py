@@ -193,3 +193,33 @@ def test_misfit_gradient_at_the_periodic_solution_full_grid(m3d):
         fd = (J(up) - J(um)) / (2 * e)
         assert abs(grad[k] - fd) <= 1e-5 * abs(fd) + 1e-9 * J0, (k, grad[k], fd)
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["ndop_64x32x8", "ndop_128x64x15"])
+def test_streaming_adjoint_matches_oracle(m3d, name):
+    # the sweep that reads its operators from HBM (what grids too large for the resident
+    # kernel use), forced on grids where the resident sweep also runs
+    import os
+    oracle.set_threads(min(16, os.cpu_count() or 1))
+    p = mi.make_problem(name)
+    P = oracle.Problem(p)
+    u = mi.default_params_ndop()
+    y0 = mi.random_state(p, seed=31)
+    wbar = mi.random_state(p, seed=32) - 1.0
+    ctx = m3d.Context.from_problem(p)
+    assert ctx.get_option(m3d.OPT_ADJOINT_PLAN) == m3d.PLAN_RESIDENT
+    ctx.set_option(m3d.OPT_ADJOINT_PLAN, m3d.PLAN_PERSISTENT)
+    assert ctx.get_option(m3d.OPT_ADJOINT_PLAN) == m3d.PLAN_PERSISTENT
+    ybar0 = torch.empty((2, p.n), dtype=torch.float64, device="cuda")
+    ubar = ctx.year_adjoint(cuda(y0), cuda(u), cuda(wbar), ybar0, 240)
+    want_y, want_u = oracle.year_adjoint(P, y0, u, wbar)
+    oracle.set_threads(1)
+    assert rel(ybar0.cpu().numpy(), want_y) < 1e-10
+    assert np.abs(ubar - want_u).max() <= 1e-9 * np.abs(want_u).max()
+    # and the resident sweep agrees with it to rounding (dense against tridiagonal implicit form)
+    ctx.set_option(m3d.OPT_ADJOINT_PLAN, m3d.PLAN_RESIDENT)
+    ybar_r = torch.empty_like(ybar0)
+    ubar_r = ctx.year_adjoint(cuda(y0), cuda(u), cuda(wbar), ybar_r, 240)
+    assert rel(ybar0.cpu().numpy(), ybar_r.cpu().numpy()) < 1e-11
+    assert np.abs(ubar - ubar_r).max() <= 1e-10 * np.abs(ubar_r).max()
+    ctx.close()

@@ -98,3 +98,35 @@ def test_npzd_ensemble_year_conserves_each_member(m3d, grid):
         m1 = float((Y1[5 * m:5 * m + 5].sum(axis=0) * p.vol).sum())
         assert abs(m1 - m0) <= 1e-12 * m0, m
     ens.close()
+
+
+def test_adjoint_gradient_matches_central_differences(m3d, grid):
+    # the 1-degree tiles do not hold their operators in shared memory, so the adjoint runs the
+    # streaming sweep; checkpoint every 480 steps.  J(u) = 1/2 |M (phi(y0; u) - obs)|^2 on a
+    # random 10 % of the cells, against central differences with h = 1e-6 relative
+    p, _ = grid
+    r = mi.rng(1410, "observations")
+    ctx = m3d.Context.from_problem(p, model=m3d.MODEL_NDOP, ntracer=2, nparam=7)
+    assert ctx.get_option(m3d.OPT_ADJOINT_PLAN) == m3d.PLAN_PERSISTENT
+    u0 = mi.default_params_ndop()
+    y0 = torch.from_numpy(mi.random_state(p, seed=41)).cuda()
+    mask = torch.from_numpy((r.random((2, p.n)) < 0.1).astype(np.float64)).cuda()
+    obs = y0 * torch.from_numpy(1.0 + 0.05 * r.standard_normal((2, p.n))).cuda()
+
+    def J(uu):
+        y1 = torch.empty_like(y0)
+        ctx.year_map(y0, y1, torch.from_numpy(uu).cuda())
+        return 0.5 * float(torch.sum((mask * (y1 - obs)) ** 2))
+
+    y1 = torch.empty_like(y0)
+    ctx.year_map(y0, y1, torch.from_numpy(u0).cuda())
+    grad = ctx.year_adjoint(y0, torch.from_numpy(u0).cuda(), mask * mask * (y1 - obs), torch.empty_like(y0), 480)
+    J0 = J(u0)
+    for k in range(7):
+        e = 1e-6 * u0[k]
+        up, um = u0.copy(), u0.copy()
+        up[k] += e
+        um[k] -= e
+        fd = (J(up) - J(um)) / (2 * e)
+        assert abs(grad[k] - fd) <= 1e-5 * abs(fd) + 1e-9 * J0, (k, grad[k], fd)
+    ctx.close()
