@@ -401,6 +401,20 @@ def run_ours(args):
                                  "model_year_equivalents": rep["year_maps"] + rep["tangent_maps"],
                                  "krylov_per_newton_step": rep.get("krylov"), "residuals": rep.get("residuals"),
                                  "line_search_steps": rep.get("lambdas")}
+        # spin-up to the Newton tolerance (the paper's comparison of Section 7), capped
+        spinup = {}
+        if args.spinup_years > 0:
+            yS = torch.from_numpy(y0_h).cuda()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = ctx.spinup(yS, u, args.spinup_years, tol=1e-8)
+            dt_s = time.perf_counter() - t0
+            first_below = {}
+            for thr in (1e-2, 1e-4, 1e-6, 1e-8):
+                hit = np.nonzero(res < thr)[0]
+                first_below["%g" % thr] = int(hit[0]) + 1 if hit.size else None
+            spinup = {"seconds": dt_s, "years": int(res.size), "final_residual": float(res[-1]),
+                      "reached_1e-8": bool(res[-1] < 1e-8), "years_to_reach": first_below, "cap": args.spinup_years}
         ctx.close()
 
     if rank != 0:
@@ -444,6 +458,8 @@ def run_ours(args):
         "adjoint": costs,
         "ensemble": ensemble,
     }
+    if spinup:
+        line["spinup"] = spinup
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
     print(json.dumps(line), flush=True)
@@ -569,6 +585,8 @@ def main():
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-Krylov solve timing")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/tangent cost timing")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched ensemble timing")
+    ap.add_argument("--spinup-years", type=int, default=0,
+                    help="also time a spin-up of up to this many years to ||phi(y) - y|| < 1e-8 (e.g. 3000)")
     ap.add_argument("--newton-tangent", action="store_true",
                     help="also time Newton-Krylov with tangent Jacobian-vector products")
     ap.add_argument("--profile-steps", type=int, default=0,
