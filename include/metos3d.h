@@ -43,8 +43,12 @@ typedef enum {
 } m3d_status;
 
 /*
- * Biogeochemical models (Section 2.2).  A single context (metos3d_init) runs NONE and NDOP;
- * ensembles (metos3d_ensemble_init) run N, NDOP, PHY and NPZD members side by side.
+ * Biogeochemical models (Section 2.2).  A single context (metos3d_init) runs every model: NONE
+ * and NDOP with the tiled year kernels (and, for NDOP, the tangent and adjoint), N, PHY and
+ * NPZD through a one-member ensemble (year map, steps, spin-up, Newton-Krylov with
+ * finite-difference products, diagnostics).  Ensembles (metos3d_ensemble_init) run N, NDOP,
+ * PHY and NPZD members side by side.  The parameters of each model are listed with the
+ * ensemble calls below.
  */
 enum {
     M3D_MODEL_NONE = 0,         /* q = 0: pure transport, any number of tracers */
@@ -96,8 +100,8 @@ typedef struct {
 /* Model and time discretisation. */
 typedef struct {
     int model_id;               /* M3D_MODEL_* */
-    int ntracer;                /* 2 for M3D_MODEL_NDOP; 1..M3D_MAX_TRACERS for M3D_MODEL_NONE */
-    int nparam;                 /* 7 for M3D_MODEL_NDOP (see metos3d_bgc) */
+    int ntracer;                /* the model's count (N 1, NDOP 2, PHY 3, NPZD 5); 1..M3D_MAX_TRACERS for NONE */
+    int nparam;                 /* the model's count (N 5, NDOP 7 -- see metos3d_bgc --, PHY 11, NPZD 13) */
     int nsub;                   /* internal model steps per ocean step, >= 1 (the paper's runs use 8) */
     int nstep;                  /* ocean steps per model year (2880 in the paper) */
 } m3d_model;

@@ -82,6 +82,10 @@ struct m3d_ctx {
     int year_result_buf = 0;
     long long last_launches = 0;
     std::string err;
+    // models only ensembles run (N, PO4-DOP-PHY, NPZD-DOP): a one-member ensemble does the steps
+    m3d_ensemble *ens = nullptr;
+    std::vector<double> ens_u;          // the parameters last given to it
+    int ens_u_valid = 0;
 };
 
 // Record a failure on c (or for metos3d_init when c is null) and return s.

@@ -342,6 +342,71 @@ void deal_slices(int s0, int s1, const std::vector<int> &len, int nwarps, std::v
     woff.push_back(base);
 }
 
+// Tracer and parameter counts of the models a single context runs through a one-member
+// ensemble (0 / -1 for the others).
+int ensemble_backed_ntracer(int model)
+{
+    return model == M3D_MODEL_N ? 1 : model == M3D_MODEL_PHY ? 3 : model == M3D_MODEL_NPZD ? 5 : 0;
+}
+int ensemble_backed_nparam(int model)
+{
+    return model == M3D_MODEL_N ? 5 : model == M3D_MODEL_PHY ? 11 : model == M3D_MODEL_NPZD ? 13 : -1;
+}
+
+// A context for N, PO4-DOP-PHY or NPZD-DOP: the steps run in a one-member ensemble; the
+// context keeps what its own calls need (parameters, volumes, a staging pair of states, the
+// reductions).
+m3d_status init_ensemble_backed(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt, const m3d_model *md,
+                                void *stream)
+{
+    m3d_ctx *c = new (std::nothrow) m3d_ctx();
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "out of host memory");
+    cudaGetLastError();
+    auto bail = [&](m3d_status s) {
+        g_init_error = c->err;
+        if (c->ens) metos3d_ensemble_free(c->ens);
+        release(c);
+        delete c;
+        cudaGetLastError();
+        return s;
+    };
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)stream;
+    c->n = g->n;
+    c->ncol = g->ncol;
+    c->ntr = md->ntracer;
+    c->nparam = md->nparam;
+    c->nsub = md->nsub;
+    c->nstep = md->nstep;
+    c->nmonth = mt->nmonth;
+    c->model = md->model_id;
+    c->plan = M3D_PLAN_GRAPH;            // one launch per step, the year one CUDA graph
+    std::vector<double> u0((size_t)md->nparam, 0.0);
+    m3d_member mem{md->model_id, md->nparam, u0.data()};
+    m3d_status st = metos3d_ensemble_init(&c->ens, g, mt, 1, &mem, md->nsub, md->nstep, stream);
+    if (st != M3D_OK) {
+        c->ens = nullptr;
+        fail(c, st, "%s", metos3d_ensemble_last_error(nullptr));
+        return bail(st);
+    }
+    cudaError_t e;
+#define UPE(...) do { e = (__VA_ARGS__); if (e != cudaSuccess) { fail(c, M3D_ERR_CUDA, "device set-up (%s): %s", #__VA_ARGS__, cudaGetErrorString(e)); return bail(M3D_ERR_CUDA); } } while (0)
+    const size_t len = (size_t)c->ntr * c->n;
+    UPE(upload(c, &c->u_dev, (const double *)nullptr, (size_t)std::max(1, c->nparam)));
+    UPE(upload(c, &c->vol, g->vol, (size_t)c->n));
+    UPE(upload(c, &c->ybuf[0], (const double *)nullptr, 2 * len));
+    c->ybuf[1] = c->ybuf[0] + len;
+    c->ybuf_cap = (long long)len;
+    UPE(upload(c, &c->red_part, (const double *)nullptr, (size_t)kRedBlocks));
+    UPE(upload(c, &c->red_out, (const double *)nullptr, (size_t)1));
+    UPE(cudaMallocHost((void **)&c->red_host, sizeof(double)));
+    UPE(cudaMallocHost((void **)&c->status_host, 4 * sizeof(int)));
+#undef UPE
+    for (int i = 0; i < 4; i++) c->status_host[i] = 0;
+    *out = c;
+    return M3D_OK;
+}
+
 }  // namespace
 
 // If the L x L row-major block B is the inverse of a tridiagonal matrix M (to 1e-11 relative),
@@ -472,6 +537,7 @@ void metos3d_free(m3d_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     release(ctx);
+    if (ctx->ens) metos3d_ensemble_free(ctx->ens);
     cudaSetDevice(prev);
     delete ctx;
 }
@@ -480,6 +546,7 @@ m3d_status metos3d_set_stream(m3d_ctx *ctx, void *stream)
 {
     if (!ctx) return fail(nullptr, M3D_ERR_ARG, "metos3d_set_stream: null context");
     ctx->stream = (cudaStream_t)stream;
+    if (ctx->ens) metos3d_ensemble_set_stream(ctx->ens, stream);
     return M3D_OK;
 }
 
@@ -502,9 +569,13 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     } else if (md->model_id == M3D_MODEL_NONE) {
         if (md->ntracer < 1 || md->ntracer > M3D_MAX_TRACERS || md->nparam < 0)
             return fail(nullptr, M3D_ERR_ARG, "model: 1..%d tracers for the transport-only model", M3D_MAX_TRACERS);
+    } else if (ensemble_backed_ntracer(md->model_id) > 0) {
+        if (md->ntracer != ensemble_backed_ntracer(md->model_id) || md->nparam != ensemble_backed_nparam(md->model_id))
+            return fail(nullptr, M3D_ERR_ARG, "model: model %d needs %d tracers and %d parameters", md->model_id,
+                        ensemble_backed_ntracer(md->model_id), ensemble_backed_nparam(md->model_id));
+        return init_ensemble_backed(out, g, mt, md, stream);
     } else {
-        return fail(nullptr, M3D_ERR_UNSUPPORTED, "model: model_id %d is not available for a single context "
-                    "(ensembles run it)", md->model_id);
+        return fail(nullptr, M3D_ERR_UNSUPPORTED, "model: unknown model_id %d", md->model_id);
     }
 
     m3d_ctx *c = new (std::nothrow) m3d_ctx();
@@ -993,6 +1064,32 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
 
 namespace {
 
+// An ensemble-backed context: give its member the parameters now in c->u_dev (synchronous;
+// re-tabulated only when they changed).
+m3d_status ens_sync_params(m3d_ctx *c)
+{
+    std::vector<double> u((size_t)c->nparam);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(u.data(), c->u_dev, sizeof(double) * u.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    if (c->ens_u_valid && u == c->ens_u) return M3D_OK;
+    m3d_status st = metos3d_ensemble_set_params(c->ens, 0, u.data());
+    if (st != M3D_OK) return fail(c, st, "%s", metos3d_ensemble_last_error(c->ens));
+    c->ens_u = u;
+    c->ens_u_valid = 1;
+    return M3D_OK;
+}
+
+// The year (or nsteps steps from j0) of an ensemble-backed context, device arrays.
+m3d_status ens_run(m3d_ctx *c, int j0, int nsteps, const double *y0, double *y1)
+{
+    m3d_status st = ens_sync_params(c);
+    if (st != M3D_OK) return st;
+    st = nsteps < 0 ? metos3d_ensemble_year_map(c->ens, y0, y1) : metos3d_ensemble_steps(c->ens, j0, nsteps, y0, y1);
+    if (st != M3D_OK) return fail(c, st, "%s", metos3d_ensemble_last_error(c->ens));
+    c->last_launches = metos3d_ensemble_last_launch_count(c->ens);
+    return M3D_OK;
+}
+
 m3d_status launch_prologue(m3d_ctx *c, const double *u)
 {
     if (c->model != M3D_MODEL_NDOP) return M3D_OK;
@@ -1184,6 +1281,7 @@ m3d_status metos3d_step(m3d_ctx *c, int j, const double *y_in, double *y_out, co
     if (a < b + len && b < a + len) return fail(c, M3D_ERR_ARG, "metos3d_step: y_in and y_out overlap");
     if (c->nparam > 0)
         CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_dev, u, sizeof(double) * c->nparam, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->ens) return ens_run(c, j, 1, y_in, y_out);
     m3d_status st = launch_prologue(c, c->u_dev);
     if (st != M3D_OK) return st;
     return launch_step(c, j, y_in, y_out);
@@ -1194,6 +1292,11 @@ m3d_status metos3d_year_map(m3d_ctx *c, const double *y0, double *y1, const doub
     if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_map: null context");
     if (!y0 || !y1 || (c->nparam > 0 && !u)) return fail(c, M3D_ERR_ARG, "metos3d_year_map: null pointer");
     size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    if (c->ens) {
+        if (c->nparam > 0)
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_dev, u, sizeof(double) * c->nparam, cudaMemcpyDeviceToDevice, c->stream));
+        return ens_run(c, 0, -1, y0, y1);
+    }
     if (c->plan == 1 && !c->year_graph) {
         m3d_status st = build_year_graph(c);
         if (st != M3D_OK) return st;
@@ -1210,6 +1313,16 @@ m3d_status metos3d_year_map_host(m3d_ctx *c, const double *y0_host, double *y1_h
     if (!y0_host || !y1_host || (c->nparam > 0 && !u_host))
         return fail(c, M3D_ERR_ARG, "metos3d_year_map_host: null pointer");
     size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    if (c->ens) {
+        if (c->nparam > 0)
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(c->u_dev, u_host, sizeof(double) * c->nparam, cudaMemcpyHostToDevice, c->stream));
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], y0_host, len, cudaMemcpyHostToDevice, c->stream));
+        m3d_status st = ens_run(c, 0, -1, c->ybuf[0], c->ybuf[1]);
+        if (st != M3D_OK) return st;
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(y1_host, c->ybuf[1], len, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+        return M3D_OK;
+    }
     if (c->plan == 1 && !c->year_graph) {
         m3d_status st = build_year_graph(c);
         if (st != M3D_OK) return st;
@@ -1237,6 +1350,9 @@ m3d_status metos3d_sync(m3d_ctx *c)
 m3d_status metos3d_set_option(m3d_ctx *c, int option, long long value)
 {
     if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_set_option: null context");
+    if (c->ens && option != M3D_OPT_WAIT_TIMEOUT_NS)
+        return fail(c, M3D_ERR_UNSUPPORTED, "option %d: this model runs in a one-member ensemble (one launch per step)",
+                    option);
     switch (option) {
     case M3D_OPT_YEAR_PLAN:
         if (value == M3D_PLAN_PERSISTENT && !c->persistent_ok)
@@ -1367,6 +1483,7 @@ m3d_status m3d_set_params(m3d_ctx *c, const double *u, cudaMemcpyKind kind)
 
 m3d_status m3d_year_device(m3d_ctx *c, const double *y0, double *y1)
 {
+    if (c->ens) return ens_run(c, 0, -1, y0, y1);
     size_t len = sizeof(double) * (size_t)c->ntr * c->n;
     if (c->plan == M3D_PLAN_GRAPH && !c->year_graph) {
         m3d_status st = build_year_graph(c);

@@ -56,3 +56,16 @@ def test_ensemble_init_rejects_bad_members_without_gpu_work(lib):
     with pytest.raises(m3d.Metos3dError) as ei:
         m3d.Ensemble.from_problem(p, [], stream=fake_stream)
     assert ei.value.status == m3d.M3D_ERR_ARG
+
+
+def test_single_context_model_counts_are_checked_without_gpu_work(lib):
+    import types
+    import m3d_inputs as mi
+    p = mi.make_problem("tiny_4x3x3")
+    fake_stream = types.SimpleNamespace(cuda_stream=0)
+    with pytest.raises(m3d.Metos3dError) as ei:
+        m3d.Context.from_problem(p, model=m3d.MODEL_PHY, ntracer=2, nparam=11, stream=fake_stream)
+    assert ei.value.status == m3d.M3D_ERR_ARG and "3 tracers and 11 parameters" in str(ei.value)
+    with pytest.raises(m3d.Metos3dError) as ei:
+        m3d.Context.from_problem(p, model=4, ntracer=4, nparam=4, stream=fake_stream)
+    assert ei.value.status == m3d.M3D_ERR_UNSUPPORTED
