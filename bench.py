@@ -50,7 +50,8 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the year kernel, from one ncu capture of this
 # workload (see profiles/); None where no capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {("resident", True): 178786304 + 4192256}
+# Keys: (plan, tridiagonal implicit form, per-step explicit operators).
+TRAFFIC_PER_LAUNCH = {("resident", True, False): 178786304 + 4192256}
 
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz maximum SM clock.
 # (A DFMA throughput probe on this GPU measured 1.20 TFLOP/s, 1.92 FMA/clock/SM at the
@@ -137,25 +138,29 @@ def run_ensemble(prob, t_single_ndop, flush):
     }
 
 
-def algorithmic_per_step(prob, ntr=2, tridiagonal=False):
+def algorithmic_per_step(prob, ntr=2, tridiagonal=False, step_operators=False):
     """Algorithmic bytes and FP64 flops of one TMM step.
 
-    bytes: explicit values of two months and their column indices, row pointers, the
-    implicit operator of two months (dense blocks: S_imp values each; tridiagonal form:
-    three Thomas factors per cell each), and the state read and written once.
-    flops: explicit part, one FMA to interpolate each entry plus one FMA per tracer;
-    implicit part, the same per dense block entry, or per cell and tracer two Thomas
-    solves (forward FMA, scaling multiply, backward FMA: 5 flops each) and the
-    interpolation (3 flops); the source term, ~20 flops per euphotic cell, ~8 per aphotic
-    cell, plus adding the increment to every tracer.
+    bytes: explicit values of two months (or, with per-step operators, the step's one
+    interpolated matrix) and their column indices, row pointers, the implicit operator of
+    two months (dense blocks: S_imp values each; tridiagonal form: three Thomas factors per
+    cell each), and the state read and written once.
+    flops: explicit part, one FMA per entry and tracer, plus one FMA per entry to
+    interpolate the monthly matrices unless the per-step operators were built beforehand
+    (once per context, not per year map); implicit part, the same per dense block entry, or
+    per cell and tracer two Thomas solves (forward FMA, scaling multiply, backward FMA: 5
+    flops each) and the interpolation (3 flops); the source term, ~20 flops per euphotic
+    cell, ~8 per aphotic cell, plus adding the increment to every tracer.
     """
     n, nnz, s_imp = prob.n, prob.nnz, prob.s_imp
     imp_bytes = (2 * 3 * n * 8) if tridiagonal else s_imp * 2 * 8
-    bytes_ = nnz * (2 * 8 + 4) + 4 * (n + 1) + imp_bytes + ntr * n * (8 + 8)
+    exp_values = 1 if step_operators else 2
+    bytes_ = nnz * (exp_values * 8 + 4) + 4 * (n + 1) + imp_bytes + ntr * n * (8 + 8)
     L = prob.nlayer
     n_eu = int(np.minimum(L, 2).sum())
     imp_flops = (13 * ntr * n) if tridiagonal else s_imp * (2 + 2 * ntr)
-    flops = nnz * (2 + 2 * ntr) + imp_flops + 20 * n_eu + 8 * (n - n_eu) + 2 * ntr * n
+    exp_flops = nnz * (2 * ntr if step_operators else 2 + 2 * ntr)
+    flops = exp_flops + imp_flops + 20 * n_eu + 8 * (n - n_eu) + 2 * ntr * n
     return bytes_, flops
 
 
@@ -359,6 +364,32 @@ def run_ours(args):
         e2e_dt = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
         e2e_value = whole_job_rate(world, e2e_steps, e2e_dt)
 
+        # the per-step explicit operators: their size, the time to build them, and the year
+        # map with the kernel interpolating every entry itself instead (identical results)
+        step_ops = bool(ctx.get_option(m3d.OPT_STEP_OPERATORS))
+        stepops = {"on": step_ops}
+        if step_ops:
+            stepops["bytes"] = int(ctx.get_option(m3d.OPT_STEP_OPERATOR_BYTES))
+            ctx.set_option(m3d.OPT_STEP_OPERATORS, 0)
+            k = max(1, min(args.steps, 3))
+            ctx.year_map(y0, ya, u)
+            t_int = 0.0
+            for _ in range(k):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.year_map(y0, ya, u)
+                e1.record(stream)
+                e1.synchronize()
+                t_int += e0.elapsed_time(e1) / 1e3
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.set_option(m3d.OPT_STEP_OPERATORS, 1)
+            stepops["build_s"] = time.perf_counter() - t0
+            stepops["in_kernel_interpolation"] = {"value": k / t_int, "unit": UNIT, "ms_per_year": 1e3 * t_int / k,
+                                                  "years": k}
+
         # cost of the adjoint year map (checkpoint every 240 steps) and of the tangent year map,
         # each relative to one year map, wall clock with the device synchronised on both sides
         costs = {}
@@ -432,7 +463,8 @@ def run_ours(args):
             pg.destroy_process_group()
         return 0
     hbm_peak, hbm_src = peaks()
-    bytes_step, flops_step = algorithmic_per_step(prob, tridiagonal=tridiagonal)
+    bytes_step, flops_step = algorithmic_per_step(prob, tridiagonal=tridiagonal, step_operators=step_ops)
+    _, method_flops_step = algorithmic_per_step(prob, tridiagonal=tridiagonal, step_operators=False)
     t_year = total / args.steps
     flops_year = flops_step * prob.nstep
     bytes_year = bytes_step * prob.nstep
@@ -448,13 +480,22 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed iterations (256 MiB write); 12 months of matrices (~270 MB) exceed L2"},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get((plan, tridiagonal)),
+                     "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                     "traffic": TRAFFIC_PER_LAUNCH.get((plan, tridiagonal, step_ops)),
                      "traffic_unit": "DRAM bytes per launch (one model year)",
                      "kernel": {"resident": "k_year_resident (one launch per model year)",
                                 "persistent": "k_year (one launch per model year)",
                                 "graph": "k_step (one launch per TMM step)"}[plan],
                      "plan": plan, "implicit_form": "tridiagonal" if tridiagonal else "dense",
-                     "peak_source": "FP64 units x max SM clock (152 SMs x 2 FMA/clk x 2.07 GHz)"},
+                     "peak_source": "FP64 units x max SM clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                     "flops_per_step": flops_step,
+                     "method_flops_per_step": method_flops_step,
+                     "frac_with_interpolation": method_flops_step * prob.nstep / t_year / 1e12 / FP64_PEAK_TFLOPS,
+                     "flops_note": ("flops the kernel executes; with per-step explicit operators the linear "
+                                    "interpolation of the monthly matrices (one FMA per entry and step) is done "
+                                    "once per context when they are built, and frac_with_interpolation counts "
+                                    "it anyway")},
+        "step_operators": stepops,
         "hbm_roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src,
                          "bytes_per_step": bytes_step, "flops_per_step": flops_step},

@@ -257,6 +257,18 @@ m3d_status metos3d_sync(m3d_ctx *ctx);
  *       applied as z0 + w (z1 - z0) with z_h solved by Thomas' algorithm from the two
  *       monthly tridiagonal factors, which equals the interpolated dense product up to
  *       rounding at a third of its FP64 work; M3D_IMPLICIT_DENSE: the dense blocks.
+ *   M3D_OPT_STEP_OPERATORS (resident plan): 1 keeps the explicit matrix of every step of the
+ *       year, A_m + w_j (A_{m+1} - A_m) (Section 4), in device memory, computed once with the
+ *       same fused multiply-add the year kernel would apply; the kernel then streams step j's
+ *       values into shared memory (one bulk copy per tile and step, made during the implicit
+ *       part of step j-1 from L2, where they were prefetched a step earlier) instead of
+ *       interpolating every entry, which saves a third of the explicit part's FP64 work and
+ *       gives bit-identical results.  Costs nstep x (explicit slot count) doubles
+ *       (16.9 GB on the 128 x 64 x 15 grid).  Default 1 when that is at most an eighth of the
+ *       free device memory at init, else 0.  Setting 1 allocates and computes the array
+ *       (synchronous; M3D_ERR_CUDA if the allocation fails, M3D_ERR_UNSUPPORTED without the
+ *       resident plan); 0 frees it.  The derivative sweeps use it for their forward parts.
+ *   M3D_OPT_STEP_OPERATOR_BYTES (read only): bytes held by the per-step operators (0 if none).
  * metos3d_get_option returns -1 for an unknown option.
  */
 enum {
@@ -265,7 +277,9 @@ enum {
     M3D_OPT_TEST_WITHHOLD_TILE = 3,
     M3D_OPT_NTILES = 4,
     M3D_OPT_IMPLICIT_FORM = 5,
-    M3D_OPT_ADJOINT_PLAN = 6
+    M3D_OPT_ADJOINT_PLAN = 6,
+    M3D_OPT_STEP_OPERATORS = 7,
+    M3D_OPT_STEP_OPERATOR_BYTES = 8
 };
 enum { M3D_IMPLICIT_DENSE = 0, M3D_IMPLICIT_TRIDIAGONAL = 1 };
 enum { M3D_PLAN_PERSISTENT = 0, M3D_PLAN_GRAPH = 1, M3D_PLAN_RESIDENT = 2 };

@@ -29,6 +29,8 @@ OPT_TEST_WITHHOLD_TILE = 3
 OPT_NTILES = 4
 OPT_IMPLICIT_FORM = 5
 OPT_ADJOINT_PLAN = 6
+OPT_STEP_OPERATORS = 7
+OPT_STEP_OPERATOR_BYTES = 8
 IMPLICIT_DENSE = 0
 IMPLICIT_TRIDIAGONAL = 1
 PLAN_PERSISTENT = 0

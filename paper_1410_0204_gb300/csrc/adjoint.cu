@@ -144,6 +144,7 @@ m3d_status setup_adjoint(m3d_ctx *c, const AdjointSetup &in)
     if (e == cudaSuccess) e = upload_vec(c, &PT.bk_b, bb);
     if (e == cudaSuccess) e = upload_vec(c, &PT.bk_d, bd);
     m3d::ResidentParams RT = c->R;
+    RT.sp_b = nullptr;              // the reverse sweep applies transposed operators
     // Thomas factors of M^T: the transposed blocks are the inverses of M^T
     if (e == cudaSuccess && c->tri_ok) {
         std::vector<double> tri((size_t)c->nmonth * 3 * n, 0.0), blk;

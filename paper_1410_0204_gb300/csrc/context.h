@@ -60,6 +60,8 @@ struct m3d_ctx {
     int adj_ok = 0, adj_tri_ok = 0, adj_dense_ok = 0;
     int adj_stream_ok = 0;              // the streaming reverse sweep fits (operators read from HBM)
     int adj_force_stream = 0;           // M3D_OPT_ADJOINT_PLAN = M3D_PLAN_PERSISTENT
+    double *sp_b = nullptr;             // per-step explicit operators [nstep][slot-lanes] (or null)
+    size_t sp_b_bytes = 0;
     size_t adj_smem_stream = 0;
     StepParams PT{};
     m3d::ResidentParams RTadj{};

@@ -48,6 +48,22 @@ __global__ void __launch_bounds__(m3d::kThreads, 1) k_year_resident(StepParams P
     m3d::year_resident<NTR, MODEL, TRI>(P, R, S, base, stride, period, j0, nsteps);
 }
 
+// Per-step explicit operators: out[j][i] = sp_a[m0(j)][i] + w_j sp_d[m0(j)][i], as one fused
+// multiply-add, the same one the year kernel otherwise evaluates for every entry and step
+// (Section 4: the explicit matrix of step j interpolated linearly between the monthly means).
+// Grid: blockIdx.y = step j, blocks along x stride over the slot-lanes.
+__global__ void k_step_operators(long long spn, const double *__restrict__ sp_a, const double *__restrict__ sp_d,
+                                 const int *__restrict__ m0tab, const double *__restrict__ wtab,
+                                 double *__restrict__ out)
+{
+    const int j = blockIdx.y;
+    const double w = wtab[j];
+    const double *a = sp_a + (long long)m0tab[j] * spn, *d = sp_d + (long long)m0tab[j] * spn;
+    double *o = out + (long long)j * spn;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < spn; i += (long long)gridDim.x * blockDim.x)
+        o[i] = fma(w, __ldg(d + i), __ldg(a + i));
+}
+
 // Per-call tables of the PO4-DOP model that depend on the parameters u:
 // atten = sigma_PAR exp(-k_w d) on euphotic cells, mfrac = Martin profile on aphotic cells.
 __global__ void k_ndop_prologue(int n, const int *cell_kl, const double *h, const double *zc,
@@ -276,10 +292,49 @@ void release(m3d_ctx *c)
 {
     if (!c) return;
     if (c->year_graph) cudaGraphExecDestroy(c->year_graph);
+    if (c->sp_b) cudaFree(c->sp_b);
+    c->sp_b = nullptr;
     for (void *p : c->allocs) cudaFree(p);
     if (c->red_host) cudaFreeHost(c->red_host);
     if (c->status_host) cudaFreeHost(c->status_host);
     c->allocs.clear();
+}
+
+// Build (on) or release the per-step explicit operators the resident year kernels stream.
+// Synchronous.  The array holds nstep x slot-lanes doubles (16.9 GB on the 128 x 64 x 15 grid).
+m3d_status set_step_operators(m3d_ctx *c, bool on)
+{
+    if (!on) {
+        if (c->sp_b) {
+            CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+            CUDA_OR_FAIL(c, cudaFree(c->sp_b));
+        }
+        c->sp_b = nullptr;
+        c->sp_b_bytes = 0;
+        c->R.sp_b = c->R_tan.sp_b = nullptr;
+        return M3D_OK;
+    }
+    if (c->sp_b) return M3D_OK;
+    const long long spn = c->P.sp_mstride;
+    const size_t bytes = sizeof(double) * (size_t)spn * (size_t)c->nstep;
+    double *buf = nullptr;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, M3D_ERR_CUDA, "per-step explicit operators: cannot allocate %zu bytes", bytes);
+    }
+    const int bx = (int)std::min<long long>((spn + 255) / 256, 64);
+    k_step_operators<<<dim3(bx, c->nstep), 256, 0, c->stream>>>(spn, c->P.sp_a, c->P.sp_d, c->P.m0tab, c->P.wtab, buf);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        return fail(c, M3D_ERR_CUDA, "per-step explicit operators: %s", cudaGetErrorString(e));
+    }
+    c->sp_b = buf;
+    c->sp_b_bytes = bytes;
+    c->R.sp_b = c->R_tan.sp_b = buf;
+    c->R.sp_bstride = c->R_tan.sp_bstride = spn;
+    return M3D_OK;
 }
 
 bool all_finite(const double *p, size_t count)
@@ -1055,6 +1110,17 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
         m3d_status ast = setup_adjoint(c, as);
         if (ast != M3D_OK) return bail(ast);
     }
+    if (c->resident_ok) {
+        // per-step explicit operators by default when they take at most an eighth of the free
+        // device memory (HBM is plentiful on this GPU, FP64 issue is not)
+        size_t free_b = 0, total_b = 0;
+        UP(cudaMemGetInfo(&free_b, &total_b));
+        const size_t need = sizeof(double) * (size_t)c->P.sp_mstride * (size_t)c->nstep;
+        if (need <= free_b / 8) {
+            m3d_status sst = set_step_operators(c, true);
+            if (sst != M3D_OK) return bail(sst);
+        }
+    }
 #undef UP
     *out = c;
     return M3D_OK;
@@ -1379,6 +1445,11 @@ m3d_status metos3d_set_option(m3d_ctx *c, int option, long long value)
         if (value < -1 || value >= c->ntiles) return fail(c, M3D_ERR_ARG, "tile out of range");
         c->S.withhold_tile = (int)value;
         return M3D_OK;
+    case M3D_OPT_STEP_OPERATORS:
+        if (value != 0 && value != 1) return fail(c, M3D_ERR_ARG, "step operators: 0 or 1");
+        if (value == 1 && !c->resident_ok)
+            return fail(c, M3D_ERR_UNSUPPORTED, "per-step operators serve the resident year kernel only");
+        return set_step_operators(c, value == 1);
     case M3D_OPT_ADJOINT_PLAN:
         if (value == M3D_PLAN_PERSISTENT && !c->adj_stream_ok)
             return fail(c, M3D_ERR_UNSUPPORTED, "the streaming adjoint sweep does not fit on this GPU");
@@ -1401,6 +1472,8 @@ long long metos3d_get_option(const m3d_ctx *c, int option)
     case M3D_OPT_TEST_WITHHOLD_TILE: return c->S.withhold_tile;
     case M3D_OPT_NTILES: return c->ntiles;
     case M3D_OPT_IMPLICIT_FORM: return c->implicit_form;
+    case M3D_OPT_STEP_OPERATORS: return c->sp_b != nullptr ? 1 : 0;
+    case M3D_OPT_STEP_OPERATOR_BYTES: return (long long)c->sp_b_bytes;
     case M3D_OPT_ADJOINT_PLAN:
         if (c->adj_stream_ok && (!c->adj_ok || c->adj_force_stream)) return M3D_PLAN_PERSISTENT;
         return c->adj_ok ? M3D_PLAN_RESIDENT : -1;

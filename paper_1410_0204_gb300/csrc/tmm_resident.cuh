@@ -37,10 +37,76 @@ struct ResidentParams {
     long long tri_mstride; // 3 n
     const int *chains;     // per tile: chains (column, tracer, month) sorted by depth
     const int *chain_off;  // [ntiles+1]
+    // Per-step explicit operators, when the context keeps them: sp_b[j][slot-lane] =
+    // A_m0(j) + w_j (A_m1(j) - A_m0(j)) in the slice layout of sp_a (sp_bstride slot-lanes per
+    // step).  The year kernel then streams step j's values into shared memory instead of
+    // interpolating every entry itself.  Null: interpolate in the kernel.
+    const double *sp_b;
+    long long sp_bstride;
 };
 
 // A chain packs: tile-local first cell of the column | layers << 16 | tracer << 23 | month << 27.
 __host__ __device__ inline int pack_chain(int cb, int L, int t, int h) { return cb | (L << 16) | (t << 23) | (h << 27); }
+
+// ---- one-dimensional bulk copies (TMA) from global into shared memory, completed on an
+// mbarrier.  Addresses and sizes are multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Make initialised barriers visible to the bulk-copy (async) proxy.
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Arrive on `bar` announcing `bytes` of transfer, then copy `bytes` from src (global) to dst
+// (shared); the barrier's phase completes when the bytes have landed.  bytes == 0: a plain
+// arrival.
+__device__ __forceinline__ void bulk_copy_to_shared(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    if (bytes == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(bar)) : "memory");
+        return;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Start bringing `bytes` at src (global) into L2; no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void *src, unsigned bytes)
+{
+    if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(__cvta_generic_to_global(src)), "r"(bytes)
+                            : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// Wait until the phase of parity `parity` of `bar` has completed, at most timeout_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
+                                                  unsigned long long timeout_ns)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_test(bar, parity))
+        if (global_ns() - t0 > timeout_ns) return false;
+    return true;
+}
 
 // Shared memory layout of one tile, in bytes from the dynamic shared memory base.
 struct ResidentLayout {
@@ -140,10 +206,13 @@ __device__ __forceinline__ void load_implicit_month(const StepParams &P, const R
 // Explicit part from shared memory: z[t][row] = (A_m0 + w D_m0) y for the tile's rows, plus
 // z[t][row] when ADD (z then holds the source increment).  Neighbour state from L2.  Run by
 // warp `warp` of `nwarps` warps that share the tile's slices as the deal (wlist, woff) gives.
-template <int NTR, bool ADD>
+// STEPOP: the step's interpolated values are already in shared memory at M.sa + sboff (same
+// slice layout as sa; an offset from M.sa keeps the loads shared-memory loads).
+template <int NTR, bool ADD, bool STEPOP = false>
 __device__ __forceinline__ void spmv_resident(const StepParams &P, const Tile &T, double w,
                                               const double *__restrict__ y, const TileSmem &M,
-                                              const int *wlist, const int *woff, int nwarps, int warp)
+                                              const int *wlist, const int *woff, int nwarps, int warp,
+                                              int sboff = 0)
 {
     const int lane = threadIdx.x & 31;
     const int zmax = P.zmax;
@@ -163,7 +232,7 @@ __device__ __forceinline__ void spmv_resident(const StepParams &P, const Tile &T
             const int idx = base + q * 32;
             double v[NTR];
             Y.gather(M.si[idx], v);
-            const double a = fma(w, M.sd[idx], M.sa[idx]);
+            const double a = STEPOP ? M.sa[sboff + idx] : fma(w, M.sd[idx], M.sa[idx]);
 #pragma unroll
             for (int t = 0; t < NTR; t++) acc[t] = fma(a, v[t], acc[t]);
         }
@@ -294,19 +363,43 @@ __device__ __forceinline__ void implicit_resident(const StepParams &P, const Res
 // The year (or nsteps steps from step j0) with the tiles' months resident in shared memory.
 // State of step s (interleaved): base + (s mod period) * stride; period 2 is a ping-pong,
 // period nsteps + 1 keeps every state (the trajectory an adjoint sweep reads back).
+//
+// With per-step explicit operators (R.sp_b) the two explicit arrays of shared memory become a
+// double buffer: step s reads buffer s mod 2, and once every thread is past step s's explicit
+// part a bulk copy brings step s+1's values into the other buffer (last read in step s-1)
+// while the tile solves the implicit part.  The copy reads from L2: step s+2's values are
+// prefetched from HBM into L2 at the same time, a step ahead of their copy, which keeps
+// HBM latency out of the step.  Every wait is bounded; a tile that gives up lets its copy in
+// flight land before it returns.
 template <int NTR, int MODEL, bool TRI>
 __device__ __forceinline__ void year_resident(const StepParams &P, const ResidentParams &R, const SyncParams &S,
                                               double *base, long long stride, int period, int j0, int nsteps)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ int abort_flag;
+    __shared__ __align__(8) unsigned long long opbar[2];
     const int tile = blockIdx.x;
     const Tile T = P.tiles[tile];
     const ResidentTile RT = R.rt[tile];
     const ResidentLayout Ly = resident_layout(NTR, R.sp_max, R.bk_max, P.zmax, TRI);
     const TileSmem M = tile_smem(dsm, Ly, P, T);
+    const bool stepop = R.sp_b != nullptr;     // buffers: M.sa and M.sd = M.sa + R.sp_max
+    const unsigned opbytes = (unsigned)RT.sp_n * 8u;
+    const int copier = kThreads - 32;          // a thread off the implicit part's critical path
+    auto op_src = [&](int s) { return R.sp_b + (long long)((j0 + s) % P.nstep) * R.sp_bstride + RT.sp_base; };
+    auto fetch_operator = [&](int s) {         // step s's values into buffer s mod 2; s+1's into L2
+        bulk_copy_to_shared((s & 1) ? M.sd : M.sa, op_src(s), opbytes, &opbar[s & 1]);
+        if (s + 1 < nsteps) prefetch_l2(op_src(s + 1), opbytes);
+    };
 
+    if (stepop && threadIdx.x == 0) {
+        mbar_init(&opbar[0], 1);
+        mbar_init(&opbar[1], 1);
+        mbar_init_fence();
+        fetch_operator(0);
+    }
     copy_to_shared_int(M.si, P.sp_col + RT.sp_base, RT.sp_n);
+    __syncthreads();
     int cur_month = -1;
     for (int s = 0; s < nsteps; s++) {
         const int j = (j0 + s) % P.nstep;
@@ -316,7 +409,7 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
         const double w = __ldg(P.wtab + j);
         if (m0 != cur_month) {
             // a new month: load this tile's matrices (independent of the state, so before the wait)
-            load_explicit_month(P, RT, P.sp_a, P.sp_d, m0, M);
+            if (!stepop) load_explicit_month(P, RT, P.sp_a, P.sp_d, m0, M);
             load_implicit_month<TRI>(P, R, RT, T, R.tri, P.bk_b, P.bk_d, m0, M);
             cur_month = m0;
             __syncthreads();
@@ -333,19 +426,44 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
                                                                       kSpThreads);
             }
         } else {
-            if (s > 0) {
+            if (s > 0 || stepop) {
                 if (threadIdx.x < 32) {
-                    const bool ok = wait_neighbours(S, tile, s, s);
+                    bool ok = s > 0 ? wait_neighbours(S, tile, s, s) : true;
+                    if (ok && stepop && !mbar_wait_bounded(&opbar[s & 1], (s >> 1) & 1, S.timeout_ns)) {
+                        if (atomicCAS(S.status, 0, 1) == 0) {
+                            S.status[1] = tile;
+                            S.status[2] = s;
+                        }
+                        ok = false;
+                    }
+                    ok = __all_sync(0xffffffffu, ok);
                     if (threadIdx.x == 0) abort_flag = ok ? 0 : 1;
                 }
                 barrier_sub(3);
             }
-            if (s == 0 || !abort_flag)
+            if (stepop) {
+                // every reader observes the completed copy itself (it has, so this returns at once)
+                if (!abort_flag) {
+                    if (mbar_wait_bounded(&opbar[s & 1], (s >> 1) & 1, S.timeout_ns))
+                        spmv_resident<NTR, false, true>(P, T, w, y, M, P.sp_wlist_g, P.sp_woff_g, kSpThreads / 32,
+                                                        (int)(threadIdx.x >> 5), (s & 1) * R.sp_max);
+                    else if (atomicCAS(S.status, 0, 1) == 0) {
+                        S.status[1] = tile;
+                        S.status[2] = s;
+                    }
+                }
+            } else if (s == 0 || !abort_flag) {
                 spmv_resident<NTR, false>(P, T, w, y, M, P.sp_wlist_g, P.sp_woff_g, kSpThreads / 32,
                                           (int)(threadIdx.x >> 5));
+            }
         }
         __syncthreads();
-        if (s > 0 && abort_flag) return;
+        if ((s > 0 || stepop) && abort_flag) {
+            // the copy of step s may still be in flight (no later one was issued)
+            if (stepop && threadIdx.x == 0) mbar_wait_bounded(&opbar[s & 1], (s >> 1) & 1, S.timeout_ns);
+            return;
+        }
+        if (stepop && threadIdx.x == copier && s + 1 < nsteps) fetch_operator(s + 1);
         if (ModelTraits<MODEL>::has_q) {
             const int nc = T.ncell, zmax = P.zmax;
             for (int e = threadIdx.x; e < NTR * nc; e += blockDim.x) {

@@ -159,9 +159,50 @@ def test_all_plans_agree_bitwise(m3d, name):
         ctx.set_option(m3d.OPT_YEAR_PLAN, code)
         out[plan] = torch.empty_like(y0)
         ctx.year_map(y0, out[plan], u)
+    # the resident kernel interpolating every explicit entry itself, instead of streaming the
+    # per-step operators built at init with the same fused multiply-add
+    ctx.set_option(m3d.OPT_YEAR_PLAN, m3d.PLAN_RESIDENT)
+    assert ctx.get_option(m3d.OPT_STEP_OPERATORS) == 1
+    ctx.set_option(m3d.OPT_STEP_OPERATORS, 0)
+    out["resident_interpolating"] = torch.empty_like(y0)
+    ctx.year_map(y0, out["resident_interpolating"], u)
     ctx.sync()
     assert torch.equal(out["resident"], out["graph"])
     assert torch.equal(out["persistent"], out["graph"])
+    assert torch.equal(out["resident_interpolating"], out["graph"])
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["tiny_6x4x4", "ndop_64x32x8", "ndop_128x64x15"])
+def test_step_operators_match_in_kernel_interpolation(m3d, name):
+    """Per-step explicit operators (nstep x slot-lanes doubles, built once) against the kernel
+    interpolating the monthly matrices itself: bit-identical year maps in the tridiagonal
+    form; the option reports and releases its memory."""
+    p, _ = problem(name)
+    u = cuda(mi.default_params_ndop())
+    y0 = cuda(mi.random_state(p))
+    ctx = ctx_for(m3d, p)
+    assert ctx.get_option(m3d.OPT_IMPLICIT_FORM) == m3d.IMPLICIT_TRIDIAGONAL
+    assert ctx.get_option(m3d.OPT_STEP_OPERATORS) == 1
+    nbytes = ctx.get_option(m3d.OPT_STEP_OPERATOR_BYTES)
+    assert nbytes > 0 and nbytes % (8 * 32 * p.nstep) == 0
+    assert nbytes >= 8 * p.nnz * p.nstep                           # at least one value per entry and step
+    streamed, interpolated = torch.empty_like(y0), torch.empty_like(y0)
+    ctx.year_map(y0, streamed, u)
+    ctx.set_option(m3d.OPT_STEP_OPERATORS, 0)
+    assert ctx.get_option(m3d.OPT_STEP_OPERATORS) == 0 and ctx.get_option(m3d.OPT_STEP_OPERATOR_BYTES) == 0
+    ctx.year_map(y0, interpolated, u)
+    ctx.sync()
+    assert torch.equal(streamed, interpolated)
+    ctx.set_option(m3d.OPT_STEP_OPERATORS, 1)
+    assert ctx.get_option(m3d.OPT_STEP_OPERATOR_BYTES) == nbytes
+    again = torch.empty_like(y0)
+    ctx.year_map(y0, again, u)
+    ctx.sync()
+    assert torch.equal(again, streamed)
+    with pytest.raises(m3d.Metos3dError) as e:
+        ctx.set_option(m3d.OPT_STEP_OPERATORS, 2)
+    assert e.value.status == m3d.M3D_ERR_ARG
     ctx.close()
 
 
@@ -218,12 +259,16 @@ def test_persistent_wait_timeout_is_reported_and_recoverable(m3d):
     assert ctx.get_option(m3d.OPT_NTILES) > 1
     ctx.set_option(m3d.OPT_WAIT_TIMEOUT_NS, 50_000_000)      # 50 ms
     ctx.set_option(m3d.OPT_TEST_WITHHOLD_TILE, 0)
-    for plan in (m3d.PLAN_RESIDENT, m3d.PLAN_PERSISTENT):
+    # the resident kernel streaming per-step operators (its tiles let their bulk copy in
+    # flight land before they stop), interpolating in the kernel, and the persistent kernel
+    for plan, stepop in ((m3d.PLAN_RESIDENT, 1), (m3d.PLAN_RESIDENT, 0), (m3d.PLAN_PERSISTENT, 0)):
         ctx.set_option(m3d.OPT_YEAR_PLAN, plan)
+        ctx.set_option(m3d.OPT_STEP_OPERATORS, stepop)
         ctx.year_map(y0, y1, u)
         with pytest.raises(m3d.Metos3dError) as e:
             ctx.sync()
         assert e.value.status == m3d.M3D_ERR_TIMEOUT
+    ctx.set_option(m3d.OPT_STEP_OPERATORS, 1)
     ctx.set_option(m3d.OPT_YEAR_PLAN, m3d.PLAN_RESIDENT)
     ctx.set_option(m3d.OPT_TEST_WITHHOLD_TILE, -1)
     ctx.set_option(m3d.OPT_WAIT_TIMEOUT_NS, 2_000_000_000)
