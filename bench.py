@@ -51,7 +51,7 @@ def peaks():
 # DRAM bytes (read + write) per launch of the year kernel, from one ncu capture of this
 # workload (see profiles/); None where no capture of the current kernel exists.
 # Keys: (plan, tridiagonal implicit form, per-step explicit operators).
-TRAFFIC_PER_LAUNCH = {("resident", True, False): 178786304 + 4192256}
+TRAFFIC_PER_LAUNCH = {("resident", True, True): 16971404032 + 4501760}
 
 # FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz maximum SM clock.
 # (A DFMA throughput probe on this GPU measured 1.20 TFLOP/s, 1.92 FMA/clock/SM at the
@@ -537,6 +537,26 @@ def run_profile_steps(nsteps):
     return 0
 
 
+def run_profile_years(nyears, grid):
+    """A short run for profilers: nyears year maps (the resident year kernel) on `grid`."""
+    import torch
+    import paper_1410_0204_gb300 as m3d
+    prob = mi.make_problem(grid)
+    ctx = m3d.Context.from_problem(prob, model=m3d.MODEL_NDOP, ntracer=2, nparam=7)
+    y = torch.from_numpy(mi.initial_state(prob)).cuda()
+    u = torch.from_numpy(mi.default_params_ndop()).cuda()
+    yn = torch.empty_like(y)
+    for _ in range(nyears):
+        ctx.year_map(y, yn, u)
+        y, yn = yn, y
+    torch.cuda.synchronize()
+    out = {"profile_years": nyears, "grid": grid, "plan": ctx.get_option(m3d.OPT_YEAR_PLAN),
+           "step_operator_bytes": ctx.get_option(m3d.OPT_STEP_OPERATOR_BYTES)}
+    ctx.close()
+    print(json.dumps(out))
+    return 0
+
+
 def run_scale_1deg(args):
     """The 1-degree grid (360 x 180 x 23, 700,000 cells): the single-context N-DOP year map and
     the 16-member NPZD-DOP ensemble year map, each timed with CUDA events over whole years."""
@@ -644,6 +664,9 @@ def main():
                     help="only run this many single TMM steps of the workload (for profilers)")
     ap.add_argument("--profile-ensemble-steps", type=int, default=0,
                     help="only run this many steps of the 64-member ensemble (for profilers)")
+    ap.add_argument("--profile-years", type=int, default=0,
+                    help="only run this many year maps (for profilers) on --profile-grid")
+    ap.add_argument("--profile-grid", default=WORKLOAD, help="grid of --profile-years")
     ap.add_argument("--scale-1deg", action="store_true",
                     help="time the 1-degree grid (single context and 16-member ensemble) instead")
     args = ap.parse_args()
@@ -653,6 +676,8 @@ def main():
         return run_profile_ensemble(args.profile_ensemble_steps)
     if args.profile_steps:
         return run_profile_steps(args.profile_steps)
+    if args.profile_years:
+        return run_profile_years(args.profile_years, args.profile_grid)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
