@@ -342,6 +342,52 @@ m3d_status metos3d_newton_solve(m3d_ctx *ctx, double *y, const double *u, const 
                                 m3d_newton_report *report);
 
 /*
+ * Gradient at the periodic solution (the parameter optimisation of Sections 1 and 9, where
+ * the misfit is evaluated on the periodic state ys(u) = phi(ys(u); u) that Newton's method
+ * finds).  phi conserves mass, so ys(u) is defined for a fixed total mass: d ys / d u solves
+ * (I - phi_y) dy = phi_u du with vol^T dy = 0 (vol repeated per tracer).  For a misfit J with
+ * g = dJ/dy at ys, the implicit function theorem gives dJ/du = dJ/du|_y + (d ys / d u)^T g, and
+ * the second term is computed by one adjoint solve:
+ *     find lambda with vol^T lambda = 0 and P (I - phi_y^T) lambda = P g,
+ *     P x = x - (vol^T x / vol^T vol) vol   (the projection on the zero-mass directions),
+ * then ubar = phi_u^T lambda (lambda = 0 and ubar = 0 when ||P g|| <= 1e-13 ||g||: a g along
+ * the mass direction alone, up to rounding).  The solve is restarted GMRES with modified Gram-Schmidt on the
+ * zero-mass directions (where P (I - phi_y^T) is the adjoint of I - phi_y, invertible there
+ * when the periodic solution is unique for its mass); each iteration is one reverse sweep of
+ * the adjoint year map at ys, whose forward sweep runs once for the whole solve.
+ *
+ * ystar: device [ntracer][n], the periodic solution (e.g. from metos3d_newton_solve);
+ * u: device [nparam]; g: device [ntracer][n]; lambda: device [ntracer][n] output (may be
+ * NULL); ubar_host: host [nparam] output, (d ys / d u)^T g.  opts NULL for the defaults
+ * (metos3d_gradient_default_options); report may be NULL.  PO4-DOP only, as
+ * metos3d_year_adjoint.  Returns M3D_NOT_CONVERGED (results and report filled in) if the
+ * relative residual tolerance is not met within max_krylov iterations.  Synchronous;
+ * allocates the Krylov basis ((restart + 11) state vectors) and the adjoint's trajectory
+ * ((ckpt_every + 1) states; the default keeps the whole year, 2.4 GB for 52,749 cells and two
+ * tracers) for the call.
+ */
+typedef struct {
+    double tol;                 /* ||P g - P (I - phi_y^T) lambda|| / ||P g|| to reach (default 1e-8) */
+    int restart;                /* GMRES restart length (default 200) */
+    int max_krylov;             /* GMRES iterations in total (default 1000) */
+    int ckpt_every;             /* adjoint checkpoints (default: nstep, the whole trajectory kept) */
+} m3d_gradient_opts;
+
+typedef struct {
+    int converged;
+    int krylov;                 /* GMRES iterations */
+    int reverse_sweeps;         /* reverse sweeps of the adjoint year map */
+    double forward_years;       /* forward steps run / nstep (1 with the default ckpt_every) */
+    double residual;            /* final relative residual, recomputed from lambda */
+    double seconds;
+} m3d_gradient_report;
+
+void metos3d_gradient_default_options(m3d_gradient_opts *opts);
+m3d_status metos3d_periodic_gradient(m3d_ctx *ctx, const double *ystar, const double *u, const double *g,
+                                     double *lambda, double *ubar_host, const m3d_gradient_opts *opts,
+                                     m3d_gradient_report *report);
+
+/*
  * Batched ensembles.  The paper's parameter studies and optimisations (Sections 1 and 9) run the
  * same transport for many parameter sets; an ensemble advances many members -- each with its
  * own model and parameters -- through the same TMM steps at once, so that every matrix entry

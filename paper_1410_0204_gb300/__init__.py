@@ -10,5 +10,5 @@ from .binding import (Context, Metos3dError, bgc, declared_symbols, load, librar
                       OPT_WAIT_TIMEOUT_NS, OPT_TEST_WITHHOLD_TILE, OPT_NTILES, PLAN_PERSISTENT, PLAN_GRAPH,
                       PLAN_RESIDENT, OPT_IMPLICIT_FORM, OPT_ADJOINT_PLAN, OPT_STEP_OPERATORS,
                       OPT_STEP_OPERATOR_BYTES, IMPLICIT_DENSE, IMPLICIT_TRIDIAGONAL,
-                      JV_FD, JV_TANGENT, NewtonOptions, NewtonReport,
+                      JV_FD, JV_TANGENT, NewtonOptions, NewtonReport, GradientOptions, GradientReport,
                       year_map_autograd, Ensemble, MODEL_N, MODEL_PHY, MODEL_NPZD, MODEL_NTRACER)

@@ -92,6 +92,19 @@ JV_FD = 0
 JV_TANGENT = 1
 
 
+class GradientOptions(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_krylov", C.c_int), ("ckpt_every", C.c_int)]
+
+
+class GradientReport(C.Structure):
+    _fields_ = [("converged", C.c_int), ("krylov", C.c_int), ("reverse_sweeps", C.c_int),
+                ("forward_years", C.c_double), ("residual", C.c_double), ("seconds", C.c_double)]
+
+    def to_dict(self):
+        return {"converged": bool(self.converged), "krylov": self.krylov, "reverse_sweeps": self.reverse_sweeps,
+                "forward_years": self.forward_years, "residual": self.residual, "seconds": self.seconds}
+
+
 class _Member(C.Structure):
     _fields_ = [("model_id", C.c_int), ("nparam", C.c_int), ("u", C.POINTER(C.c_double))]
 
@@ -147,6 +160,10 @@ def load(build_if_missing: bool = False):
     L.metos3d_newton_default_options.argtypes = [C.POINTER(NewtonOptions)]
     L.metos3d_newton_default_options.restype = None
     L.metos3d_newton_solve.argtypes = [vp, vp, vp, C.POINTER(NewtonOptions), C.POINTER(NewtonReport)]
+    L.metos3d_gradient_default_options.argtypes = [C.POINTER(GradientOptions)]
+    L.metos3d_gradient_default_options.restype = None
+    L.metos3d_periodic_gradient.argtypes = [vp, vp, vp, vp, vp, dp, C.POINTER(GradientOptions),
+                                            C.POINTER(GradientReport)]
     L.metos3d_spinup.argtypes = [vp, vp, vp, C.c_int, C.c_double, dp, C.POINTER(C.c_int)]
     L.metos3d_year_tangent.argtypes = [vp, vp, vp, vp, vp, vp]
     L.metos3d_year_adjoint.argtypes = [vp, vp, vp, vp, vp, dp, C.c_int]
@@ -173,7 +190,8 @@ def load(build_if_missing: bool = False):
         fn = getattr(L, name)
         if name not in ("metos3d_last_error", "metos3d_free", "metos3d_last_launch_count",
                         "metos3d_residual_static_error", "metos3d_get_option",
-                        "metos3d_newton_default_options", "metos3d_ensemble_last_launch_count",
+                        "metos3d_newton_default_options", "metos3d_gradient_default_options",
+                        "metos3d_ensemble_last_launch_count",
                         "metos3d_ensemble_last_error", "metos3d_ensemble_free"):
             fn.restype = C.c_int
     _lib = L
@@ -376,6 +394,24 @@ class Context:
         if check and st not in (M3D_OK, M3D_NOT_CONVERGED):
             _check(st, self._ctx)
         return st, rep.to_dict()
+
+    def periodic_gradient(self, ystar, u, g, lam=None, check=True, **opts):
+        """(d ys/d u)^T g at the periodic solution ys (metos3d_periodic_gradient); lam, if given,
+        receives the adjoint solution.  Returns (status, ubar ndarray, report dict)."""
+        self._sync_stream()
+        o = GradientOptions()
+        self._L.metos3d_gradient_default_options(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        rep = GradientReport()
+        ubar = np.zeros(self.nparam)
+        st = self._L.metos3d_periodic_gradient(self._ctx, _dev_ptr(ystar, self.numel, "ystar"),
+                                               _dev_ptr(u, self.nparam, "u"), _dev_ptr(g, self.numel, "g"),
+                                               _dev_ptr(lam, self.numel, "lam", True) if lam is not None else None,
+                                               _dp(ubar), C.byref(o), C.byref(rep))
+        if check and st not in (M3D_OK, M3D_NOT_CONVERGED):
+            _check(st, self._ctx)
+        return st, ubar, rep.to_dict()
 
     def sync(self):
         """Wait for the stream; raises Metos3dError(M3D_ERR_TIMEOUT) if the last year map timed out."""

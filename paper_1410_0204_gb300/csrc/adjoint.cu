@@ -299,83 +299,138 @@ m3d_status adjoint_segment(m3d_ctx *c, bool tri, const double *traj, long long l
 
 }  // namespace
 
-extern "C" m3d_status metos3d_year_adjoint(m3d_ctx *c, const double *y0, const double *u, const double *ybar1,
-                                           double *ybar0, double *ubar_host, int ckpt_every)
+m3d_status AdjointSweep::begin(m3d_ctx *ctx, int ckpt_every)
 {
-    if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_adjoint: null context");
-    if (!y0 || !u || !ybar1 || !ybar0) return fail(c, M3D_ERR_ARG, "metos3d_year_adjoint: null pointer");
-    const bool stream = c->adj_stream_ok && (!c->adj_ok || c->adj_force_stream);
+    c = ctx;
+    stream = c->adj_stream_ok && (!c->adj_ok || c->adj_force_stream);
     if (!c->adj_ok && !stream)
         return fail(c, M3D_ERR_UNSUPPORTED,
-                    "metos3d_year_adjoint: needs the PO4-DOP model with one internal step, a structurally "
+                    "adjoint year map: needs the PO4-DOP model with one internal step, a structurally "
                     "symmetric explicit pattern, and a tile that fits on the GPU");
-    const int K = ckpt_every > 0 ? std::min(ckpt_every, c->nstep) : std::min(240, c->nstep);
-    const int nseg = (c->nstep + K - 1) / K;
-    const bool tri = !stream && c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && c->adj_tri_ok && c->tri_resident_ok;
+    K = ckpt_every > 0 ? std::min(ckpt_every, c->nstep) : std::min(240, c->nstep);
+    nseg = (c->nstep + K - 1) / K;
+    tri = !stream && c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && c->adj_tri_ok && c->tri_resident_ok;
     if (!stream && !tri && !c->adj_dense_ok)
-        return fail(c, M3D_ERR_UNSUPPORTED, "metos3d_year_adjoint: the dense form does not fit");
-    const long long len = (long long)c->ntr * c->n;
+        return fail(c, M3D_ERR_UNSUPPORTED, "adjoint year map: the dense form does not fit");
+    len = (long long)c->ntr * c->n;
     const size_t vb = sizeof(double) * (size_t)len;
-    void *p = nullptr;
-    double *traj = nullptr, *chk = nullptr, *zb = nullptr, *yb = nullptr;
-    auto cleanup = [&]() { free_owned(c, traj); free_owned(c, chk); free_owned(c, zb); free_owned(c, yb); };
-#define ALLOC(ptr, bytes) do { cudaError_t e_ = m3d_alloc(c, &p, (bytes)); \
-        if (e_ != cudaSuccess) { cleanup(); return fail(c, M3D_ERR_CUDA, "metos3d_year_adjoint: %s", cudaGetErrorString(e_)); } \
-        ptr = (double *)p; } while (0)
-    ALLOC(traj, vb * (size_t)(K + 1));
-    ALLOC(chk, vb * (size_t)(nseg + 1));
-    ALLOC(zb, vb * 2);
-    ALLOC(yb, vb * 2);
-#undef ALLOC
-    m3d_status st = M3D_OK;
-#define TRY(x) do { st = (x); if (st != M3D_OK) { cleanup(); return st; } } while (0)
-    TRY(m3d_set_params(c, u, cudaMemcpyDeviceToDevice));
-    TRY(m3d_prologue(c));
+    const size_t sizes[4] = {vb * (size_t)(K + 1), vb * (size_t)(nseg + 1), vb * 2, vb * 2};
+    double **bufs[4] = {&traj, &chk, &zb, &yb};
+    for (int b = 0; b < 4; b++) {
+        void *p = nullptr;
+        cudaError_t e = m3d_alloc(c, &p, sizes[b]);
+        if (e != cudaSuccess) {
+            release();
+            return fail(c, M3D_ERR_CUDA, "adjoint year map: %s (%zu bytes)", cudaGetErrorString(e), sizes[b]);
+        }
+        *bufs[b] = (double *)p;
+    }
+    held = -1;
+    launches = 0;
+    reverse_sweeps = 0;
+    return M3D_OK;
+}
+
+void AdjointSweep::release()
+{
+    if (!c) return;
+    free_owned(c, traj);
+    free_owned(c, chk);
+    free_owned(c, zb);
+    free_owned(c, yb);
+    traj = chk = zb = yb = nullptr;
+    held = -1;
+}
+
+// Recompute segment seg from its checkpoint into traj (all its states kept).
+static m3d_status recompute_segment(AdjointSweep &A, int seg)
+{
+    m3d_ctx *c = A.c;
+    const size_t vb = sizeof(double) * (size_t)A.len;
+    const int j0 = seg * A.K, ns = std::min(A.K, c->nstep - j0);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(A.traj, A.chk + (size_t)seg * A.len, vb, cudaMemcpyDeviceToDevice, c->stream));
+    m3d_status st = A.stream ? forward_segment_stream(c, A.traj, A.len, j0, ns)
+                             : forward_segment(c, A.tri, A.traj, A.len, j0, ns);
+    if (st != M3D_OK) return st;
+    A.launches += A.stream ? 3LL * ns : 1;
+    A.held = seg;
+    return M3D_OK;
+}
+
+m3d_status AdjointSweep::forward(const double *y0, const double *u)
+{
+    const size_t vb = sizeof(double) * (size_t)len;
+    m3d_status st = m3d_set_params(c, u, cudaMemcpyDeviceToDevice);
+    if (st != M3D_OK) return st;
+    st = m3d_prologue(c);
+    if (st != M3D_OK) return st;
     const int nb = (c->n + 255) / 256;
     k_martin_b<<<nb, 256, 0, c->stream>>>(c->n, c->cell_kl, c->h, c->u_dev, c->mfrac_b);
     c->rk.to_interleaved<<<nb, 256, 0, c->stream>>>(c->n, y0, chk);
     CUDA_OR_FAIL(c, cudaGetLastError());
-    // forward sweep, one checkpoint per segment
+    launches += 3;
+    // one checkpoint per segment; traj ends holding the last segment
     for (int seg = 0; seg < nseg; seg++) {
-        const int j0 = seg * K, ns = std::min(K, c->nstep - j0);
-        CUDA_OR_FAIL(c, cudaMemcpyAsync(traj, chk + (size_t)seg * len, vb, cudaMemcpyDeviceToDevice, c->stream));
-        TRY(stream ? forward_segment_stream(c, traj, len, j0, ns) : forward_segment(c, tri, traj, len, j0, ns));
+        st = recompute_segment(*this, seg);
+        if (st != M3D_OK) return st;
+        const int ns = std::min(K, c->nstep - seg * K);
         CUDA_OR_FAIL(c, cudaMemcpyAsync(chk + (size_t)(seg + 1) * len, traj + (size_t)ns * len, vb,
                                         cudaMemcpyDeviceToDevice, c->stream));
     }
-    // reverse sweep, segment by segment (the last segment's states are still in traj)
+    return M3D_OK;
+}
+
+m3d_status AdjointSweep::reverse(const double *ybar1, double *ybar0, double *ubar_host)
+{
+    const int nb = (c->n + 255) / 256;
     double *ya = yb, *ybn = yb + len;
     c->rk.to_interleaved<<<nb, 256, 0, c->stream>>>(c->n, ybar1, ya);
     CUDA_OR_FAIL(c, cudaGetLastError());
+    launches += 1;
     double ub[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::vector<double> part((size_t)8 * c->ntiles);
+    m3d_status st = M3D_OK;
     for (int seg = nseg - 1; seg >= 0; seg--) {
         const int j0 = seg * K, ns = std::min(K, c->nstep - j0);
-        if (seg != nseg - 1) {
-            CUDA_OR_FAIL(c, cudaMemcpyAsync(traj, chk + (size_t)seg * len, vb, cudaMemcpyDeviceToDevice, c->stream));
-            TRY(stream ? forward_segment_stream(c, traj, len, j0, ns) : forward_segment(c, tri, traj, len, j0, ns));
+        if (held != seg) {
+            st = recompute_segment(*this, seg);
+            if (st != M3D_OK) return st;
         }
-        TRY(stream ? adjoint_segment_stream(c, traj, len, ya, ybn, zb, zb + len, j0, ns)
-                   : adjoint_segment(c, tri, traj, len, ya, ybn, zb, zb + len, j0, ns));
+        st = stream ? adjoint_segment_stream(c, traj, len, ya, ybn, zb, zb + len, j0, ns)
+                    : adjoint_segment(c, tri, traj, len, ya, ybn, zb, zb + len, j0, ns);
+        if (st != M3D_OK) return st;
+        launches += 1;
         CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
         CUDA_OR_FAIL(c, cudaMemcpyAsync(part.data(), c->A.ubar_part, sizeof(double) * part.size(),
                                         cudaMemcpyDeviceToHost, c->stream));
-        TRY(metos3d_sync(c));
+        st = metos3d_sync(c);
+        if (st != M3D_OK) return st;
         for (int t = 0; t < c->ntiles; t++)
             for (int k = 0; k < 7; k++) ub[k] += part[(size_t)t * 8 + k];
         std::swap(ya, ybn);
     }
     c->rk.from_interleaved<<<nb, 256, 0, c->stream>>>(c->n, ya, ybar0);
     CUDA_OR_FAIL(c, cudaGetLastError());
+    launches += 1;
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     if (ubar_host)
         for (int k = 0; k < 7; k++) ubar_host[k] = ub[k];
-    // prologue, Martin gradient and two layout passes; per segment a forward (one launch, or
-    // three per step when streaming) and a reverse launch; the last segment is not recomputed
-    const long long fwd = stream ? 3LL * c->nstep : nseg;
-    const long long refwd = stream ? 3LL * (c->nstep - std::min(K, c->nstep - (nseg - 1) * K)) : nseg - 1;
-    c->last_launches = 4 + fwd + refwd + nseg;
-    cleanup();
+    reverse_sweeps++;
     return M3D_OK;
-#undef TRY
+}
+
+extern "C" m3d_status metos3d_year_adjoint(m3d_ctx *c, const double *y0, const double *u, const double *ybar1,
+                                           double *ybar0, double *ubar_host, int ckpt_every)
+{
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_adjoint: null context");
+    if (!y0 || !u || !ybar1 || !ybar0) return fail(c, M3D_ERR_ARG, "metos3d_year_adjoint: null pointer");
+    AdjointSweep A;
+    m3d_status st = A.begin(c, ckpt_every);
+    if (st == M3D_OK) st = A.forward(y0, u);
+    if (st == M3D_OK) st = A.reverse(ybar1, ybar0, ubar_host);
+    // prologue, Martin gradient, three layout passes; per segment a forward (one launch, or
+    // three per step when streaming) and a reverse launch; the last segment is not recomputed
+    if (st == M3D_OK) c->last_launches = (int)A.launches;
+    A.release();
+    return st;
 }

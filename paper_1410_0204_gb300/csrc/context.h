@@ -114,6 +114,26 @@ m3d_status m3d_step_device(m3d_ctx *c, int j, const double *y, double *yn);
 m3d_status m3d_prologue(m3d_ctx *c);
 // Device allocation owned by the context (freed by metos3d_free).
 cudaError_t m3d_alloc(m3d_ctx *c, void **p, size_t bytes);
+// The adjoint year map as one forward sweep and any number of reverse sweeps at the same
+// (y0, u).  The forward sweep keeps a checkpoint every K steps (K >= nstep: the whole
+// trajectory); each reverse sweep recomputes the K-step segments it needs that are not held
+// (none when K >= nstep) and returns ybar0 = phi_y^T ybar1 and ubar = phi_u^T ybar1.  So
+// repeated products phi_y^T v at one state, as a Krylov solve makes, cost one reverse sweep
+// each after the first forward sweep.  PO4-DOP only (the caller checks c->adj_ok or
+// c->adj_stream_ok through begin()).
+struct AdjointSweep {
+    m3d_ctx *c = nullptr;
+    int K = 0, nseg = 0, held = -1;     // held: the segment whose states traj holds
+    bool stream = false, tri = false;
+    long long len = 0;
+    double *traj = nullptr, *chk = nullptr, *zb = nullptr, *yb = nullptr;
+    long long launches = 0;             // kernel launches so far
+    int reverse_sweeps = 0;
+    m3d_status begin(m3d_ctx *ctx, int ckpt_every);   // checks, then allocates the buffers
+    m3d_status forward(const double *y0, const double *u);
+    m3d_status reverse(const double *ybar1, double *ybar0, double *ubar_host);
+    void release();
+};
 // Checks of a grid and its matrices (sizes, CSR order and range, block sizes, finiteness).
 m3d_status m3d_validate_inputs(const m3d_grid *g, const m3d_matrices *mt, std::string &why);
 // Thomas factors of M when the row-major L x L block B is M's inverse and M is tridiagonal.

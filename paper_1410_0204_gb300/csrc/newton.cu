@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "context.h"
@@ -181,9 +182,13 @@ m3d_status apply_jacobian(Solver &S, const double *y, const double *py, double y
     return S.launch_ok();
 }
 
-// Restarted GMRES(m) with modified Gram-Schmidt for J x = b, x0 = 0.
-m3d_status gmres(Solver &S, const double *b, double *x, const double *y, const double *py, double ynorm,
-                 double eps, double tol_rel, int maxit, int *iters, int *year_maps)
+// w = A v for a vector v of norm vnorm (the operator of a Krylov solve).
+using Operator = std::function<m3d_status(const double *v, double vnorm, double *w)>;
+
+// Restarted GMRES(m) with modified Gram-Schmidt for A x = b, x0 = 0.  res_rel (may be null)
+// receives the last residual estimate relative to ||b||.
+m3d_status gmres(Solver &S, const Operator &apply, const double *b, double *x, double tol_rel, int maxit, int *iters,
+                 double *res_rel = nullptr)
 {
     m3d_ctx *c = S.c;
     Workspace &W = S.W;
@@ -194,6 +199,7 @@ m3d_status gmres(Solver &S, const double *b, double *x, const double *y, const d
     m3d_status st = S.norm(b, &bnorm);
     if (st != M3D_OK) return st;
     *iters = 0;
+    if (res_rel) *res_rel = 0.0;
     if (bnorm == 0.0) return M3D_OK;
     double *r = W.w;                               // the first residual is b itself
     double beta = bnorm;
@@ -208,7 +214,7 @@ m3d_status gmres(Solver &S, const double *b, double *x, const double *y, const d
         for (int k = 0; k < m; k++) {
             double *vk = W.V + (size_t)k * N;
             double *hk = W.H + (size_t)k * (m + 1);
-            st = apply_jacobian(S, y, py, ynorm, eps, vk, 1.0, W.w, year_maps);
+            st = apply(vk, 1.0, W.w);
             if (st != M3D_OK) return st;
             for (int i = 0; i <= k; i++) {            // modified Gram-Schmidt, coefficients on the device
                 const double *vi = W.V + (size_t)i * N;
@@ -257,17 +263,19 @@ m3d_status gmres(Solver &S, const double *b, double *x, const double *y, const d
             st = S.axpby(x, 1.0, x, yk[i], W.V + (size_t)i * N);
             if (st != M3D_OK) return st;
         }
+        if (res_rel) *res_rel = std::fabs(g[k_used]) / bnorm;
         if (done && (std::fabs(g[k_used]) <= tol_rel * bnorm || *iters >= maxit)) break;
         // restart from the true residual r = b - J x
         double xnorm = 0.0;
         st = S.norm(x, &xnorm);
         if (st != M3D_OK) return st;
-        st = apply_jacobian(S, y, py, ynorm, eps, x, xnorm, W.tmp, year_maps);
+        st = apply(x, xnorm, W.tmp);
         if (st != M3D_OK) return st;
         st = S.axpby(r, 1.0, b, -1.0, W.tmp);
         if (st != M3D_OK) return st;
         st = S.norm(r, &beta);
         if (st != M3D_OK) return st;
+        if (res_rel) *res_rel = beta / bnorm;
         if (beta <= tol_rel * bnorm || *iters >= maxit) break;
         st = S.axpby(W.V, 1.0 / beta, r, 0.0, r);
         if (st != M3D_OK) return st;
@@ -429,7 +437,10 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
         TRY(S.axpby(W.tmp, -1.0, W.F, 0.0, W.F));                 // b = -F (tmp is reused inside gmres)
         TRY(S.axpby(W.yn, 1.0, W.tmp, 0.0, W.tmp));               // keep b in yn during the solve
         int its = 0;
-        TRY(gmres(S, W.yn, W.s, W.y, W.py, ynorm, o.fd_eps, eta, o.max_krylov, &its, &R.year_maps));
+        const Operator jac = [&](const double *v, double vnorm, double *w) {
+            return apply_jacobian(S, W.y, W.py, ynorm, o.fd_eps, v, vnorm, w, &R.year_maps);
+        };
+        TRY(gmres(S, jac, W.yn, W.s, eta, o.max_krylov, &its));
         R.krylov_total += its;
         // project the step onto zero-mass directions: s -= (w.s / w.w) w
         double ms = 0.0;
@@ -479,6 +490,117 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
     m3d_status out = R.converged ? M3D_OK : M3D_NOT_CONVERGED;
     if (!R.converged) fail(c, M3D_NOT_CONVERGED, "Newton stopped at residual %.3e after %d steps", r, R.newton_steps);
     return finish(out);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+void metos3d_gradient_default_options(m3d_gradient_opts *o)
+{
+    if (!o) return;
+    o->tol = 1e-8;
+    o->restart = 200;
+    o->max_krylov = 1000;
+    o->ckpt_every = 0;
+}
+
+m3d_status metos3d_periodic_gradient(m3d_ctx *c, const double *ystar, const double *u, const double *g,
+                                     double *lambda, double *ubar_host, const m3d_gradient_opts *opts,
+                                     m3d_gradient_report *rep)
+{
+    if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_periodic_gradient: null context");
+    if (!ystar || !u || !g || !ubar_host) return fail(c, M3D_ERR_ARG, "metos3d_periodic_gradient: null pointer");
+    m3d_gradient_opts o;
+    metos3d_gradient_default_options(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.restart < 1 || o.max_krylov < 1)
+        return fail(c, M3D_ERR_ARG, "metos3d_periodic_gradient: bad options");
+    auto t0 = std::chrono::steady_clock::now();
+    m3d_gradient_report R;
+    memset(&R, 0, sizeof R);
+    Solver S{c, {}, 0, 0};
+    AdjointSweep A;
+    m3d_status st = A.begin(c, o.ckpt_every > 0 ? o.ckpt_every : c->nstep);
+    if (st != M3D_OK) return st;
+    st = ensure_workspace(c, S, o.restart);
+    Workspace &W = S.W;
+    const long long N = S.N;
+    auto finish = [&](m3d_status s) {
+        R.reverse_sweeps = A.reverse_sweeps;
+        R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (rep) *rep = R;
+        A.release();
+        release_workspace(c, W);
+        return s;
+    };
+    if (st != M3D_OK) return finish(st);
+#define TRY(x) do { st = (x); if (st != M3D_OK) return finish(st); } while (0)
+    auto cu = [&](cudaError_t e) -> m3d_status {
+        return e == cudaSuccess ? M3D_OK : fail(c, M3D_ERR_CUDA, "metos3d_periodic_gradient: %s", cudaGetErrorString(e));
+    };
+    long long fwd_steps = 0;
+    auto count_forward = [&]() {
+        // every recomputed segment is K steps (the last one possibly fewer); the first sweep is nstep
+        R.forward_years = (double)fwd_steps / c->nstep;
+    };
+    TRY(A.forward(ystar, u));
+    fwd_steps += c->nstep;
+    // the zero-mass projection P x = x - (w.x / w.w) w, w = vol repeated per tracer
+    double wsum = 0.0;
+    TRY(S.dot_dev(c->vol, c->vol, W.scal, false, c->n));
+    TRY(S.read(W.scal, &wsum, 1));
+    wsum *= c->ntr;
+    auto project = [&](double *x) -> m3d_status {
+        double m = 0.0;
+        m3d_status s2 = S.mass(x, &m);
+        if (s2 != M3D_OK) return s2;
+        k_sub_mass<<<S.grid, 256, 0, c->stream>>>(x, c->vol, c->n, m / wsum, N);
+        return S.launch_ok();
+    };
+    // segments a reverse sweep recomputes: all but the held one when the trajectory is split
+    const long long recompute_steps = A.nseg > 1 ? (long long)c->nstep - std::min(A.K, c->nstep - (A.nseg - 1) * A.K) : 0;
+    // w = P (v - phi_y^T v), one reverse sweep
+    const Operator adjoint_op = [&](const double *v, double, double *w) -> m3d_status {
+        m3d_status s2 = A.reverse(v, W.phv, nullptr);
+        if (s2 != M3D_OK) return s2;
+        fwd_steps += recompute_steps;
+        s2 = S.axpby(w, 1.0, v, -1.0, W.phv);
+        if (s2 != M3D_OK) return s2;
+        return project(w);
+    };
+    // b = P g; what is left of a g along the mass direction alone is rounding (no gradient at
+    // fixed mass), so b is taken as zero when it is that small
+    TRY(cu(cudaMemcpyAsync(W.F, g, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream)));
+    double gnorm = 0.0, bnorm = 0.0;
+    TRY(S.norm(W.F, &gnorm));
+    TRY(project(W.F));
+    TRY(S.norm(W.F, &bnorm));
+    if (bnorm <= 1e-13 * gnorm) {
+        TRY(cu(cudaMemsetAsync(W.F, 0, sizeof(double) * N, c->stream)));
+        bnorm = 0.0;
+    }
+    int its = 0;
+    double est = 0.0;
+    TRY(gmres(S, adjoint_op, W.F, W.x, o.tol, o.max_krylov, &its, &est));
+    TRY(project(W.x));
+    R.krylov = its;
+    // ubar = phi_u^T lambda; the same sweep gives phi_y^T lambda for the true residual
+    TRY(A.reverse(W.x, W.phv, ubar_host));
+    fwd_steps += recompute_steps;
+    TRY(S.axpby(W.w, 1.0, W.x, -1.0, W.phv));
+    TRY(project(W.w));
+    TRY(S.axpby(W.w, 1.0, W.F, -1.0, W.w));
+    double rnorm = 0.0;
+    TRY(S.norm(W.w, &rnorm));
+    R.residual = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+    R.converged = est <= o.tol;
+    count_forward();
+    if (lambda) TRY(cu(cudaMemcpyAsync(lambda, W.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream)));
+    TRY(cu(cudaStreamSynchronize(c->stream)));
+    c->last_launches = (int)std::min<long long>(A.launches, 1LL << 30);
+#undef TRY
+    return finish(R.converged ? M3D_OK : M3D_NOT_CONVERGED);
 }
 
 }  // extern "C"
