@@ -600,6 +600,10 @@ def run_scale_1deg(args):
     t_adj = time.perf_counter() - t0
     adj_plan = {m3d.PLAN_RESIDENT: "resident", m3d.PLAN_PERSISTENT: "streaming"}.get(
         ctx.get_option(m3d.OPT_ADJOINT_PLAN), "none")
+    # the tangent year map (phi and phi' v in one pass), CUDA events
+    v = torch.ones_like(y0)
+    phi, jv = torch.empty_like(y0), torch.empty_like(y0)
+    t_tan = timed(lambda: ctx.year_tangent(y0, v, u, phi, jv), reps)
     ctx.close()
     _, flops_single = algorithmic_per_step(prob, tridiagonal=True)
     members = mi.make_ensemble(((mi.MODEL_NPZD, 16),), seed=1410)
@@ -620,6 +624,7 @@ def run_scale_1deg(args):
                          "frac": flops_single * prob.nstep / t_single / 1e12 / FP64_PEAK_TFLOPS},
             "adjoint": {"seconds": t_adj, "adjoint_over_forward": t_adj / t_single, "ckpt_every": 480,
                         "sweep": adj_plan},
+            "tangent": {"seconds": t_tan, "tangent_over_forward": t_tan / t_single},
             "ensemble": {"workload": "16 NPZD-DOP members (5 tracers), parameters within +-50% of the defaults",
                          "member_years_per_s": len(members) / t_ens, "seconds_per_ensemble_year": t_ens,
                          "tiling": {"cols_per_block": cpb, "warps_per_block": nw, "autotune_ms_per_step": ms},

@@ -344,8 +344,12 @@ bool all_finite(const double *p, size_t count)
     return true;
 }
 
-// Contiguous partition of the water columns into tiles of about equal FP64 work.
-std::vector<int> partition_columns(const m3d_grid *g, const int *rowptr, int ntr, int ntiles)
+// Contiguous partition of the water columns into tiles of about equal FP64 work.  With
+// max_cells > 0 no tile may hold more cells than that: when the equal-work partition breaks
+// the cap, the tiles are the greedy packing (each tile takes columns while its work stays
+// within W and its cells within max_cells) for the smallest W that needs at most ntiles tiles,
+// which is the smallest largest tile work any contiguous partition under the cap can reach.
+std::vector<int> partition_columns(const m3d_grid *g, const int *rowptr, int ntr, int ntiles, int max_cells = 0)
 {
     std::vector<double> work(g->ncol);
     for (int c = 0; c < g->ncol; c++) {
@@ -365,7 +369,38 @@ std::vector<int> partition_columns(const m3d_grid *g, const int *rowptr, int ntr
         if (t < ntiles && acc >= total * t / ntiles && c + 1 < g->ncol) bounds.push_back(c + 1);
     }
     bounds.push_back(g->ncol);
-    return bounds;
+    int widest = 0;
+    for (size_t t = 0; t + 1 < bounds.size(); t++)
+        widest = std::max(widest, g->col_start[bounds[t + 1]] - g->col_start[bounds[t]]);
+    if (max_cells <= 0 || widest <= max_cells) return bounds;
+    auto greedy = [&](double W, std::vector<int> *out) {
+        int tiles = 0, cells = 0;
+        double acc = 0.0;
+        if (out) out->assign(1, 0);
+        for (int c = 0; c < g->ncol; c++) {
+            const int L = g->col_start[c + 1] - g->col_start[c];
+            if (c > 0 && (acc + work[c] > W || cells + L > max_cells)) {
+                tiles++;
+                if (out) out->push_back(c);
+                acc = 0.0;
+                cells = 0;
+            }
+            acc += work[c];
+            cells += L;
+        }
+        if (out) out->push_back(g->ncol);
+        return tiles + 1;
+    };
+    double lo = *std::max_element(work.begin(), work.end()), hi = total;
+    if (greedy(hi, nullptr) > ntiles) return bounds;      // the cap alone needs more tiles
+    for (int it = 0; it < 60 && hi - lo > 1e-9 * hi; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (greedy(mid, nullptr) <= ntiles) hi = mid;
+        else lo = mid;
+    }
+    std::vector<int> capped;
+    greedy(hi, &capped);
+    return capped;
 }
 
 // Deal the slices [s0, s1) (cost = slot count) to the warps of one tile: longest first to
@@ -677,7 +712,12 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
         const long long need = (long long)(1.25 * g->n * per_cell / (double)prop.sharedMemPerBlockOptin) + 1;
         ntarget = (int)std::min<long long>(g->ncol, std::max<long long>(ntarget, need));
     }
-    std::vector<int> bounds = partition_columns(g, rp, c->ntr, ntarget);
+    // PO4-DOP contexts also run the tangent, whose tile holds four components: cap the tile so
+    // that they fit in shared memory (binding only on very large grids)
+    int max_cells = 0;
+    if (md->model_id == M3D_MODEL_NDOP)
+        max_cells = (int)(((long long)prop.sharedMemPerBlockOptin - 2048) / (sizeof(double) * (2 * c->ntr + 2)));
+    std::vector<int> bounds = partition_columns(g, rp, c->ntr, ntarget, max_cells);
     int ntiles = (int)bounds.size() - 1;
     c->ntiles = ntiles;
 

@@ -70,6 +70,29 @@ def test_single_context_year_conserves_mass(m3d, grid):
     ctx.close()
 
 
+def test_tangent_year_matches_central_differences(m3d, grid):
+    # the tangent's tiles hold four components, which fit in shared memory because the tiles
+    # of a PO4-DOP context are capped at the cells that allow it; phi'(y) v against
+    # (phi(y + h v) - phi(y - h v)) / 2h, and the tangent's phi against the year map
+    p, _ = grid
+    ctx = m3d.Context.from_problem(p, model=m3d.MODEL_NDOP, ntracer=2, nparam=7)
+    y0 = torch.from_numpy(mi.random_state(p, 2, seed=77)).cuda()
+    v = torch.from_numpy(mi.random_state(p, 2, seed=78) - 0.5).cuda()
+    u = torch.from_numpy(mi.default_params_ndop()).cuda()
+    phi, jv = torch.empty_like(y0), torch.empty_like(y0)
+    ctx.year_tangent(y0, v, u, phi, jv)
+    y1 = torch.empty_like(y0)
+    ctx.year_map(y0, y1, u)
+    h = 1e-6 * float(torch.linalg.norm(y0)) / float(torch.linalg.norm(v))
+    yp, ym = torch.empty_like(y0), torch.empty_like(y0)
+    ctx.year_map(y0 + h * v, yp, u)
+    ctx.year_map(y0 - h * v, ym, u)
+    fd = ((yp - ym) / (2 * h)).cpu().numpy()
+    assert rel_err(phi.cpu().numpy(), y1.cpu().numpy()) <= 1e-13
+    assert np.max(np.abs(jv.cpu().numpy() - fd)) <= 1e-6 * np.max(np.abs(fd))
+    ctx.close()
+
+
 def test_npzd_ensemble_steps_match_oracle(m3d, grid):
     p, P = grid
     members = mi.make_ensemble(((mi.MODEL_NPZD, 16),), seed=5)
