@@ -604,8 +604,9 @@ def run_scale_1deg(args):
     v = torch.ones_like(y0)
     phi, jv = torch.empty_like(y0), torch.empty_like(y0)
     t_tan = timed(lambda: ctx.year_tangent(y0, v, u, phi, jv), reps)
+    tridiagonal = ctx.get_option(m3d.OPT_IMPLICIT_FORM) == m3d.IMPLICIT_TRIDIAGONAL
     ctx.close()
-    _, flops_single = algorithmic_per_step(prob, tridiagonal=True)
+    _, flops_single = algorithmic_per_step(prob, tridiagonal=tridiagonal)
     members = mi.make_ensemble(((mi.MODEL_NPZD, 16),), seed=1410)
     ens = m3d.Ensemble.from_problem(prob, members)
     Y0 = torch.from_numpy(np.vstack([mi.initial_state(prob, 5, mi.model_initial_values(mi.MODEL_NPZD))
@@ -618,7 +619,8 @@ def run_scale_1deg(args):
     line = {"metric": METRIC, "value": 1.0 / t_single, "unit": UNIT, "n_gpus": 1, "steps": reps,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name + " year map: PO4-DOP, 2 tracers, 2880 TMM steps per model year",
-                       "n": prob.n, "ncol": prob.ncol, "nnz": prob.nnz, "S_imp": prob.s_imp, "plan": plan},
+                       "n": prob.n, "ncol": prob.ncol, "nnz": prob.nnz, "S_imp": prob.s_imp, "plan": plan,
+                       "implicit_form": "tridiagonal" if tridiagonal else "dense"},
             "roofline": {"bound": "alu", "achieved": flops_single * prob.nstep / t_single / 1e12,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": flops_single * prob.nstep / t_single / 1e12 / FP64_PEAK_TFLOPS},

@@ -251,12 +251,15 @@ m3d_status metos3d_sync(m3d_ctx *ctx);
  *       M3D_PLAN_PERSISTENT (default otherwise, e.g. on a 1-degree grid): a streaming sweep that
  *       reads the transposed operators from HBM every step and applies dense implicit blocks,
  *       its forward segments recomputed one step launch at a time; -1 when neither fits.
- *   M3D_OPT_IMPLICIT_FORM (resident plan): M3D_IMPLICIT_TRIDIAGONAL (default when every
- *       monthly implicit block is, to 1e-11 relative, the inverse of a tridiagonal matrix,
- *       as a vertical diffusion (I - dt K)^{-1} is): the interpolated implicit part is
- *       applied as z0 + w (z1 - z0) with z_h solved by Thomas' algorithm from the two
- *       monthly tridiagonal factors, which equals the interpolated dense product up to
- *       rounding at a third of its FP64 work; M3D_IMPLICIT_DENSE: the dense blocks.
+ *   M3D_OPT_IMPLICIT_FORM: M3D_IMPLICIT_TRIDIAGONAL (default when every monthly implicit
+ *       block is, to 1e-11 relative, the inverse of a tridiagonal matrix, as a vertical
+ *       diffusion (I - dt K)^{-1} is, and the plan in use can apply it): the interpolated
+ *       implicit part is applied as (1 - w) z0 + w z1 with z_h solved by Thomas' algorithm
+ *       from the two monthly tridiagonal factors, which equals the interpolated dense product
+ *       up to rounding at a third of its FP64 work.  The resident kernel keeps the factors in
+ *       shared memory; the persistent and graph plans read them from global memory (contexts
+ *       of at most two tracers).  All plans give the same bits in either form.
+ *       M3D_IMPLICIT_DENSE: the dense blocks.
  *   M3D_OPT_STEP_OPERATORS (resident plan): 1 keeps the explicit matrix of every step of the
  *       year, A_m + w_j (A_{m+1} - A_m) (Section 4), in device memory, computed once with the
  *       same fused multiply-add the year kernel would apply; the kernel then streams step j's

@@ -116,6 +116,7 @@ m3d_status setup_adjoint(m3d_ctx *c, const AdjointSetup &in)
             }
         }
     StepParams PT = c->P;
+    PT.use_tri = 0;                 // the forward Thomas factors are not the transposed operator's
     cudaError_t e = upload_vec(c, &PT.sp_a, a);
     if (e == cudaSuccess) e = upload_vec(c, &PT.sp_d, d);
     // transposed dense blocks in the forward block layout: lane (row r of column cc) holds B[k][r]

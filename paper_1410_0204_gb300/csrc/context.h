@@ -61,6 +61,7 @@ struct m3d_ctx {
     int adj_stream_ok = 0;              // the streaming reverse sweep fits (operators read from HBM)
     int adj_force_stream = 0;           // M3D_OPT_ADJOINT_PLAN = M3D_PLAN_PERSISTENT
     double *sp_b = nullptr;             // per-step explicit operators [nstep][slot-lanes] (or null)
+    int tri_stream_ok = 0;              // the streaming kernels can apply the Thomas form (<= 2 tracers)
     size_t sp_b_bytes = 0;
     size_t adj_smem_stream = 0;
     StepParams PT{};

@@ -1062,6 +1062,28 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
                 c->R.tri_mstride = 3LL * c->n;
                 c->R_tan.tri = tri_dev;
                 c->R_tan.tri_mstride = 3LL * c->n;
+                // (column, tracer) chains of the streaming kernels' Thomas part, deepest first
+                if (c->ntr <= 2) {
+                    std::vector<int> tch, tch_off(ntiles + 1, 0);
+                    for (int t = 0; t < ntiles; t++) {
+                        int c0 = bounds[t], c1 = bounds[t + 1], cell0 = g->col_start[c0];
+                        std::vector<int> cols;
+                        for (int cc = c0; cc < c1; cc++) cols.push_back(cc);
+                        std::stable_sort(cols.begin(), cols.end(), [&](int a, int b) {
+                            return (g->col_start[a + 1] - g->col_start[a]) > (g->col_start[b + 1] - g->col_start[b]);
+                        });
+                        for (int cc : cols)
+                            for (int tr = 0; tr < c->ntr; tr++)
+                                tch.push_back(m3d::pack_chain(g->col_start[cc] - cell0,
+                                                              g->col_start[cc + 1] - g->col_start[cc], tr, 0));
+                        tch_off[t + 1] = (int)tch.size();
+                    }
+                    UP(upload_vec(c, &P.tchains, tch));
+                    UP(upload_vec(c, &P.tchain_off, tch_off));
+                    P.tri = tri_dev;
+                    P.tri_mstride = 3LL * c->n;
+                    c->tri_stream_ok = 1;
+                }
                 // Thomas chains (column, component, month) per tile, deepest columns first; the
                 // model with its tangent has twice the components
                 for (int variant = 0; variant < 2; variant++) {
@@ -1108,8 +1130,11 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
             c->tri_resident_ok = (long long)rps * prop.multiProcessorCount >= ntiles;
         }
         if (c->tri_resident_ok && !c->resident_ok) c->resident_ok = 1;
-        c->implicit_form = c->tri_resident_ok ? M3D_IMPLICIT_TRIDIAGONAL : M3D_IMPLICIT_DENSE;
         c->plan = c->resident_ok ? M3D_PLAN_RESIDENT : (c->persistent_ok ? M3D_PLAN_PERSISTENT : M3D_PLAN_GRAPH);
+        // the Thomas form wherever the plan in use can apply it
+        const bool tri_here = c->plan == M3D_PLAN_RESIDENT ? c->tri_resident_ok : c->tri_stream_ok;
+        c->implicit_form = tri_here ? M3D_IMPLICIT_TRIDIAGONAL : M3D_IMPLICIT_DENSE;
+        P.use_tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && c->tri_stream_ok;
         if (c->model == M3D_MODEL_NDOP) {
             // the model with its tangent: same tiles, four state components
             YearVariant &V = c->tan;
@@ -1279,7 +1304,7 @@ m3d_status run_year_from_ybuf(m3d_ctx *c, double *out, cudaMemcpyKind kind)
         long long stride = -c->ybuf_cap;                    // y_s = ybuf[1] - (s mod 2) cap
         int period = 2, j0 = 0, nsteps = c->nstep;
         void *args[] = {&P, &R, &S, &b0, &stride, &period, &j0, &nsteps};
-        const bool tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL;
+        const bool tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && c->tri_resident_ok;
         CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)(tri ? c->rk.year_tri : c->rk.year), dim3(c->ntiles),
                                                     dim3(m3d::kThreads), args,
                                                     tri ? c->resident_tri_smem : c->resident_smem, c->stream));
@@ -1474,12 +1499,18 @@ m3d_status metos3d_set_option(m3d_ctx *c, int option, long long value)
         c->S.timeout_ns = (unsigned long long)value;
         return M3D_OK;
     case M3D_OPT_IMPLICIT_FORM:
-        if (value == M3D_IMPLICIT_TRIDIAGONAL && !c->tri_resident_ok)
+        if (value == M3D_IMPLICIT_TRIDIAGONAL && !c->tri_resident_ok && !c->tri_stream_ok)
             return fail(c, M3D_ERR_UNSUPPORTED, "the implicit blocks have no usable tridiagonal form");
-        if (value == M3D_IMPLICIT_DENSE && !(c->resident_smem <= c->resident_tri_smem || c->resident_ok))
+        if (value == M3D_IMPLICIT_DENSE && c->plan == M3D_PLAN_RESIDENT &&
+            !(c->resident_smem <= c->resident_tri_smem || c->resident_ok))
             return fail(c, M3D_ERR_UNSUPPORTED, "the dense resident kernel does not fit");
         if (value != M3D_IMPLICIT_DENSE && value != M3D_IMPLICIT_TRIDIAGONAL) return fail(c, M3D_ERR_ARG, "bad form");
         c->implicit_form = (int)value;
+        c->P.use_tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && c->tri_stream_ok;
+        if (c->year_graph) {                 // its launches captured the previous form
+            cudaGraphExecDestroy(c->year_graph);
+            c->year_graph = nullptr;
+        }
         return M3D_OK;
     case M3D_OPT_TEST_WITHHOLD_TILE:
         if (value < -1 || value >= c->ntiles) return fail(c, M3D_ERR_ARG, "tile out of range");

@@ -72,6 +72,13 @@ struct StepParams {
     const int *sp_wlist_g, *sp_woff_g;
     const double *bk_b, *bk_d;             // [nmonth][...]: B_m and B_{m+1} - B_m
     long long bk_mstride;
+    // The implicit part in Thomas form for the streaming kernels (use_tri != 0; at most two
+    // tracers): factors [month][3][n] (-l_k, 1/d_k, -e_k/d_{k+1}), and per tile its (column,
+    // tracer) chains packed as pack_chain(first tile-local cell, layers, tracer, 0), deepest first
+    const double *tri;
+    long long tri_mstride;
+    const int *tchains, *tchain_off;       // [ntiles+1]
+    int use_tri;
     // biogeochemistry
     const int *eu_list, *ap_list;          // tile-local cells, grouped per tile
     const int *sh_list;                    // tile-local bottom cells of shallow columns (nsub = 1)
@@ -443,6 +450,43 @@ __device__ __forceinline__ void step_tile(const StepParams &P, int tile, int j,
     }
     __syncthreads();
 
+    // ---- implicit part in Thomas form: y_{j+1} = (1 - w) M_m0^{-1} z + w M_m1^{-1} z, one
+    // thread per (column, tracer) solving both months in turn with the factors read from
+    // global memory (the tile's shared memory holds z and, in the export scratch no longer
+    // needed, the forward sweep's intermediates).  Month m1 first: its weighted solution
+    // c1 u1 is stored, then month m0 adds c0 u0 with one fused multiply-add, as the resident
+    // kernel's blend does, so both give the same bits.
+    if constexpr (NTR <= 2) {
+        if (P.use_tri) {
+            const int m1 = (m0 + 1) % P.nmonth;
+            const int c0 = __ldg(P.tchain_off + tile), c1 = __ldg(P.tchain_off + tile + 1);
+            for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) {
+                const int pc = __ldg(P.tchains + c);
+                const int cb = pc & 0xffff, L = (pc >> 16) & 0x7f, t = (pc >> 23) & 0xf;
+                const int cell = T.cell0 + cb;
+                const double *zc = z + t * zmax + cb;
+                double *g = ek + t * zmax + cb;
+                double *out = yn + (size_t)t * n + cell;
+                for (int h = 1; h >= 0; h--) {
+                    const double *F = P.tri + (long long)(h ? m1 : m0) * P.tri_mstride + cell;
+                    const double *nl = F, *rd = F + n, *ne = F + 2 * (size_t)n;
+                    const double wt = h ? w : 1.0 - w;
+                    double acc = 0.0;
+                    for (int k = 0; k < L; k++) {            // g_k = z_k - l_k g_{k-1}
+                        acc = fma(__ldg(nl + k), acc, zc[k]);
+                        g[k] = acc;
+                    }
+                    double u = 0.0;
+                    for (int k = L - 1; k >= 0; k--) {       // u_k = g_k - (e_k/d_{k+1}) u_{k+1}
+                        u = fma(__ldg(ne + k), u, g[k]);
+                        const double cw = wt * __ldg(rd + k);
+                        out[k] = h ? cw * u : fma(cw, u, out[k]);
+                    }
+                }
+            }
+            return;
+        }
+    }
     // ---- implicit part: y_{j+1} = (B_m0 + w (B_m1 - B_m0)) z, column by column
     {
         const double *__restrict__ b0 = P.bk_b + (long long)m0 * P.bk_mstride;

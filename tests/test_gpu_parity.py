@@ -148,7 +148,8 @@ def test_year_map_paper_grid_matches_oracle(m3d):
 
 @pytest.mark.parametrize("name", ["ndop_64x32x8", "ndop_128x64x15"])
 def test_all_plans_agree_bitwise(m3d, name):
-    """All plans run the same per-tile arithmetic in the same order: identical results."""
+    """All plans run the same per-tile arithmetic in the same order: identical results, in
+    the dense and in the Thomas form of the implicit part."""
     p, _ = problem(name)
     u = cuda(mi.default_params_ndop())
     y0 = cuda(mi.random_state(p))
@@ -170,6 +171,18 @@ def test_all_plans_agree_bitwise(m3d, name):
     assert torch.equal(out["resident"], out["graph"])
     assert torch.equal(out["persistent"], out["graph"])
     assert torch.equal(out["resident_interpolating"], out["graph"])
+    # the Thomas form: resident chains with factors in shared memory, and the streaming
+    # kernels' chains reading them from global memory, blend in the same order
+    ctx.set_option(m3d.OPT_IMPLICIT_FORM, m3d.IMPLICIT_TRIDIAGONAL)
+    tri = {}
+    for plan, code in PLANS.items():
+        ctx.set_option(m3d.OPT_YEAR_PLAN, code)
+        tri[plan] = torch.empty_like(y0)
+        ctx.year_map(y0, tri[plan], u)
+    ctx.sync()
+    assert torch.equal(tri["resident"], tri["graph"])
+    assert torch.equal(tri["persistent"], tri["graph"])
+    assert not torch.equal(tri["graph"], out["graph"])      # the two forms differ in rounding
     ctx.close()
 
 

@@ -88,7 +88,9 @@ def test_tangent_year_matches_central_differences(m3d, grid):
     ctx.year_map(y0 + h * v, yp, u)
     ctx.year_map(y0 - h * v, ym, u)
     fd = ((yp - ym) / (2 * h)).cpu().numpy()
-    assert rel_err(phi.cpu().numpy(), y1.cpu().numpy()) <= 1e-13
+    # the year map applies the implicit part in Thomas form, the tangent's four-component
+    # tile the dense blocks: equal up to rounding
+    assert rel_err(phi.cpu().numpy(), y1.cpu().numpy()) <= 1e-11
     assert np.max(np.abs(jv.cpu().numpy() - fd)) <= 1e-6 * np.max(np.abs(fd))
     ctx.close()
 
