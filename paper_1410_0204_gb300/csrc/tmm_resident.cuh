@@ -383,7 +383,8 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
     const ResidentTile RT = R.rt[tile];
     const ResidentLayout Ly = resident_layout(NTR, R.sp_max, R.bk_max, P.zmax, TRI);
     const TileSmem M = tile_smem(dsm, Ly, P, T);
-    const bool stepop = R.sp_b != nullptr;     // buffers: M.sa and M.sd = M.sa + R.sp_max
+    // buffers: M.sa and M.sd = M.sa + R.sp_max (no copy is started for an empty launch)
+    const bool stepop = R.sp_b != nullptr && nsteps > 0;
     const unsigned opbytes = (unsigned)RT.sp_n * 8u;
     const int copier = kThreads - 32;          // a thread off the implicit part's critical path
     auto op_src = [&](int s) { return R.sp_b + (long long)((j0 + s) % P.nstep) * R.sp_bstride + RT.sp_base; };

@@ -103,3 +103,29 @@ def test_without_the_mass_condition_the_derivative_is_wrong(setup):
     dY_free = np.linalg.lstsq(np.eye(N) - Jy, Ju, rcond=1e-10)[0]
     dY = implicit.periodic_state_derivative(P, ystar, u)
     assert np.max(np.abs(dY_free - dY)) > 1e-3 * np.max(np.abs(dY))
+
+
+def test_plausible_mistakes_fail_the_difference_pins(setup):
+    # each variant is one slip in writing the stacked system; every one must miss the
+    # Richardson differences of the Newton solves by far more than the pins' tolerance
+    p, P, u, ystar, solve = setup
+    Jy, Ju = implicit.year_jacobians(P, ystar, u)
+    N = ystar.size
+    w = np.tile(p.vol, ystar.shape[0])
+    w = w / np.linalg.norm(w)
+
+    def stacked(A, rhs):
+        return np.linalg.lstsq(np.vstack([A, w[None, :]]), np.vstack([rhs, np.zeros((1, rhs.shape[1]))]),
+                               rcond=None)[0]
+
+    fd = np.stack([richardson(lambda uu: solve(uu, ystar).ravel(), u, k) for k in range(u.size)], axis=1)
+    good = stacked(np.eye(N) - Jy, Ju)
+    assert np.max(np.abs(good - fd)) <= 1e-5 * np.max(np.abs(fd))
+    mutants = {
+        "transposed Jacobian": stacked(np.eye(N) - Jy.T, Ju),
+        "sign of phi_y": stacked(np.eye(N) + Jy, Ju),
+        "sign of phi_u": stacked(np.eye(N) - Jy, -Ju),
+        "phi_y without the identity": stacked(-Jy, Ju),
+    }
+    for name, dY in mutants.items():
+        assert np.max(np.abs(dY - fd)) > 1e-2 * np.max(np.abs(fd)), name
