@@ -328,6 +328,7 @@ m3d_status AdjointSweep::begin(m3d_ctx *ctx, int ckpt_every)
     }
     held = -1;
     launches = 0;
+    forward_steps = 0;
     reverse_sweeps = 0;
     return M3D_OK;
 }
@@ -354,6 +355,7 @@ static m3d_status recompute_segment(AdjointSweep &A, int seg)
                              : forward_segment(c, A.tri, A.traj, A.len, j0, ns);
     if (st != M3D_OK) return st;
     A.launches += A.stream ? 3LL * ns : 1;
+    A.forward_steps += ns;
     A.held = seg;
     return M3D_OK;
 }

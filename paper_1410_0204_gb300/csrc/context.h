@@ -129,6 +129,7 @@ struct AdjointSweep {
     long long len = 0;
     double *traj = nullptr, *chk = nullptr, *zb = nullptr, *yb = nullptr;
     long long launches = 0;             // kernel launches so far
+    long long forward_steps = 0;        // TMM steps run forward (first sweep and recomputations)
     int reverse_sweeps = 0;
     m3d_status begin(m3d_ctx *ctx, int ckpt_every);   // checks, then allocates the buffers
     m3d_status forward(const double *y0, const double *u);

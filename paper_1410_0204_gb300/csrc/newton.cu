@@ -528,6 +528,7 @@ m3d_status metos3d_periodic_gradient(m3d_ctx *c, const double *ystar, const doub
     const long long N = S.N;
     auto finish = [&](m3d_status s) {
         R.reverse_sweeps = A.reverse_sweeps;
+        R.forward_years = (double)A.forward_steps / c->nstep;
         R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (rep) *rep = R;
         A.release();
@@ -539,13 +540,7 @@ m3d_status metos3d_periodic_gradient(m3d_ctx *c, const double *ystar, const doub
     auto cu = [&](cudaError_t e) -> m3d_status {
         return e == cudaSuccess ? M3D_OK : fail(c, M3D_ERR_CUDA, "metos3d_periodic_gradient: %s", cudaGetErrorString(e));
     };
-    long long fwd_steps = 0;
-    auto count_forward = [&]() {
-        // every recomputed segment is K steps (the last one possibly fewer); the first sweep is nstep
-        R.forward_years = (double)fwd_steps / c->nstep;
-    };
     TRY(A.forward(ystar, u));
-    fwd_steps += c->nstep;
     // the zero-mass projection P x = x - (w.x / w.w) w, w = vol repeated per tracer
     double wsum = 0.0;
     TRY(S.dot_dev(c->vol, c->vol, W.scal, false, c->n));
@@ -558,13 +553,10 @@ m3d_status metos3d_periodic_gradient(m3d_ctx *c, const double *ystar, const doub
         k_sub_mass<<<S.grid, 256, 0, c->stream>>>(x, c->vol, c->n, m / wsum, N);
         return S.launch_ok();
     };
-    // segments a reverse sweep recomputes: all but the held one when the trajectory is split
-    const long long recompute_steps = A.nseg > 1 ? (long long)c->nstep - std::min(A.K, c->nstep - (A.nseg - 1) * A.K) : 0;
     // w = P (v - phi_y^T v), one reverse sweep
     const Operator adjoint_op = [&](const double *v, double, double *w) -> m3d_status {
         m3d_status s2 = A.reverse(v, W.phv, nullptr);
         if (s2 != M3D_OK) return s2;
-        fwd_steps += recompute_steps;
         s2 = S.axpby(w, 1.0, v, -1.0, W.phv);
         if (s2 != M3D_OK) return s2;
         return project(w);
@@ -587,7 +579,6 @@ m3d_status metos3d_periodic_gradient(m3d_ctx *c, const double *ystar, const doub
     R.krylov = its;
     // ubar = phi_u^T lambda; the same sweep gives phi_y^T lambda for the true residual
     TRY(A.reverse(W.x, W.phv, ubar_host));
-    fwd_steps += recompute_steps;
     TRY(S.axpby(W.w, 1.0, W.x, -1.0, W.phv));
     TRY(project(W.w));
     TRY(S.axpby(W.w, 1.0, W.F, -1.0, W.w));
@@ -595,7 +586,6 @@ m3d_status metos3d_periodic_gradient(m3d_ctx *c, const double *ystar, const doub
     TRY(S.norm(W.w, &rnorm));
     R.residual = bnorm > 0.0 ? rnorm / bnorm : 0.0;
     R.converged = est <= o.tol;
-    count_forward();
     if (lambda) TRY(cu(cudaMemcpyAsync(lambda, W.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream)));
     TRY(cu(cudaStreamSynchronize(c->stream)));
     c->last_launches = (int)std::min<long long>(A.launches, 1LL << 30);
