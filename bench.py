@@ -50,13 +50,25 @@ def peaks():
 
 # DRAM bytes (read + write) per launch of the year kernel, from one ncu capture of this
 # workload (see profiles/); None where no capture of the current kernel exists.
-# Keys: (plan, tridiagonal implicit form, per-step explicit operators).
-TRAFFIC_PER_LAUNCH = {("resident", True, True): 16971404032 + 4501760}
+# Keys: (plan, tridiagonal implicit form, per-step explicit operators, kernel revision).
+# The revision names the year kernel's code the capture was taken of; a changed kernel
+# gets a new revision and no traffic until it is captured again.
+YEAR_KERNEL_REVISION = "r2-split-phases"
+TRAFFIC_PER_LAUNCH = {}
 
-# FP64 peak: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz maximum SM clock.
-# (A DFMA throughput probe on this GPU measured 1.20 TFLOP/s, 1.92 FMA/clock/SM at the
-# clock it ran.)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 peak of the GPU per SM clock: ncu's sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained
+# on GB300 is 304 thread-level DFMA per cycle (2 per SM), i.e. 608 FP64 flops per cycle.
+FP64_FLOPS_PER_CLOCK = 304 * 2
+# Nominal: the same at the maximum SM clock, 2.07 GHz (used where no clock was sampled).
+FP64_PEAK_TFLOPS = FP64_FLOPS_PER_CLOCK * 2.07e9 / 1e12
+
+
+def fp64_peak_tflops(sm_mhz):
+    """FP64 peak at the SM clock sampled during the timed region (nominal clock if none)."""
+    if not sm_mhz:
+        return FP64_PEAK_TFLOPS, "ncu dfma peak_sustained (304/clk) x nominal 2070 MHz"
+    return FP64_FLOPS_PER_CLOCK * float(sm_mhz) * 1e6 / 1e12, \
+        "ncu dfma peak_sustained (304/clk) x sampled median SM clock %.0f MHz" % float(sm_mhz)
 
 
 # FP64 flops per cell of the source terms, per member: (euphotic cell, aphotic cell).  A division
@@ -189,13 +201,22 @@ class ClockSampler:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.index = index
+        # nvidia-smi numbers GPUs in PCI order whatever CUDA_VISIBLE_DEVICES says: select the
+        # GPU by the UUID of the CUDA device this process uses
+        self.index = str(index)
+        try:
+            import torch
+            uid = str(torch.cuda.get_device_properties(index).uuid)
+            if uid and uid != "None":
+                self.index = uid if uid.startswith(("GPU-", "MIG-")) else "GPU-" + uid
+        except Exception:
+            pass
         self.proc = None
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
@@ -353,6 +374,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         times = []
         launches = 0
+        # the year kernel's own launch, timed by the library with CUDA events on its stream
+        ctx.set_option(m3d.OPT_KERNEL_TIMING, 1)
+        kernel_s, kernel_n = 0.0, 0
         with ClockSampler(local) as clocks:
             for _ in range(args.steps):
                 flush.fill_(1.0)                       # L2 flushed between timed iterations
@@ -364,6 +388,11 @@ def run_ours(args):
                 launches += ctx.last_launch_count()
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1) / 1e3)
+                kns = ctx.get_option(m3d.OPT_LAST_KERNEL_NS)
+                if kns > 0:
+                    kernel_s += kns * 1e-9
+                    kernel_n += 1
+        ctx.set_option(m3d.OPT_KERNEL_TIMING, 0)
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
@@ -447,7 +476,7 @@ def run_ours(args):
         # Newton-Krylov periodic solve to ||phi(y) - y|| < 1e-8 from the constant initial state
         newton = {}
         if not args.no_newton:
-            modes = [("fd", m3d.JV_FD)] + ([("tangent", m3d.JV_TANGENT)] if args.newton_tangent else [])
+            modes = [("fd", m3d.JV_FD)] + ([] if args.no_newton_tangent else [("tangent", m3d.JV_TANGENT)])
             for label, jv in modes:
                 yN = torch.from_numpy(y0_h).cuda()
                 torch.cuda.synchronize()
@@ -459,7 +488,8 @@ def run_ours(args):
                                  "year_maps": rep["year_maps"], "tangent_maps": rep["tangent_maps"],
                                  "model_year_equivalents": rep["year_maps"] + rep["tangent_maps"],
                                  "krylov_per_newton_step": rep.get("krylov"), "residuals": rep.get("residuals"),
-                                 "line_search_steps": rep.get("lambdas")}
+                                 "line_search_steps": rep.get("lambdas"), "forcing_terms": rep.get("etas"),
+                                 "line_search_trials": rep.get("trials")}
         # spin-up to the Newton tolerance (the paper's comparison of Section 7), capped
         spinup = {}
         if args.spinup_years > 0:
@@ -484,10 +514,13 @@ def run_ours(args):
     bytes_step, flops_step = method_per_step(prob)
     xbytes_step, xflops_step = executed_per_step(prob, tridiagonal=tridiagonal, step_operators=step_ops)
     t_year = total / args.steps
+    t_kernel = kernel_s / max(kernel_n, 1) if kernel_n else t_year
     achieved_tf = flops_step * prob.nstep / t_year / 1e12
-    achieved_gbs = bytes_step * prob.nstep / t_year / 1e9
-    executed_tf = xflops_step * prob.nstep / t_year / 1e12
+    achieved_gbs = bytes_step * prob.nstep / t_kernel / 1e9
+    executed_tf = xflops_step * prob.nstep / t_kernel / 1e12
     clock = clocks.summary()
+    fp64_peak, fp64_src = fp64_peak_tflops(clock.get("sm_mhz"))
+    traffic = TRAFFIC_PER_LAUNCH.get((plan, tridiagonal, step_ops, YEAR_KERNEL_REVISION))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_year, "higher_is_better": True,
@@ -496,26 +529,28 @@ def run_ours(args):
                    "n": prob.n, "ncol": prob.ncol, "nnz": prob.nnz, "S_imp": prob.s_imp,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed iterations (256 MiB write); 12 months of matrices (~270 MB) exceed L2"},
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": TRAFFIC_PER_LAUNCH.get((plan, tridiagonal, step_ops)),
-                     "traffic_unit": "DRAM bytes per launch (one model year)",
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src + " (MEASURED_PEAKS hbm_gbs)"
+                     if hbm_src == "measured" else "fallback 6.8 TB/s",
+                     "traffic": traffic,
+                     "traffic_unit": "DRAM bytes per launch (one model year), ncu",
                      "kernel": {"resident": "k_year_resident (one launch per model year)",
                                 "persistent": "k_year (one launch per model year)",
                                 "graph": "k_step (one launch per TMM step)"}[plan],
-                     "plan": plan, "implicit_form": "tridiagonal" if tridiagonal else "dense",
-                     "peak_source": "FP64 units x max SM clock (152 SMs x 2 FMA/clk x 2.07 GHz)",
-                     "flops_per_step": flops_step,
-                     "executed": {"flops_per_step": xflops_step, "bytes_per_step": xbytes_step,
-                                  "achieved": executed_tf, "frac": executed_tf / FP64_PEAK_TFLOPS},
-                     "flops_note": ("achieved counts the method's flops (interpolated explicit and dense implicit "
-                                    "products of both months); the kernel executes fewer (executed): the implicit "
-                                    "part in Thomas form, and with per-step explicit operators the interpolation "
-                                    "done once per context when they are built")},
+                     "kernel_ms": 1e3 * t_kernel, "kernel_launches_timed": kernel_n,
+                     "bytes_per_step": bytes_step,
+                     "bytes_note": ("algorithmic bytes of the method per TMM step: nnz (2 x 8 + 4) + 4 (n + 1) + "
+                                    "S_imp 2 x 8 + ntr n (8 + 8), x 2880 steps per launch"),
+                     "plan": plan, "implicit_form": "tridiagonal" if tridiagonal else "dense"},
+        "fp64": {"bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak, "peak_source": fp64_src,
+                 "executed": {"flops_per_step": xflops_step, "bytes_per_step": xbytes_step,
+                              "achieved": executed_tf, "frac": executed_tf / fp64_peak},
+                 "note": ("FP64 flops the kernel executes (Thomas form of the implicit part; with per-step "
+                          "explicit operators no interpolation in the kernel) per kernel time"),
+                 "method_flops_per_step": flops_step},
+        "dram_measured": ({"gbs": traffic / t_kernel / 1e9, "frac": traffic / t_kernel / 1e9 / hbm_peak,
+                           "note": "ncu DRAM bytes of one launch / kernel time"} if traffic else None),
         "step_operators": stepops,
-        "hbm_roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src,
-                         "bytes_per_step": bytes_step, "flops_per_step": flops_step},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(y0_h.nbytes + u_h.nbytes),
                 "d2h_bytes_per_step": int(y0_h.nbytes)},
         "throughput": {"cell_tracer_steps_per_s": value * prob.n * 2 * prob.nstep,
@@ -685,8 +720,8 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched ensemble timing")
     ap.add_argument("--spinup-years", type=int, default=0,
                     help="also time a spin-up of up to this many years to ||phi(y) - y|| < 1e-8 (e.g. 3000)")
-    ap.add_argument("--newton-tangent", action="store_true",
-                    help="also time Newton-Krylov with tangent Jacobian-vector products")
+    ap.add_argument("--no-newton-tangent", action="store_true",
+                    help="skip the Newton-Krylov solve with tangent Jacobian-vector products")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run this many single TMM steps of the workload (for profilers)")
     ap.add_argument("--profile-ensemble-steps", type=int, default=0,

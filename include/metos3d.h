@@ -272,6 +272,10 @@ m3d_status metos3d_sync(m3d_ctx *ctx);
  *       (synchronous; M3D_ERR_CUDA if the allocation fails, M3D_ERR_UNSUPPORTED without the
  *       resident plan); 0 frees it.  The derivative sweeps use it for their forward parts.
  *   M3D_OPT_STEP_OPERATOR_BYTES (read only): bytes held by the per-step operators (0 if none).
+ *   M3D_OPT_KERNEL_TIMING: 1 records CUDA events on the context's stream around every launch
+ *       of the year kernel (resident and persistent plans), default 0.
+ *   M3D_OPT_LAST_KERNEL_NS (read only): device time of the last year-kernel launch timed that
+ *       way, in nanoseconds; -1 if none was timed or it has not completed (synchronize first).
  * metos3d_get_option returns -1 for an unknown option.
  */
 enum {
@@ -282,7 +286,9 @@ enum {
     M3D_OPT_IMPLICIT_FORM = 5,
     M3D_OPT_ADJOINT_PLAN = 6,
     M3D_OPT_STEP_OPERATORS = 7,
-    M3D_OPT_STEP_OPERATOR_BYTES = 8
+    M3D_OPT_STEP_OPERATOR_BYTES = 8,
+    M3D_OPT_KERNEL_TIMING = 9,
+    M3D_OPT_LAST_KERNEL_NS = 10
 };
 enum { M3D_IMPLICIT_DENSE = 0, M3D_IMPLICIT_TRIDIAGONAL = 1 };
 enum { M3D_PLAN_PERSISTENT = 0, M3D_PLAN_GRAPH = 1, M3D_PLAN_RESIDENT = 2 };
@@ -300,8 +306,10 @@ m3d_status metos3d_spinup(m3d_ctx *ctx, double *y, const double *u, int nyears, 
 
 /*
  * Matrix-free Newton-Krylov periodic solve (Sections 6 and 7): Newton's method on
- * F(y) = y - phi(y) = 0, globalised by a backtracking line search with cubic interpolation
- * (Armijo constant 1e-4, steps kept in [0.1, 0.5] of the previous one); each Newton system
+ * F(y) = y - phi(y) = 0, globalised by a backtracking line search on f = |F|^2 / 2 with
+ * quadratic (first backtrack) and cubic (later ones) interpolation (Armijo constant 1e-4,
+ * steps kept in [0.1, 0.5] of the previous one; the slope of f along the step s is
+ * F.J s = -(|F|^2 - rho^2), rho the GMRES residual of the step); each Newton system
  * (I - phi'(y)) s = -F(y) is solved by restarted GMRES with modified Gram-Schmidt
  * orthogonalisation to the Eisenstat-Walker tolerance (choice 2: eta_0 = 0.3,
  * gamma = 0.9, alpha = (1+sqrt 5)/2, safeguarded, kept within [0.5 tol/||F||, 0.9]).
@@ -313,7 +321,9 @@ m3d_status metos3d_spinup(m3d_ctx *ctx, double *y, const double *u, int nyears, 
  * y: device [ntracer][n], initial guess on entry and solution on exit; u: device [nparam];
  * opts NULL for the defaults (metos3d_newton_default_options); report may be NULL.
  * Returns M3D_NOT_CONVERGED (with the report filled in) if the tolerance is not met.
- * Synchronous; allocates its Krylov basis ((restart + 11) state vectors) for the call.
+ * Synchronous; allocates its Krylov basis ((restart + 11) state vectors) for the call.  The
+ * Krylov iterations run on the device (rotations and convergence test included); the host
+ * reads their status one iteration late, so the GPU is never left waiting for it.
  */
 enum { M3D_JV_FD = 0, M3D_JV_TANGENT = 1 };
 typedef struct {
@@ -327,6 +337,7 @@ typedef struct {
 } m3d_newton_opts;
 
 #define M3D_NEWTON_MAX_HIST 64
+#define M3D_NEWTON_MAX_TRIALS 512
 typedef struct {
     int converged;
     int newton_steps;
@@ -336,7 +347,12 @@ typedef struct {
     double residual0, residual; /* ||F|| at the start and at the end */
     double residuals[M3D_NEWTON_MAX_HIST];   /* ||F|| after each Newton step ([0]: initial) */
     int krylov[M3D_NEWTON_MAX_HIST];         /* GMRES iterations of each Newton step */
-    double lambdas[M3D_NEWTON_MAX_HIST];     /* line-search step of each Newton step */
+    double lambdas[M3D_NEWTON_MAX_HIST];     /* accepted line-search step of each Newton step */
+    double etas[M3D_NEWTON_MAX_HIST];        /* forcing term (GMRES tolerance) of each Newton step */
+    double slopes[M3D_NEWTON_MAX_HIST];      /* slope of |F|^2 / 2 along each Newton step */
+    int trials[M3D_NEWTON_MAX_HIST];         /* line-search trials of each Newton step */
+    int ntrial;                              /* entries of trial_lambdas */
+    double trial_lambdas[M3D_NEWTON_MAX_TRIALS];  /* every step length tried, in order */
     double seconds;
 } m3d_newton_report;
 

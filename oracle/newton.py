@@ -92,93 +92,169 @@ def gmres_mgs(apply_J, b, tol_rel, restart, maxit):
             return x, it, beta / bnorm
 
 
-def newton_krylov(P, y0, u, tol=1e-8, max_newton=40, restart=200, max_krylov=200, fd_eps=1e-8,
-                  model=MODEL_NDOP, nsub=1, jv=None):
-    """Newton-Krylov periodic solve; returns (y, report dict).
+GOLDEN = (1.0 + math.sqrt(5.0)) / 2.0
 
-    Forcing terms (Eisenstat & Walker, choice 2): eta_0 = 0.3, then
-    eta_k = 0.9 (||F_k|| / ||F_{k-1}||)^((1+sqrt 5)/2), safeguarded by 0.9 eta_{k-1}^((1+sqrt 5)/2)
-    when that exceeds 0.1, and kept in [0.5 tol / ||F_k||, 0.9].
-    Jacobian-vector products: J v = v - (phi(y + h v) - phi(y)) / h, h = fd_eps ||y|| / ||v||,
-    unless a function jv(y, phi_y, v) returning phi'(y) v is given.
-    Line search: Armijo condition f(y + l s) <= f(y) + 1e-4 l f'(0) on f = ||F||^2 / 2 with
-    f'(0) = -||F||^2, starting at l = 1, then quadratic and cubic backtracking with
-    l in [0.1 l_prev, 0.5 l_prev] (Dennis & Schnabel).
-    Mass: phi conserves sum_i vol_i y_i, so I - phi'(y) is singular and the periodic
-    solution is unique only for a given total mass.  Every Newton step s is projected onto
-    the zero-mass directions, s <- s - (w.s / w.w) w with w = vol repeated per tracer,
-    which removes the rounding drift of the finite-difference products.
+
+def forcing_term(r, r_prev, eta_prev, tol, eta0=0.3, gamma=0.9, alpha=GOLDEN, eta_max=0.9):
+    """Inner tolerance of the next Newton step (Eisenstat & Walker 1996, choice 2).
+
+    First step: eta_0.  Later steps: gamma (||F_k|| / ||F_{k-1}||)^alpha, raised to the
+    safeguard gamma eta_{k-1}^alpha when the safeguard exceeds 0.1 (so that eta does not
+    drop sharply after one lucky step).  Finally kept within [0.5 tol / ||F_k||, eta_max]:
+    no oversolving of the last step and never a useless tolerance near 1.
+    """
+    if eta_prev is None:
+        eta = eta0
+    else:
+        eta = gamma * (r / r_prev) ** alpha
+        safe = gamma * eta_prev ** alpha
+        if safe > 0.1:
+            eta = max(eta, safe)
+    return min(max(eta, 0.5 * tol / r), eta_max)
+
+
+def quadratic_backtrack(f0, slope, lam, f_lam):
+    """Minimiser of the quadratic model m(x) = f0 + slope x + c x^2 fitted to m(lam) = f_lam
+    (Dennis & Schnabel, Section 6.3.2: the first backtrack)."""
+    return -slope * lam * lam / (2.0 * (f_lam - f0 - slope * lam))
+
+
+def cubic_backtrack(f0, slope, lam, f_lam, lam_prev, f_prev):
+    """Local minimiser of the cubic model m(x) = f0 + slope x + b x^2 + a x^3 fitted to the last
+    two trials, m(lam) = f_lam and m(lam_prev) = f_prev (Dennis & Schnabel, Section 6.3.2: every
+    later backtrack).  m'(x) = slope + 2 b x + 3 a x^2 = 0 at x = (-b + sqrt(b^2 - 3 a slope)) / (3 a);
+    with a = 0 the model is the quadratic and x = -slope / (2 b)."""
+    r1 = f_lam - f0 - lam * slope
+    r2 = f_prev - f0 - lam_prev * slope
+    den = lam - lam_prev
+    a = (r1 / (lam * lam) - r2 / (lam_prev * lam_prev)) / den
+    b = (-lam_prev * r1 / (lam * lam) + lam * r2 / (lam_prev * lam_prev)) / den
+    if a == 0.0:
+        return -slope / (2.0 * b)
+    disc = max(b * b - 3.0 * a * slope, 0.0)
+    return (-b + math.sqrt(disc)) / (3.0 * a)
+
+
+def line_search(f, f0, slope, armijo=1e-4, lam_min=1e-4, lo=0.1, hi=0.5):
+    """Backtracking line search along a descent direction of f, with f(0) = f0, f'(0) = slope < 0.
+
+    Tries lam = 1 first and accepts the first lam with the Armijo decrease
+    f(lam) <= f0 + armijo lam slope (or lam below lam_min).  After a failed trial the next lam
+    is the minimiser of the quadratic model (first backtrack) or of the cubic model through
+    the last two trials (later backtracks), kept within [lo, hi] times the failed lam.
+    Returns (lam, f(lam), trials), trials the list of (lam, f(lam)) in the order tried.
+    """
+    lam, prev, trials = 1.0, None, []
+    while True:
+        fl = f(lam)
+        trials.append((lam, fl))
+        if fl <= f0 + armijo * lam * slope or lam < lam_min:
+            return lam, fl, trials
+        if prev is None:
+            lt = quadratic_backtrack(f0, slope, lam, fl)
+        else:
+            lt = cubic_backtrack(f0, slope, lam, fl, prev[0], prev[1])
+        prev = (lam, fl)
+        lam = min(max(lt, lo * lam), hi * lam)
+
+
+def newton_krylov(P, y0, u, tol=1e-8, max_newton=40, restart=200, max_krylov=200, fd_eps=1e-8,
+                  model=MODEL_NDOP, nsub=1, jv=None, record_steps=False):
+    """Newton-Krylov periodic solve of the year map of P; returns (y, report dict).
+
+    phi conserves sum_i vol_i y_i, so I - phi'(y) is singular and the periodic solution is
+    unique only for a given total mass: the Newton steps are projected on the zero-mass
+    directions (w = vol repeated per tracer), see newton_solve.
     """
     shape = np.shape(y0)
-    y = np.array(y0, dtype=np.float64).ravel()
     wmass = np.tile(np.asarray(P.prob.vol, dtype=np.float64), shape[0])
 
     def phi(v):
         return year_map(P, v.reshape(shape), u, model=model, nsub=nsub).ravel()
 
+    jvf = None
+    if jv is not None:
+        def jvf(y, py, v):
+            return jv(y.reshape(shape), py.reshape(shape), v.reshape(shape)).ravel()
+    y, rep = newton_solve(phi, np.asarray(y0, dtype=np.float64).ravel(), tol=tol, max_newton=max_newton,
+                          restart=restart, max_krylov=max_krylov, fd_eps=fd_eps, jv=jvf, wmass=wmass,
+                          record_steps=record_steps)
+    return y.reshape(shape), rep
+
+
+def newton_solve(phi, y0, tol=1e-8, max_newton=40, restart=200, max_krylov=200, fd_eps=1e-8, jv=None,
+                 wmass=None, record_steps=False):
+    """Newton's method on F(y) = y - phi(y) = 0 for a map phi of flat vectors; returns (y, report).
+
+    Forcing terms: forcing_term (Eisenstat & Walker, choice 2); each Newton system
+    (I - phi'(y)) s = -F(y) solved by gmres_mgs to that tolerance.  Jacobian-vector products:
+    J v = v - (phi(y + h v) - phi(y)) / h, h = fd_eps ||y|| / ||v||, unless a function
+    jv(y, phi_y, v) returning phi'(y) v is given.  wmass (optional): every step s is projected
+    on the directions orthogonal to it, s <- s - (w.s / w.w) w (for the year map, w = vol
+    repeated per tracer: the mass it conserves; the projection removes the rounding drift of
+    the finite-difference products).  Line search: line_search on f(lam) = ||F(y + lam s)||^2 / 2,
+    whose slope at 0 is F^T J s.  GMRES's step s minimises ||F + J s|| over its Krylov space,
+    so its residual rho = ||F + J s|| is orthogonal to J s and F^T J s = -(||F||^2 - rho^2) (in one
+    GMRES cycle, which restart >= max_krylov gives): the inexact step's own slope, not the
+    -||F||^2 of an exact Newton step (with eta up to 0.9 the two differ by a factor up to 5).
+    The report holds, per Newton step, eta, the GMRES iterations and residual rho, the slope,
+    the accepted lam and every lam tried; with record_steps, also the steps s and the states
+    y they start from.
+    """
+    y = np.array(y0, dtype=np.float64)
     py = phi(y)
     F = y - py
     r = float(np.linalg.norm(F))
-    rep = {"residuals": [r], "krylov": [], "year_maps": 1, "lambdas": [], "converged": False}
-    gamma, alpha = 0.9, (1.0 + math.sqrt(5.0)) / 2.0
+    rep = {"residuals": [r], "krylov": [], "year_maps": 1, "lambdas": [], "etas": [], "slopes": [],
+           "gmres_residuals": [], "trials": [], "converged": False}
+    if record_steps:
+        rep["steps"], rep["states"] = [], []
     eta_prev, r_prev = None, None
     for _ in range(max_newton):
         if r <= tol:
             rep["converged"] = True
             break
-        if eta_prev is None:
-            eta = 0.3
-        else:
-            eta = gamma * (r / r_prev) ** alpha
-            safe = gamma * eta_prev ** alpha
-            if safe > 0.1:
-                eta = max(eta, safe)
-        eta = min(max(eta, 0.5 * tol / r), 0.9)
+        eta = forcing_term(r, r_prev, eta_prev, tol)
         ynorm = float(np.linalg.norm(y))
 
         def apply_J(v):
             if jv is not None:
-                return v - jv(y.reshape(shape), py.reshape(shape), v.reshape(shape)).ravel()
+                return v - jv(y, py, v)
             h = fd_eps * ynorm / float(np.linalg.norm(v))
             rep["year_maps"] += 1
             return v - (phi(y + h * v) - py) / h
 
         nfd = rep["year_maps"]
-        s, its, _ = gmres_mgs(apply_J, -F, eta, restart, max_krylov)
-        s = s - (float(np.dot(wmass, s)) / float(np.dot(wmass, wmass))) * wmass
-        rep["krylov"].append(its)
+        s, its, res_rel = gmres_mgs(apply_J, -F, eta, restart, max_krylov)
+        if wmass is not None:
+            s = s - (float(np.dot(wmass, s)) / float(np.dot(wmass, wmass))) * wmass
         if jv is not None:
             rep["year_maps"] = nfd + 2 * its         # a tangent year map costs about two
-        f0 = 0.5 * r * r
-        slope = -r * r
-        lam, lam_prev, f_prev = 1.0, None, None
-        while True:
-            yn = y + lam * s
-            pyn = phi(yn)
+        rho = res_rel * r
+        slope = -(r * r - rho * rho)
+        cache = {}
+
+        def f(lam):
+            cache[lam] = phi(y + lam * s)
             rep["year_maps"] += 1
-            Fn = yn - pyn
-            fn = 0.5 * float(np.dot(Fn, Fn))
-            if fn <= f0 + 1e-4 * lam * slope or lam < 1e-4:
-                break
-            if lam_prev is None:
-                lt = -slope / (2.0 * (fn - f0 - slope))
-            else:
-                a1 = fn - f0 - lam * slope
-                a2 = f_prev - f0 - lam_prev * slope
-                den = lam - lam_prev
-                a = (a1 / (lam * lam) - a2 / (lam_prev * lam_prev)) / den
-                b = (-lam_prev * a1 / (lam * lam) + lam * a2 / (lam_prev * lam_prev)) / den
-                if a == 0.0:
-                    lt = -slope / (2.0 * b)
-                else:
-                    disc = max(b * b - 3.0 * a * slope, 0.0)
-                    lt = (-b + math.sqrt(disc)) / (3.0 * a)
-            lam_prev, f_prev = lam, fn
-            lam = min(max(lt, 0.1 * lam), 0.5 * lam)
+            Fl = y + lam * s - cache[lam]
+            return 0.5 * float(np.dot(Fl, Fl))
+
+        lam, fn, trials = line_search(f, 0.5 * r * r, slope)
+        if record_steps:
+            rep["steps"].append(s.copy())
+            rep["states"].append(y.copy())
+        yn = y + lam * s
+        pyn = cache[lam]
+        rep["krylov"].append(its)
+        rep["etas"].append(eta)
+        rep["gmres_residuals"].append(rho)
+        rep["slopes"].append(slope)
         rep["lambdas"].append(lam)
-        y, py, F = yn, pyn, Fn
+        rep["trials"].append([t[0] for t in trials])
+        y, py, F = yn, pyn, yn - pyn
         r_prev, eta_prev = r, eta
         r = math.sqrt(2.0 * fn)
         rep["residuals"].append(r)
     rep["converged"] = r <= tol
-    return y.reshape(shape), rep
+    return y, rep

@@ -31,6 +31,8 @@ OPT_IMPLICIT_FORM = 5
 OPT_ADJOINT_PLAN = 6
 OPT_STEP_OPERATORS = 7
 OPT_STEP_OPERATOR_BYTES = 8
+OPT_KERNEL_TIMING = 9
+OPT_LAST_KERNEL_NS = 10
 IMPLICIT_DENSE = 0
 IMPLICIT_TRIDIAGONAL = 1
 PLAN_PERSISTENT = 0
@@ -71,6 +73,7 @@ class NewtonOptions(C.Structure):
 
 
 NEWTON_MAX_HIST = 64
+NEWTON_MAX_TRIALS = 512
 
 
 class NewtonReport(C.Structure):
@@ -78,14 +81,24 @@ class NewtonReport(C.Structure):
                 ("year_maps", C.c_int), ("tangent_maps", C.c_int), ("residual0", C.c_double),
                 ("residual", C.c_double), ("residuals", C.c_double * NEWTON_MAX_HIST),
                 ("krylov", C.c_int * NEWTON_MAX_HIST), ("lambdas", C.c_double * NEWTON_MAX_HIST),
-                ("seconds", C.c_double)]
+                ("etas", C.c_double * NEWTON_MAX_HIST), ("slopes", C.c_double * NEWTON_MAX_HIST),
+                ("trials", C.c_int * NEWTON_MAX_HIST), ("ntrial", C.c_int),
+                ("trial_lambdas", C.c_double * NEWTON_MAX_TRIALS), ("seconds", C.c_double)]
 
     def to_dict(self):
         k = self.newton_steps
+        kk = min(k, NEWTON_MAX_HIST)
+        flat = list(self.trial_lambdas[:self.ntrial])
+        per_step, at = [], 0
+        for cnt in self.trials[:kk]:
+            per_step.append(flat[at:at + cnt])
+            at += cnt
         return {"converged": bool(self.converged), "newton_steps": k, "krylov_total": self.krylov_total,
                 "year_maps": self.year_maps, "tangent_maps": self.tangent_maps, "residual0": self.residual0,
                 "residual": self.residual, "residuals": list(self.residuals[:k + 1]),
-                "krylov": list(self.krylov[:k]), "lambdas": list(self.lambdas[:k]), "seconds": self.seconds}
+                "krylov": list(self.krylov[:kk]), "lambdas": list(self.lambdas[:kk]),
+                "etas": list(self.etas[:kk]), "slopes": list(self.slopes[:kk]), "trials": per_step,
+                "seconds": self.seconds}
 
 
 JV_FD = 0

@@ -84,6 +84,8 @@ struct m3d_ctx {
     cudaGraphExec_t year_graph = nullptr;
     int year_result_buf = 0;
     long long last_launches = 0;
+    cudaEvent_t kev[2] = {nullptr, nullptr};   // around the last year-kernel launch (M3D_OPT_KERNEL_TIMING)
+    int time_kernel = 0, kev_recorded = 0;
     std::string err;
     // models only ensembles run (N, PO4-DOP-PHY, NPZD-DOP): a one-member ensemble does the steps
     m3d_ensemble *ens = nullptr;

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(m3d::kThreads, 1) k_year(StepParams P, m3d::Sy
                                                         double *buf1, int j0, int nsteps)
 {
     extern __shared__ double smem[];
+    if (S.skip && *(volatile const int *)S.skip) return;
     m3d::year_persistent<NTR, MODEL>(P, S, buf0, buf1, j0, nsteps, smem);
 }
 
@@ -45,6 +46,7 @@ __global__ void __launch_bounds__(m3d::kThreads, 1) k_year_resident(StepParams P
                                                                  m3d::SyncParams S, double *base, long long stride,
                                                                  int period, int j0, int nsteps)
 {
+    if (S.skip && *(volatile const int *)S.skip) return;
     m3d::year_resident<NTR, MODEL, TRI>(P, R, S, base, stride, period, j0, nsteps);
 }
 
@@ -627,6 +629,8 @@ void metos3d_free(m3d_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     release(ctx);
+    for (cudaEvent_t e : ctx->kev)
+        if (e) cudaEventDestroy(e);
     if (ctx->ens) metos3d_ensemble_free(ctx->ens);
     cudaSetDevice(prev);
     delete ctx;
@@ -1247,8 +1251,13 @@ m3d_status launch_year_persistent(m3d_ctx *c, year_kernel_t kernel, size_t smem,
     m3d::SyncParams S = c->S;
     double *b0 = c->ybuf[0], *b1 = c->ybuf[1];
     void *args[] = {&P, &S, &b0, &b1, &j0, &nsteps};
+    if (c->time_kernel) CUDA_OR_FAIL(c, cudaEventRecord(c->kev[0], c->stream));
     CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)kernel, dim3(c->ntiles), dim3(m3d::kThreads), args, smem,
                                                 c->stream));
+    if (c->time_kernel) {
+        CUDA_OR_FAIL(c, cudaEventRecord(c->kev[1], c->stream));
+        c->kev_recorded = 1;
+    }
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
     return M3D_OK;
 }
@@ -1305,9 +1314,14 @@ m3d_status run_year_from_ybuf(m3d_ctx *c, double *out, cudaMemcpyKind kind)
         int period = 2, j0 = 0, nsteps = c->nstep;
         void *args[] = {&P, &R, &S, &b0, &stride, &period, &j0, &nsteps};
         const bool tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && c->tri_resident_ok;
+        if (c->time_kernel) CUDA_OR_FAIL(c, cudaEventRecord(c->kev[0], c->stream));
         CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)(tri ? c->rk.year_tri : c->rk.year), dim3(c->ntiles),
                                                     dim3(m3d::kThreads), args,
                                                     tri ? c->resident_tri_smem : c->resident_smem, c->stream));
+        if (c->time_kernel) {
+            CUDA_OR_FAIL(c, cudaEventRecord(c->kev[1], c->stream));
+            c->kev_recorded = 1;
+        }
         CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost,
                                         c->stream));
         double *res = (nsteps & 1) ? b1 : b0;
@@ -1471,9 +1485,11 @@ m3d_status metos3d_sync(m3d_ctx *c)
     if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_sync: null context");
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     if (c->status_host[0] != 0) {
-        int tile = c->status_host[1], step = c->status_host[2];
+        int tile = c->status_host[1], step = c->status_host[2], copy = c->status_host[3];
         c->status_host[0] = 0;
-        return fail(c, M3D_ERR_TIMEOUT, "year map: tile %d gave up waiting for its neighbours at step %d", tile, step);
+        c->status_host[3] = 0;
+        return fail(c, M3D_ERR_TIMEOUT, "year map: tile %d gave up waiting for its neighbours at step %d%s", tile, step,
+                    copy ? " (and its own operator copy did not land within the bound)" : "");
     }
     return M3D_OK;
 }
@@ -1521,6 +1537,12 @@ m3d_status metos3d_set_option(m3d_ctx *c, int option, long long value)
         if (value == 1 && !c->resident_ok)
             return fail(c, M3D_ERR_UNSUPPORTED, "per-step operators serve the resident year kernel only");
         return set_step_operators(c, value == 1);
+    case M3D_OPT_KERNEL_TIMING:
+        if (value != 0 && value != 1) return fail(c, M3D_ERR_ARG, "kernel timing: 0 or 1");
+        for (int i = 0; i < 2 && value == 1; i++)
+            if (!c->kev[i]) CUDA_OR_FAIL(c, cudaEventCreate(&c->kev[i]));
+        c->time_kernel = (int)value;
+        return M3D_OK;
     case M3D_OPT_ADJOINT_PLAN:
         if (value == M3D_PLAN_PERSISTENT && !c->adj_stream_ok)
             return fail(c, M3D_ERR_UNSUPPORTED, "the streaming adjoint sweep does not fit on this GPU");
@@ -1545,6 +1567,12 @@ long long metos3d_get_option(const m3d_ctx *c, int option)
     case M3D_OPT_IMPLICIT_FORM: return c->implicit_form;
     case M3D_OPT_STEP_OPERATORS: return c->sp_b != nullptr ? 1 : 0;
     case M3D_OPT_STEP_OPERATOR_BYTES: return (long long)c->sp_b_bytes;
+    case M3D_OPT_KERNEL_TIMING: return c->time_kernel;
+    case M3D_OPT_LAST_KERNEL_NS: {
+        float ms = 0.0f;
+        if (!c->kev_recorded || cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]) != cudaSuccess) return -1;
+        return (long long)((double)ms * 1e6);
+    }
     case M3D_OPT_ADJOINT_PLAN:
         if (c->adj_stream_ok && (!c->adj_ok || c->adj_force_stream)) return M3D_PLAN_PERSISTENT;
         return c->adj_ok ? M3D_PLAN_RESIDENT : -1;

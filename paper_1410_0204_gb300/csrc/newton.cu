@@ -5,9 +5,10 @@
 // search with cubic interpolation; each Newton system (I - phi'(y)) s = -F(y) is solved
 // inexactly by restarted GMRES with modified Gram-Schmidt orthogonalisation, with the
 // inner tolerances of Eisenstat and Walker.  The Jacobian-vector products are finite
-// differences of the year map.  All vectors stay on the device; the Gram-Schmidt
-// coefficients are computed and applied on the device, and the host reads one column of
-// the Hessenberg matrix per Krylov iteration to update its Givens rotations.
+// differences of the year map or the tangent year map.  All vectors stay on the device, and
+// so does the Krylov loop: the Gram-Schmidt coefficients, the Givens rotations of the
+// Hessenberg matrix and the convergence test are kernels, and the host reads a small status
+// record per iteration one iteration late, while the next one is already queued.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -95,6 +96,21 @@ __global__ void k_sub_mass(double *s, const double *vol, int n, double c, long l
         s[i] = fma(-c, vol[i % n], s[i]);
 }
 
+// ---- GMRES cycle state on the device.  The host enqueues the Krylov iterations of a cycle
+// without reading anything back: the Hessenberg column, its Givens rotation and the
+// convergence test are all evaluated by kernels, and the host learns the outcome of
+// iteration k only while iteration k+1 is already queued (a pinned copy of this struct
+// behind an event).  Once `done` is set, the year-map kernels of the iterations still in the
+// queue return at once (SyncParams::skip) and the Givens kernel ignores them.
+struct KrylovStatus {
+    int done;                   // converged, broken down, or out of iterations
+    int k_used;                 // Krylov vectors of the cycle's solution
+    int iters;                  // iterations over all cycles of the solve
+    int maxit;
+    double tol_abs;             // tol_rel ||b||
+    double res;                 // |g[k_used]|, the cycle's residual norm estimate
+};
+
 struct Workspace {
     int m = 0;
     long long N = 0;
@@ -103,6 +119,10 @@ struct Workspace {
     double *yn = nullptr, *pyn = nullptr, *tmp = nullptr, *phv = nullptr, *x = nullptr;
     double *H = nullptr;        // [m+1][m] column-major Hessenberg (device)
     double *part = nullptr, *scal = nullptr;
+    double *g = nullptr, *cs = nullptr, *sn = nullptr, *yk = nullptr;   // [m+1], [m], [m], [m] (device)
+    KrylovStatus *kst = nullptr;              // device
+    KrylovStatus *kst_host = nullptr;         // pinned, three slots
+    cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 
 struct Solver {
@@ -111,7 +131,7 @@ struct Solver {
     long long N;
     int grid;
     bool tangent = false;           // Jacobian-vector products by the tangent year map
-    int *tangent_maps = nullptr;
+    int applies = 0;                // operator applications a GMRES call carried out
 
     m3d_status launch_ok() { CUDA_OR_FAIL(c, cudaGetLastError()); return M3D_OK; }
 
@@ -166,7 +186,6 @@ m3d_status apply_jacobian(Solver &S, const double *y, const double *py, double y
                           const double *v, double vnorm, double *w, int *year_maps)
 {
     if (S.tangent) {
-        (*S.tangent_maps)++;
         m3d_status st = m3d_year_tangent_device(S.c, y, v, S.W.phv, S.W.tmp);
         if (st != M3D_OK) return st;
         k_axpby<<<S.grid, 256, 0, S.c->stream>>>(w, 1.0, v, -1.0, S.W.tmp, S.N);
@@ -185,10 +204,87 @@ m3d_status apply_jacobian(Solver &S, const double *y, const double *py, double y
 // w = A v for a vector v of norm vnorm (the operator of a Krylov solve).
 using Operator = std::function<m3d_status(const double *v, double vnorm, double *w)>;
 
-// Restarted GMRES(m) with modified Gram-Schmidt for A x = b, x0 = 0.  res_rel (may be null)
-// receives the last residual estimate relative to ||b||.
+// Start a cycle from the residual of norm *beta (device): g = beta e_1.
+__global__ void k_krylov_begin(KrylovStatus *st, const double *beta, double *g, int m)
+{
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = (i == 0) ? beta[0] : 0.0;
+    if (threadIdx.x == 0) {
+        st->done = 0;
+        st->k_used = 0;
+        st->res = beta[0];
+    }
+}
+
+// out = in / den[0] (zero when den[0] is not positive: a breakdown, which ends the cycle)
+__global__ void k_scale_inv(double *out, const double *in, const double *den, long long len)
+{
+    const double d = den[0];
+    const double s = d > 0.0 ? 1.0 / d : 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+        out[i] = s * in[i];
+}
+
+// Column k of the Hessenberg matrix (h[0..k+1], column-major with leading dimension m+1):
+// apply the cycle's previous rotations, form the rotation that zeroes h[k+1], rotate the
+// right-hand side g, and decide whether the cycle is done.  One thread.
+__global__ void k_givens(double *H, int m, int k, double *cs, double *sn, double *g, KrylovStatus *st)
+{
+    if (threadIdx.x != 0 || st->done) return;
+    double *h = H + (size_t)k * (m + 1);
+    for (int i = 0; i < k; i++) {
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    const double d = hypot(h[k], h[k + 1]);
+    if (d == 0.0) {
+        cs[k] = 1.0;
+        sn[k] = 0.0;
+    } else {
+        cs[k] = h[k] / d;
+        sn[k] = h[k + 1] / d;
+    }
+    h[k] = d;
+    h[k + 1] = 0.0;
+    g[k + 1] = -sn[k] * g[k];
+    g[k] = cs[k] * g[k];
+    st->iters += 1;
+    st->k_used = k + 1;
+    st->res = fabs(g[k + 1]);
+    if (st->res <= st->tol_abs || st->iters >= st->maxit || d == 0.0 || k + 1 == m) st->done = 1;
+}
+
+// The cycle's correction: back substitution R y = g on the k_used leading columns, then
+// x += V y.  One block; the triangular solve on thread 0, the sum over the basis by all.
+__global__ void k_krylov_solution(const double *H, int m, const double *g, const KrylovStatus *st, double *yk)
+{
+    if (threadIdx.x != 0) return;
+    const int ku = st->k_used;
+    for (int i = ku - 1; i >= 0; i--) {
+        double s = g[i];
+        for (int j = i + 1; j < ku; j++) s -= H[(size_t)j * (m + 1) + i] * yk[j];
+        const double dii = H[(size_t)i * (m + 1) + i];
+        yk[i] = dii != 0.0 ? s / dii : 0.0;
+    }
+}
+
+__global__ void k_add_basis(double *x, const double *V, const double *yk, const KrylovStatus *st, long long N)
+{
+    const int ku = st->k_used;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        double s = x[i];
+        for (int j = 0; j < ku; j++) s = fma(yk[j], V[(size_t)j * N + i], s);
+        x[i] = s;
+    }
+}
+
+// Restarted GMRES(m) with modified Gram-Schmidt for A x = b, x0 = 0, iterations and
+// rotations on the device.  res_rel (may be null) receives the last residual estimate
+// relative to ||b||.  With lag = 1 the host checks iteration k's status only after it has
+// queued iteration k+1 (the operator's year-map kernels must honour SyncParams::skip);
+// lag = 0 waits for each iteration's status before queuing the next.
 m3d_status gmres(Solver &S, const Operator &apply, const double *b, double *x, double tol_rel, int maxit, int *iters,
-                 double *res_rel = nullptr)
+                 double *res_rel = nullptr, int lag = 1)
 {
     m3d_ctx *c = S.c;
     Workspace &W = S.W;
@@ -199,88 +295,118 @@ m3d_status gmres(Solver &S, const Operator &apply, const double *b, double *x, d
     m3d_status st = S.norm(b, &bnorm);
     if (st != M3D_OK) return st;
     *iters = 0;
+    S.applies = 0;
     if (res_rel) *res_rel = 0.0;
     if (bnorm == 0.0) return M3D_OK;
+    KrylovStatus init{0, 0, 0, maxit, tol_rel * bnorm, bnorm};
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(W.kst, &init, sizeof init, cudaMemcpyHostToDevice, c->stream));
     double *r = W.w;                               // the first residual is b itself
-    double beta = bnorm;
-    st = S.axpby(W.V, 1.0 / beta, b, 0.0, b);
-    if (st != M3D_OK) return st;
-    std::vector<double> Hh((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), col(m + 1), yk(m);
+    const double *rv = b;
+    double *beta_dev = W.scal + 1;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(beta_dev, W.scal, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    const int *saved_skip = c->S.skip;
+    c->S.skip = lag ? &W.kst->done : nullptr;
+    auto restore = [&](m3d_status s2) { c->S.skip = saved_skip; return s2; };
+    KrylovStatus host{};
     while (true) {
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int k_used = 0;
-        bool done = false;
-        for (int k = 0; k < m; k++) {
+        k_krylov_begin<<<1, 256, 0, c->stream>>>(W.kst, beta_dev, W.g, m);
+        k_scale_inv<<<S.grid, 256, 0, c->stream>>>(W.V, rv, beta_dev, N);
+        st = S.launch_ok();
+        if (st != M3D_OK) return restore(st);
+        int queued = 0;
+        for (int k = 0; k < m && *iters + queued < maxit; k++) {
             double *vk = W.V + (size_t)k * N;
             double *hk = W.H + (size_t)k * (m + 1);
             st = apply(vk, 1.0, W.w);
-            if (st != M3D_OK) return st;
+            if (st != M3D_OK) return restore(st);
             for (int i = 0; i <= k; i++) {            // modified Gram-Schmidt, coefficients on the device
                 const double *vi = W.V + (size_t)i * N;
                 st = S.dot_dev(W.w, vi, hk + i, false);
-                if (st != M3D_OK) return st;
+                if (st != M3D_OK) return restore(st);
                 k_sub_scaled<<<S.grid, 256, 0, c->stream>>>(W.w, vi, hk + i, N);
-                st = S.launch_ok();
-                if (st != M3D_OK) return st;
             }
             st = S.dot_dev(W.w, W.w, hk + k + 1, true);
-            if (st != M3D_OK) return st;
-            st = S.read(hk, col.data(), k + 2);
-            if (st != M3D_OK) return st;
-            if (col[k + 1] > 0.0) {
-                st = S.axpby(W.V + (size_t)(k + 1) * N, 1.0 / col[k + 1], W.w, 0.0, W.w);
-                if (st != M3D_OK) return st;
-            }
-            for (int i = 0; i < k; i++) {             // previous Givens rotations
-                double t = cs[i] * col[i] + sn[i] * col[i + 1];
-                col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-                col[i] = t;
-            }
-            double d = std::hypot(col[k], col[k + 1]);
-            if (d == 0.0) { cs[k] = 1.0; sn[k] = 0.0; }
-            else { cs[k] = col[k] / d; sn[k] = col[k + 1] / d; }
-            col[k] = d;
-            col[k + 1] = 0.0;
-            for (int i = 0; i <= k; i++) Hh[(size_t)k * (m + 1) + i] = col[i];
-            g[k + 1] = -sn[k] * g[k];
-            g[k] = cs[k] * g[k];
-            (*iters)++;
-            k_used = k + 1;
-            if (std::fabs(g[k + 1]) <= tol_rel * bnorm || *iters >= maxit || d == 0.0) {
-                done = std::fabs(g[k + 1]) <= tol_rel * bnorm || *iters >= maxit || d == 0.0;
-                break;
+            if (st != M3D_OK) return restore(st);
+            k_scale_inv<<<S.grid, 256, 0, c->stream>>>(W.V + (size_t)(k + 1) * N, W.w, hk + k + 1, N);
+            k_givens<<<1, 32, 0, c->stream>>>(W.H, m, k, W.cs, W.sn, W.g, W.kst);
+            st = S.launch_ok();
+            if (st != M3D_OK) return restore(st);
+            KrylovStatus *slot = W.kst_host + (k & 1);
+            CUDA_OR_FAIL(c, cudaMemcpyAsync(slot, W.kst, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, c->stream));
+            CUDA_OR_FAIL(c, cudaEventRecord(W.ev[k & 1], c->stream));
+            queued++;
+            // the outcome of iteration k - lag: the GPU is busy with the iterations queued since
+            const int kc = k - lag;
+            if (kc >= 0) {
+                CUDA_OR_FAIL(c, cudaEventSynchronize(W.ev[kc & 1]));
+                if (W.kst_host[kc & 1].done) break;
             }
         }
-        // back substitution for the upper triangular least-squares system, then x += V y
-        for (int i = k_used - 1; i >= 0; i--) {
-            double s = g[i];
-            for (int j = i + 1; j < k_used; j++) s -= Hh[(size_t)j * (m + 1) + i] * yk[j];
-            double dii = Hh[(size_t)i * (m + 1) + i];
-            yk[i] = dii != 0.0 ? s / dii : 0.0;
-        }
-        for (int i = 0; i < k_used; i++) {
-            st = S.axpby(x, 1.0, x, yk[i], W.V + (size_t)i * N);
-            if (st != M3D_OK) return st;
-        }
-        if (res_rel) *res_rel = std::fabs(g[k_used]) / bnorm;
-        if (done && (std::fabs(g[k_used]) <= tol_rel * bnorm || *iters >= maxit)) break;
-        // restart from the true residual r = b - J x
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(W.kst_host + 2, W.kst, sizeof(KrylovStatus), cudaMemcpyDeviceToHost, c->stream));
+        k_krylov_solution<<<1, 32, 0, c->stream>>>(W.H, m, W.g, W.kst, W.yk);
+        k_add_basis<<<S.grid, 256, 0, c->stream>>>(x, W.V, W.yk, W.kst, N);
+        st = S.launch_ok();
+        if (st != M3D_OK) return restore(st);
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+        host = W.kst_host[2];
+        S.applies += host.iters - *iters;
+        *iters = host.iters;
+        if (res_rel) *res_rel = host.res / bnorm;
+        if (host.res <= tol_rel * bnorm || *iters >= maxit) break;
+        // restart from the true residual r = b - A x
         double xnorm = 0.0;
         st = S.norm(x, &xnorm);
-        if (st != M3D_OK) return st;
+        if (st != M3D_OK) return restore(st);
+        c->S.skip = nullptr;
+        S.applies++;
         st = apply(x, xnorm, W.tmp);
-        if (st != M3D_OK) return st;
+        c->S.skip = lag ? &W.kst->done : nullptr;
+        if (st != M3D_OK) return restore(st);
         st = S.axpby(r, 1.0, b, -1.0, W.tmp);
-        if (st != M3D_OK) return st;
-        st = S.norm(r, &beta);
-        if (st != M3D_OK) return st;
+        if (st != M3D_OK) return restore(st);
+        double beta = 0.0;
+        st = S.dot_dev(r, r, beta_dev, true);
+        if (st != M3D_OK) return restore(st);
+        st = S.read(beta_dev, &beta, 1);
+        if (st != M3D_OK) return restore(st);
         if (res_rel) *res_rel = beta / bnorm;
-        if (beta <= tol_rel * bnorm || *iters >= maxit) break;
-        st = S.axpby(W.V, 1.0 / beta, r, 0.0, r);
-        if (st != M3D_OK) return st;
+        if (beta <= tol_rel * bnorm || beta == 0.0) break;
+        rv = r;
     }
-    return M3D_OK;
+    return restore(M3D_OK);
+}
+
+// Inner tolerance of Newton step k (Eisenstat and Walker, choice 2): 0.3 for the first step,
+// then 0.9 (|F_k| / |F_{k-1}|)^((1 + sqrt 5)/2), raised to the safeguard 0.9 eta_{k-1}^((1 + sqrt 5)/2)
+// when that exceeds 0.1, and kept within [0.5 tol / |F_k|, 0.9].
+double forcing_term(bool first, double r, double r_prev, double eta_prev, double tol)
+{
+    const double gamma = 0.9, alpha = 0.5 * (1.0 + std::sqrt(5.0));
+    double eta = 0.3;
+    if (!first) {
+        eta = gamma * std::pow(r / r_prev, alpha);
+        const double safe = gamma * std::pow(eta_prev, alpha);
+        if (safe > 0.1) eta = std::max(eta, safe);
+    }
+    return std::min(std::max(eta, 0.5 * tol / r), 0.9);
+}
+
+// First backtrack: the minimiser of the quadratic q(x) = f0 + slope x + c x^2 with q(lam) = f_lam.
+double quadratic_backtrack(double f0, double slope, double lam, double f_lam)
+{
+    return -slope * lam * lam / (2.0 * (f_lam - f0 - slope * lam));
+}
+
+// Later backtracks: the local minimiser of the cubic m(x) = f0 + slope x + b x^2 + a x^3 through
+// the last two trials (lam, f_lam) and (lam_prev, f_prev); the quadratic's when a = 0.
+double cubic_backtrack(double f0, double slope, double lam, double f_lam, double lam_prev, double f_prev)
+{
+    const double r1 = f_lam - f0 - lam * slope, r2 = f_prev - f0 - lam_prev * slope;
+    const double den = lam - lam_prev;
+    const double a = (r1 / (lam * lam) - r2 / (lam_prev * lam_prev)) / den;
+    const double b = (-lam_prev * r1 / (lam * lam) + lam * r2 / (lam_prev * lam_prev)) / den;
+    if (a == 0.0) return -slope / (2.0 * b);
+    return (-b + std::sqrt(std::max(b * b - 3.0 * a * slope, 0.0))) / (3.0 * a);
 }
 
 m3d_status ensure_workspace(m3d_ctx *c, Solver &S, int m)
@@ -305,13 +431,26 @@ m3d_status ensure_workspace(m3d_ctx *c, Solver &S, int m)
     W.part = (double *)p;
     CUDA_OR_FAIL(c, m3d_alloc(c, &p, sizeof(double) * 4));
     W.scal = (double *)p;
+    CUDA_OR_FAIL(c, m3d_alloc(c, &p, sizeof(double) * (size_t)(4 * m + 1)));
+    W.g = (double *)p;
+    W.cs = W.g + (m + 1);
+    W.sn = W.cs + m;
+    W.yk = W.sn + m;
+    CUDA_OR_FAIL(c, m3d_alloc(c, &p, sizeof(KrylovStatus)));
+    W.kst = (KrylovStatus *)p;
+    CUDA_OR_FAIL(c, cudaMallocHost(&p, 3 * sizeof(KrylovStatus)));
+    W.kst_host = (KrylovStatus *)p;
+    for (int i = 0; i < 2; i++) CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&W.ev[i], cudaEventDisableTiming));
     return M3D_OK;
 }
 
 // Release a workspace allocated through m3d_alloc (it is also freed with the context).
 void release_workspace(m3d_ctx *c, Workspace &W)
 {
-    void *ptrs[] = {W.V, W.w, W.F, W.py, W.s, W.y, W.yn, W.pyn, W.tmp, W.phv, W.x, W.H, W.part, W.scal};
+    if (W.kst_host) cudaFreeHost(W.kst_host);
+    for (cudaEvent_t e : W.ev)
+        if (e) cudaEventDestroy(e);
+    void *ptrs[] = {W.V, W.w, W.F, W.py, W.s, W.y, W.yn, W.pyn, W.tmp, W.phv, W.x, W.H, W.part, W.scal, W.g, W.kst};
     for (void *p : ptrs) {
         if (!p) continue;
         for (size_t i = 0; i < c->allocs.size(); i++)
@@ -395,7 +534,6 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
     memset(&R, 0, sizeof R);
     Solver S{c, {}, 0, 0};
     S.tangent = o.jv == M3D_JV_TANGENT;
-    S.tangent_maps = &R.tangent_maps;
     m3d_status st = ensure_workspace(c, S, o.restart);
     if (st != M3D_OK) { release_workspace(c, S.W); return st; }
     Workspace &W = S.W;
@@ -421,35 +559,40 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
     TRY(S.norm(W.F, &r));
     R.residual0 = r;
     R.residuals[0] = r;
-    const double gamma = 0.9, alpha = 0.5 * (1.0 + std::sqrt(5.0));
-    double eta_prev = -1.0, r_prev = 0.0;
+    double eta_prev = 0.0, r_prev = 0.0;
+    // the ensemble-backed models run their year as a graph of step launches, which does not
+    // honour SyncParams::skip: their Krylov iterations are checked one at a time
+    const int lag = c->ens ? 0 : 1;
     while (R.newton_steps < o.max_newton && r > o.tol) {
-        double eta;
-        if (eta_prev < 0.0) eta = 0.3;
-        else {
-            eta = gamma * std::pow(r / r_prev, alpha);
-            double safe = gamma * std::pow(eta_prev, alpha);
-            if (safe > 0.1) eta = std::max(eta, safe);
-        }
-        eta = std::min(std::max(eta, 0.5 * o.tol / r), 0.9);
+        const int step = R.newton_steps, hs = std::min(step, M3D_NEWTON_MAX_HIST - 1);
+        const double eta = forcing_term(step == 0, r, r_prev, eta_prev, o.tol);
         double ynorm = 0.0;
         TRY(S.norm(W.y, &ynorm));
         TRY(S.axpby(W.tmp, -1.0, W.F, 0.0, W.F));                 // b = -F (tmp is reused inside gmres)
         TRY(S.axpby(W.yn, 1.0, W.tmp, 0.0, W.tmp));               // keep b in yn during the solve
-        int its = 0;
+        int its = 0, fd_maps = 0;
+        double res_rel = 0.0;
         const Operator jac = [&](const double *v, double vnorm, double *w) {
-            return apply_jacobian(S, W.y, W.py, ynorm, o.fd_eps, v, vnorm, w, &R.year_maps);
+            return apply_jacobian(S, W.y, W.py, ynorm, o.fd_eps, v, vnorm, w, &fd_maps);
         };
-        TRY(gmres(S, jac, W.yn, W.s, eta, o.max_krylov, &its));
+        TRY(gmres(S, jac, W.yn, W.s, eta, o.max_krylov, &its, &res_rel, lag));
         R.krylov_total += its;
+        if (S.tangent) R.tangent_maps += S.applies;
+        else R.year_maps += S.applies;
         // project the step onto zero-mass directions: s -= (w.s / w.w) w
         double ms = 0.0;
         TRY(S.mass(W.s, &ms));
         k_sub_mass<<<S.grid, 256, 0, c->stream>>>(W.s, c->vol, c->n, ms / wsum, N);
         TRY(S.launch_ok());
-        R.krylov[std::min(R.newton_steps, M3D_NEWTON_MAX_HIST - 1)] = its;
-        // line search on f = |F|^2 / 2 along s
-        double f0 = 0.5 * r * r, slope = -r * r, lam = 1.0, lam_prev = -1.0, f_prev = 0.0, fn = 0.0;
+        R.krylov[hs] = its;
+        R.etas[hs] = eta;
+        // slope of f = |F|^2 / 2 along s: GMRES leaves a residual rho = |F + J s| orthogonal to
+        // J s (its minimal-residual property), so F.J s = -(|F|^2 - rho^2)
+        const double rho = res_rel * r;
+        const double f0 = 0.5 * r * r, slope = -(r * r - rho * rho);
+        R.slopes[hs] = slope;
+        double lam = 1.0, lam_prev = -1.0, f_prev = 0.0, fn = 0.0;
+        int trials = 0;
         while (true) {
             TRY(S.axpby(W.yn, 1.0, W.y, lam, W.s));
             TRY(S.phi(W.yn, W.pyn, &R.year_maps));
@@ -458,16 +601,11 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
             double rn = 0.0;
             TRY(S.norm(W.tmp, &rn));
             fn = 0.5 * rn * rn;
+            trials++;
+            if (R.ntrial < M3D_NEWTON_MAX_TRIALS) R.trial_lambdas[R.ntrial++] = lam;
             if (!o.line_search || fn <= f0 + 1e-4 * lam * slope || lam < 1e-4) break;
-            double lt;
-            if (lam_prev < 0.0) lt = -slope / (2.0 * (fn - f0 - slope));
-            else {
-                double a1 = fn - f0 - lam * slope, a2 = f_prev - f0 - lam_prev * slope, den = lam - lam_prev;
-                double a = (a1 / (lam * lam) - a2 / (lam_prev * lam_prev)) / den;
-                double b = (-lam_prev * a1 / (lam * lam) + lam * a2 / (lam_prev * lam_prev)) / den;
-                if (a == 0.0) lt = -slope / (2.0 * b);
-                else lt = (-b + std::sqrt(std::max(b * b - 3.0 * a * slope, 0.0))) / (3.0 * a);
-            }
+            const double lt = lam_prev < 0.0 ? quadratic_backtrack(f0, slope, lam, fn)
+                                             : cubic_backtrack(f0, slope, lam, fn, lam_prev, f_prev);
             lam_prev = lam;
             f_prev = fn;
             lam = std::min(std::max(lt, 0.1 * lam), 0.5 * lam);
@@ -480,7 +618,8 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
         r = std::sqrt(2.0 * fn);
         R.newton_steps++;
         R.residuals[std::min(R.newton_steps, M3D_NEWTON_MAX_HIST - 1)] = r;
-        R.lambdas[std::min(R.newton_steps - 1, M3D_NEWTON_MAX_HIST - 1)] = lam;
+        R.lambdas[hs] = lam;
+        R.trials[hs] = trials;
     }
 #undef TRY
     R.residual = r;
@@ -574,7 +713,7 @@ m3d_status metos3d_periodic_gradient(m3d_ctx *c, const double *ystar, const doub
     }
     int its = 0;
     double est = 0.0;
-    TRY(gmres(S, adjoint_op, W.F, W.x, o.tol, o.max_krylov, &its, &est));
+    TRY(gmres(S, adjoint_op, W.F, W.x, o.tol, o.max_krylov, &its, &est, 0));   // reverse sweeps: no skip
     TRY(project(W.x));
     R.krylov = its;
     // ubar = phi_u^T lambda; the same sweep gives phi_y^T lambda for the true residual

@@ -528,9 +528,14 @@ struct SyncParams {
     int *flags;                 // [ntiles] steps completed (0 at launch)
     const int *dep_off;         // [ntiles+1]
     const int *dep_idx;         // neighbour tiles
-    int *status;                // [4]: 0 ok / 1 timeout; tile; step; unused
+    int *status;                // [4]: 0 ok / 1 timeout; tile; step; 1 if an aborting tile's own copy did not land
     unsigned long long timeout_ns;
     int withhold_tile;          // test hook: this tile never publishes its counter (-1: none)
+    // Non-null: a device flag set by an earlier kernel on the same stream; when it is nonzero
+    // at launch the year kernels return at once (every tile reads the same value).  A Krylov
+    // solve that enqueues its iterations ahead of its convergence test uses it to skip the
+    // iterations enqueued after convergence.
+    const int *skip;
 };
 
 __device__ __forceinline__ unsigned long long global_ns()

@@ -460,8 +460,11 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
         }
         __syncthreads();
         if ((s > 0 || stepop) && abort_flag) {
-            // the copy of step s may still be in flight (no later one was issued)
-            if (stepop && threadIdx.x == 0) mbar_wait_bounded(&opbar[s & 1], (s >> 1) & 1, S.timeout_ns);
+            // The copy of step s may still be in flight (no later one was issued); it depends on
+            // no other tile, so it lands within the bound unless the GPU is failing.  If the
+            // bound runs out anyway, status[3] records it before the CTA retires.
+            if (stepop && threadIdx.x == 0 && !mbar_wait_bounded(&opbar[s & 1], (s >> 1) & 1, S.timeout_ns))
+                atomicExch(S.status + 3, 1);
             return;
         }
         if (stepop && threadIdx.x == copier && s + 1 < nsteps) fetch_operator(s + 1);

@@ -56,3 +56,27 @@ def test_newton_with_tangent_products(m3d):
     want, _ = on.newton_krylov(P, y0, u, tol=1e-8)
     assert np.abs(y.cpu().numpy() - want).max() / np.abs(want).max() < 1e-7
     ctx.close()
+
+
+def test_year_tangent_matches_oracle_benchmark_grid(m3d):
+    """The benchmark's 128 x 64 x 15 grid (52,749 cells), default plan and options: phi(y) and
+    phi'(y) v element by element against the oracle's tangent year map (run on all host cores)."""
+    import os
+    p = mi.make_problem("ndop_128x64x15")
+    P = oracle.Problem(p)
+    u = mi.default_params_ndop()
+    y = mi.random_state(p)
+    v = mi.random_state(p, seed=5) - mi.random_state(p, seed=6)
+    ctx = m3d.Context.from_problem(p)
+    phi = torch.empty((2, p.n), dtype=torch.float64, device="cuda")
+    jv = torch.empty_like(phi)
+    ctx.year_tangent(cuda(y), cuda(v), cuda(u), phi, jv)
+    ctx.sync()
+    oracle.set_threads(os.cpu_count() or 1)
+    try:
+        want_phi, want_jv = oracle.year_tangent(P, y, v, u)
+    finally:
+        oracle.set_threads(1)
+    assert rel_err(phi.cpu().numpy(), want_phi) < 1e-10
+    assert rel_err(jv.cpu().numpy(), want_jv) < 1e-10
+    ctx.close()
