@@ -272,6 +272,14 @@ m3d_status metos3d_sync(m3d_ctx *ctx);
  *       (synchronous; M3D_ERR_CUDA if the allocation fails, M3D_ERR_UNSUPPORTED without the
  *       resident plan); 0 frees it.  The derivative sweeps use it for their forward parts.
  *   M3D_OPT_STEP_OPERATOR_BYTES (read only): bytes held by the per-step operators (0 if none).
+ *   M3D_OPT_TANGENT_FORM: how metos3d_year_tangent evaluates phi'(y) v.  M3D_TANGENT_DUAL
+ *       (default): one sweep of the state and its perturbation together, the source term on
+ *       dual numbers.  M3D_TANGENT_LINEARISED (PO4-DOP, one internal step, resident plan): the
+ *       year map recording the source term's Jacobian df/dN of every euphotic cell and step
+ *       (nstep x euphotic cells doubles, held by the context), then one sweep of the
+ *       perturbation alone through the linearised step.  Newton-Krylov with tangent products
+ *       uses the linearised sweep wherever it is available, whatever this option says: its
+ *       line search records the Jacobian along the trajectory it evaluates anyway.
  *   M3D_OPT_KERNEL_TIMING: 1 records CUDA events on the context's stream around every launch
  *       of the year kernel (resident and persistent plans), default 0.
  *   M3D_OPT_LAST_KERNEL_NS (read only): device time of the last year-kernel launch timed that
@@ -288,8 +296,10 @@ enum {
     M3D_OPT_STEP_OPERATORS = 7,
     M3D_OPT_STEP_OPERATOR_BYTES = 8,
     M3D_OPT_KERNEL_TIMING = 9,
-    M3D_OPT_LAST_KERNEL_NS = 10
+    M3D_OPT_LAST_KERNEL_NS = 10,
+    M3D_OPT_TANGENT_FORM = 11
 };
+enum { M3D_TANGENT_DUAL = 0, M3D_TANGENT_LINEARISED = 1 };
 enum { M3D_IMPLICIT_DENSE = 0, M3D_IMPLICIT_TRIDIAGONAL = 1 };
 enum { M3D_PLAN_PERSISTENT = 0, M3D_PLAN_GRAPH = 1, M3D_PLAN_RESIDENT = 2 };
 m3d_status metos3d_set_option(m3d_ctx *ctx, int option, long long value);

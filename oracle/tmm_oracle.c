@@ -536,6 +536,170 @@ static void ndop_q_tangent(int nlayer, const double *h, const double *d, double 
     }
 }
 
+/* Tangent of the N model (R10), by hand: df_k = alpha K_N / (PO4_k + K_N)^2 I_k/(I_k + K_I) dPO4_k,
+ * dq_k = -df_k (euphotic), dE = sum_k df_k h_k, dq_k = dE (top_k - bot_k) / h_k (aphotic), and
+ * the shallow column's bottom layer gets dE / h. */
+static void n_q_tangent(int nlayer, const double *h, const double *d, double insol, double ice,
+                        const double *PO4, const double *dPO4, const double *u, double *q, double *dq)
+{
+    const double sigma_par = 0.4;
+    double kw = u[0], alpha = 360.0 * u[1], KN = u[2], KI = u[3], b = u[4];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double E = 0.0, dE = 0.0, zeu = 0.0;
+    for (int k = 0; k < neu; k++) {
+        double I = insol * sigma_par * (1.0 - ice) * exp(-kw * d[k]);
+        double LF = I / (KI + I);
+        double f = alpha * (PO4[k] / (PO4[k] + KN)) * LF;
+        double df = alpha * (KN / ((PO4[k] + KN) * (PO4[k] + KN))) * LF * dPO4[k];
+        q[k] = -f;
+        dq[k] = -df;
+        E += f * h[k];
+        dE += df * h[k];
+        zeu += h[k];
+    }
+    double ztop = zeu;
+    for (int k = neu; k < nlayer; k++) {
+        double zbot = ztop + h[k];
+        double top = pow(ztop / zeu, -b);
+        double bot = (k + 1 < nlayer) ? pow(zbot / zeu, -b) : 0.0;
+        q[k] = E * (top - bot) / h[k];
+        dq[k] = dE * (top - bot) / h[k];
+        ztop = zbot;
+    }
+    if (neu >= nlayer) {
+        q[nlayer - 1] += E / h[nlayer - 1];
+        dq[nlayer - 1] += dE / h[nlayer - 1];
+    }
+}
+
+/* Tangent of the PO4-DOP-PHY model (Section 2.2.2, R11), by hand.  With M = PO4/(PO4+K_1) and
+ * LF = I/(I+K_I): df_1 = mu_1 LF (M dPHY + PHY K_1/(PO4+K_1)^2 dPO4), df_3 = sigma_3 df_1,
+ * dloss = (lambda_3 + 2 kappa_3 PHY) dPHY, and every q is linear in those and in DOP, PHY. */
+static void phy_q_tangent(int nlayer, const double *h, const double *d, double insol, double ice,
+                          const double *y, const double *dy, const double *u, double *q, double *dq)
+{
+    const double sigma_par = 0.4;
+    const double *PO4 = y, *DOP = y + nlayer, *PHY = y + 2 * nlayer;
+    const double *dPO4 = dy, *dDOP = dy + nlayer, *dPHY = dy + 2 * nlayer;
+    double *q1 = q, *q2 = q + nlayer, *q3 = q + 2 * nlayer;
+    double *dq1 = dq, *dq2 = dq + nlayer, *dq3 = dq + 2 * nlayer;
+    double mu1 = 360.0 * u[0], kw = u[1], K1 = u[2], KI = u[3], l2 = 360.0 * u[4];
+    double sig2 = u[5], l3 = 360.0 * u[6], k3 = 360.0 * u[7], l3p = 360.0 * u[8];
+    double sig3 = u[9], b = u[10];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double E = 0.0, dE = 0.0, zeu = 0.0;
+    for (int k = 0; k < neu; k++) {
+        double I = insol * sigma_par * (1.0 - ice) * exp(-kw * d[k]);
+        double LF = I / (KI + I);
+        double M = PO4[k] / (PO4[k] + K1);
+        double dM = K1 / ((PO4[k] + K1) * (PO4[k] + K1)) * dPO4[k];
+        double f1 = mu1 * PHY[k] * M * LF;
+        double df1 = mu1 * LF * (dPHY[k] * M + PHY[k] * dM);
+        double f3 = sig3 * f1, df3 = sig3 * df1;
+        double loss = l3 * PHY[k] + k3 * PHY[k] * PHY[k];
+        double dloss = (l3 + 2.0 * k3 * PHY[k]) * dPHY[k];
+        q1[k] = -f1 + l2 * DOP[k];
+        q2[k] = sig2 * f3 + loss - l2 * DOP[k] + l3p * PHY[k];
+        q3[k] = (1.0 - sig3) * f1 - loss - l3p * PHY[k];
+        dq1[k] = -df1 + l2 * dDOP[k];
+        dq2[k] = sig2 * df3 + dloss - l2 * dDOP[k] + l3p * dPHY[k];
+        dq3[k] = (1.0 - sig3) * df1 - dloss - l3p * dPHY[k];
+        E += (1.0 - sig2) * f3 * h[k];
+        dE += (1.0 - sig2) * df3 * h[k];
+        zeu += h[k];
+    }
+    double ztop = zeu;
+    for (int k = neu; k < nlayer; k++) {
+        double zbot = ztop + h[k];
+        double top = pow(ztop / zeu, -b);
+        double bot = (k + 1 < nlayer) ? pow(zbot / zeu, -b) : 0.0;
+        q1[k] = E * (top - bot) / h[k] + l2 * DOP[k];
+        q2[k] = -l2 * DOP[k] + l3p * PHY[k];
+        q3[k] = -l3p * PHY[k];
+        dq1[k] = dE * (top - bot) / h[k] + l2 * dDOP[k];
+        dq2[k] = -l2 * dDOP[k] + l3p * dPHY[k];
+        dq3[k] = -l3p * dPHY[k];
+        ztop = zbot;
+    }
+    if (neu >= nlayer) {
+        q1[nlayer - 1] += E / h[nlayer - 1];
+        dq1[nlayer - 1] += dE / h[nlayer - 1];
+    }
+}
+
+/* Tangent of the NPZD-DOP model (R12), by hand: dU = mu_P LF (M dP + P K_N/(N+K_N)^2 dN),
+ * dG = mu_Z (P/(K_P+P) dZ + Z K_P/(K_P+P)^2 dP), the losses' derivatives, and the sinking
+ * fluxes dS_k = w_D dD_k (none through the floor). */
+static void npzd_q_tangent(int nlayer, const double *h, const double *d, double insol, double ice,
+                           const double *y, const double *dy, const double *u, double *q, double *dq)
+{
+    const double sigma_par = 0.4;
+    const double *N = y, *P = y + nlayer, *Z = y + 2 * nlayer, *D = y + 3 * nlayer;
+    const double *DOP = y + 4 * nlayer;
+    const double *dN = dy, *dP = dy + nlayer, *dZ = dy + 2 * nlayer, *dD = dy + 3 * nlayer;
+    const double *dDOP = dy + 4 * nlayer;
+    double kw = u[0], muP = 360.0 * u[1], KN = u[2], KI = u[3], muZ = 360.0 * u[4];
+    double KP = u[5], eps = u[6], lP = 360.0 * u[7], kZ = 360.0 * u[8], lZ = 360.0 * u[9];
+    double lD = 360.0 * u[10], lO = 360.0 * u[11], wD = 360.0 * u[12];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double Sin = 0.0, dSin = 0.0;
+    for (int k = 0; k < nlayer; k++) {
+        double U = 0.0, dU = 0.0;
+        if (k < neu) {
+            double I = insol * sigma_par * (1.0 - ice) * exp(-kw * d[k]);
+            double LF = I / (KI + I);
+            double M = N[k] / (N[k] + KN);
+            U = muP * P[k] * M * LF;
+            dU = muP * LF * (M * dP[k] + P[k] * (KN / ((N[k] + KN) * (N[k] + KN))) * dN[k]);
+        }
+        double R = P[k] / (KP + P[k]);
+        double G = muZ * Z[k] * R;
+        double dG = muZ * (R * dZ[k] + Z[k] * (KP / ((KP + P[k]) * (KP + P[k]))) * dP[k]);
+        double mP = lP * P[k], mZ = kZ * Z[k] * Z[k], eZ = lZ * Z[k];
+        double dmP = lP * dP[k], dmZ = 2.0 * kZ * Z[k] * dZ[k], deZ = lZ * dZ[k];
+        double rD = lD * D[k], rO = lO * DOP[k], drD = lD * dD[k], drO = lO * dDOP[k];
+        double Sout = (k + 1 < nlayer) ? wD * D[k] : 0.0;
+        double dSout = (k + 1 < nlayer) ? wD * dD[k] : 0.0;
+        q[k] = -U + rO;
+        q[nlayer + k] = U - G - mP;
+        q[2 * nlayer + k] = eps * G - mZ - eZ;
+        q[3 * nlayer + k] = mP + mZ - rD + (Sin - Sout) / h[k];
+        q[4 * nlayer + k] = (1.0 - eps) * G + eZ + rD - rO;
+        dq[k] = -dU + drO;
+        dq[nlayer + k] = dU - dG - dmP;
+        dq[2 * nlayer + k] = eps * dG - dmZ - deZ;
+        dq[3 * nlayer + k] = dmP + dmZ - drD + (dSin - dSout) / h[k];
+        dq[4 * nlayer + k] = (1.0 - eps) * dG + deZ + drD - drO;
+        Sin = Sout;
+        dSin = dSout;
+    }
+}
+
+/* q and its tangent along dy for any model; y, dy, q, dq are (ntracer, nlayer). */
+static int model_q_tangent(int model, int ntracer, int nparam, int nlayer, const double *h, const double *d,
+                           double insol, double ice, const double *y, const double *dy, const double *u,
+                           double *q, double *dq)
+{
+    if (model == ORACLE_MODEL_NDOP && ntracer == 2 && nparam == 7) {
+        ndop_q_tangent(nlayer, h, d, insol, ice, y, y + nlayer, dy, dy + nlayer, u, q, q + nlayer, dq,
+                       dq + nlayer);
+        return 0;
+    }
+    if (model == ORACLE_MODEL_N && ntracer == 1 && nparam == 5) {
+        n_q_tangent(nlayer, h, d, insol, ice, y, dy, u, q, dq);
+        return 0;
+    }
+    if (model == ORACLE_MODEL_PHY && ntracer == 3 && nparam == 11) {
+        phy_q_tangent(nlayer, h, d, insol, ice, y, dy, u, q, dq);
+        return 0;
+    }
+    if (model == ORACLE_MODEL_NPZD && ntracer == 5 && nparam == 13) {
+        npzd_q_tangent(nlayer, h, d, insol, ice, y, dy, u, q, dq);
+        return 0;
+    }
+    return -1;
+}
+
 /* The model interface and its tangent: ybgc as oracle_bgc, dybgc its derivative along dy. */
 int oracle_bgc_tangent(int model, double t, double dt, double lat, double insol, double dayfrac,
                        double ice, double wind, int ntracer, int nlayer, const double *h,
@@ -548,22 +712,21 @@ int oracle_bgc_tangent(int model, double t, double dt, double lat, double insol,
         for (int i = 0; i < ntracer * nlayer; i++) { ybgc[i] = 0.0; dybgc[i] = 0.0; }
         return 0;
     }
-    if (model != ORACLE_MODEL_NDOP || ntracer != 2 || nparam != 7) return -1;
-    double ys[2 * ORACLE_MAX_LAYER], dys[2 * ORACLE_MAX_LAYER];
-    double qN[ORACLE_MAX_LAYER], qD[ORACLE_MAX_LAYER], dqN[ORACLE_MAX_LAYER], dqD[ORACLE_MAX_LAYER];
-    memcpy(ys, y, sizeof(double) * 2 * nlayer);
-    memcpy(dys, dy, sizeof(double) * 2 * nlayer);
+    if (ntracer < 1 || ntracer > ORACLE_MAX_TRACER) return -1;
+    int len = ntracer * nlayer;
+    double ys[ORACLE_MAX_TRACER * ORACLE_MAX_LAYER], dys[ORACLE_MAX_TRACER * ORACLE_MAX_LAYER];
+    double q[ORACLE_MAX_TRACER * ORACLE_MAX_LAYER], dq[ORACLE_MAX_TRACER * ORACLE_MAX_LAYER];
+    memcpy(ys, y, sizeof(double) * len);
+    memcpy(dys, dy, sizeof(double) * len);
     double ds = dt / nsub;
     for (int s = 0; s < nsub; s++) {
-        ndop_q_tangent(nlayer, h, d, insol, ice, ys, ys + nlayer, dys, dys + nlayer, u, qN, qD, dqN, dqD);
-        for (int k = 0; k < nlayer; k++) {
-            ys[k] += ds * qN[k];
-            ys[nlayer + k] += ds * qD[k];
-            dys[k] += ds * dqN[k];
-            dys[nlayer + k] += ds * dqD[k];
+        if (model_q_tangent(model, ntracer, nparam, nlayer, h, d, insol, ice, ys, dys, u, q, dq) != 0) return -1;
+        for (int i = 0; i < len; i++) {
+            ys[i] += ds * q[i];
+            dys[i] += ds * dq[i];
         }
     }
-    for (int i = 0; i < 2 * nlayer; i++) {
+    for (int i = 0; i < len; i++) {
         ybgc[i] = ys[i] - y[i];
         dybgc[i] = dys[i] - dy[i];
     }
@@ -727,6 +890,199 @@ static void ndop_q_adjoint(int nlayer, const double *h, const double *d, double 
     }
 }
 
+/* Reverse of the N model q (R10) at PO4, by hand: given the cotangent qb of q, add the
+ * cotangent of PO4 into yb and of u into ub. */
+static void n_q_adjoint(int nlayer, const double *h, const double *d, double insol, double ice,
+                        const double *PO4, const double *u, const double *qb, double *yb, double *ub)
+{
+    const double sigma_par = 0.4;
+    double kw = u[0], alpha = 360.0 * u[1], KN = u[2], KI = u[3], b = u[4];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double I[ORACLE_MAX_LAYER], f[ORACLE_MAX_LAYER];
+    double E = 0.0, zeu = 0.0;
+    for (int k = 0; k < neu; k++) {
+        I[k] = insol * sigma_par * (1.0 - ice) * exp(-kw * d[k]);
+        f[k] = alpha * (PO4[k] / (PO4[k] + KN)) * (I[k] / (KI + I[k]));
+        E += f[k] * h[k];
+        zeu += h[k];
+    }
+    /* aphotic q_k = E (top - bot) / h_k; shallow bottom layer q += E / h */
+    double Eb = 0.0, ztop = zeu;
+    for (int k = neu; k < nlayer; k++) {
+        double zbot = ztop + h[k];
+        double top = pow(ztop / zeu, -b);
+        double bot = (k + 1 < nlayer) ? pow(zbot / zeu, -b) : 0.0;
+        double dtop = -log(ztop / zeu) * top;          /* d top / d b */
+        double dbot = (k + 1 < nlayer) ? -log(zbot / zeu) * bot : 0.0;
+        Eb += qb[k] * (top - bot) / h[k];
+        ub[4] += qb[k] * E * (dtop - dbot) / h[k];
+        ztop = zbot;
+    }
+    if (neu >= nlayer) Eb += qb[nlayer - 1] / h[nlayer - 1];
+    /* euphotic q_k = -f_k, E = sum f_k h_k, f = alpha' M LF */
+    for (int k = 0; k < neu; k++) {
+        double fb = -qb[k] + Eb * h[k];
+        double M = PO4[k] / (PO4[k] + KN), LF = I[k] / (KI + I[k]);
+        ub[1] += fb * 360.0 * M * LF;
+        yb[k] += fb * alpha * LF * KN / ((PO4[k] + KN) * (PO4[k] + KN));
+        ub[2] += fb * alpha * LF * (-PO4[k] / ((PO4[k] + KN) * (PO4[k] + KN)));
+        ub[3] += fb * alpha * M * (-I[k] / ((KI + I[k]) * (KI + I[k])));
+        ub[0] += fb * alpha * M * (KI / ((KI + I[k]) * (KI + I[k]))) * (-d[k] * I[k]);
+    }
+}
+
+/* Reverse of the PO4-DOP-PHY q (Section 2.2.2, R11) at y = (PO4, DOP, PHY), by hand. */
+static void phy_q_adjoint(int nlayer, const double *h, const double *d, double insol, double ice,
+                          const double *y, const double *u, const double *qb, double *yb, double *ub)
+{
+    const double sigma_par = 0.4;
+    const double *PO4 = y, *DOP = y + nlayer, *PHY = y + 2 * nlayer;
+    const double *qb1 = qb, *qb2 = qb + nlayer, *qb3 = qb + 2 * nlayer;
+    double *PO4b = yb, *DOPb = yb + nlayer, *PHYb = yb + 2 * nlayer;
+    double mu1 = 360.0 * u[0], kw = u[1], K1 = u[2], KI = u[3], l2 = 360.0 * u[4];
+    double sig2 = u[5], l3 = 360.0 * u[6], k3 = 360.0 * u[7], l3p = 360.0 * u[8];
+    double sig3 = u[9], b = u[10];
+    int neu = nlayer < 2 ? nlayer : 2;
+    double I[ORACLE_MAX_LAYER], f1[ORACLE_MAX_LAYER];
+    double sumf3h = 0.0, zeu = 0.0;
+    for (int k = 0; k < neu; k++) {
+        I[k] = insol * sigma_par * (1.0 - ice) * exp(-kw * d[k]);
+        f1[k] = mu1 * PHY[k] * (PO4[k] / (PO4[k] + K1)) * (I[k] / (KI + I[k]));
+        sumf3h += sig3 * f1[k] * h[k];
+        zeu += h[k];
+    }
+    double E = (1.0 - sig2) * sumf3h;
+    /* aphotic: q1 = E (top - bot)/h + l2 DOP, q2 = -l2 DOP + l3' PHY, q3 = -l3' PHY */
+    double Eb = 0.0, ztop = zeu;
+    for (int k = neu; k < nlayer; k++) {
+        double zbot = ztop + h[k];
+        double top = pow(ztop / zeu, -b);
+        double bot = (k + 1 < nlayer) ? pow(zbot / zeu, -b) : 0.0;
+        double dtop = -log(ztop / zeu) * top;
+        double dbot = (k + 1 < nlayer) ? -log(zbot / zeu) * bot : 0.0;
+        Eb += qb1[k] * (top - bot) / h[k];
+        ub[10] += qb1[k] * E * (dtop - dbot) / h[k];
+        DOPb[k] += l2 * (qb1[k] - qb2[k]);
+        ub[4] += 360.0 * (qb1[k] - qb2[k]) * DOP[k];
+        PHYb[k] += l3p * (qb2[k] - qb3[k]);
+        ub[8] += 360.0 * (qb2[k] - qb3[k]) * PHY[k];
+        ztop = zbot;
+    }
+    if (neu >= nlayer) Eb += qb1[nlayer - 1] / h[nlayer - 1];
+    /* E = (1 - sigma_2) sum f_3 h */
+    ub[5] += -Eb * sumf3h;
+    for (int k = 0; k < neu; k++) {
+        double f3 = sig3 * f1[k];
+        /* q2 = sigma_2 f3 + ..., E: f3b; f3 = sigma_3 f1 */
+        double f3b = sig2 * qb2[k] + Eb * (1.0 - sig2) * h[k];
+        ub[5] += qb2[k] * f3;
+        double f1b = -qb1[k] + (1.0 - sig3) * qb3[k] + sig3 * f3b;
+        ub[9] += f3b * f1[k] - qb3[k] * f1[k];
+        /* loss = l3 PHY + k3 PHY^2 in q2 (+) and q3 (-) */
+        double lossb = qb2[k] - qb3[k];
+        PHYb[k] += lossb * (l3 + 2.0 * k3 * PHY[k]);
+        ub[6] += 360.0 * lossb * PHY[k];
+        ub[7] += 360.0 * lossb * PHY[k] * PHY[k];
+        DOPb[k] += l2 * (qb1[k] - qb2[k]);
+        ub[4] += 360.0 * (qb1[k] - qb2[k]) * DOP[k];
+        PHYb[k] += l3p * (qb2[k] - qb3[k]);
+        ub[8] += 360.0 * (qb2[k] - qb3[k]) * PHY[k];
+        /* f1 = mu1 PHY M LF */
+        double M = PO4[k] / (PO4[k] + K1), LF = I[k] / (KI + I[k]);
+        ub[0] += f1b * 360.0 * PHY[k] * M * LF;
+        PHYb[k] += f1b * mu1 * M * LF;
+        PO4b[k] += f1b * mu1 * PHY[k] * LF * K1 / ((PO4[k] + K1) * (PO4[k] + K1));
+        ub[2] += f1b * mu1 * PHY[k] * LF * (-PO4[k] / ((PO4[k] + K1) * (PO4[k] + K1)));
+        ub[3] += f1b * mu1 * PHY[k] * M * (-I[k] / ((KI + I[k]) * (KI + I[k])));
+        ub[1] += f1b * mu1 * PHY[k] * M * (KI / ((KI + I[k]) * (KI + I[k]))) * (-d[k] * I[k]);
+    }
+}
+
+/* Reverse of the NPZD-DOP q (R12) at y = (N, P, Z, D, DOP), by hand. */
+static void npzd_q_adjoint(int nlayer, const double *h, const double *d, double insol, double ice,
+                           const double *y, const double *u, const double *qb, double *yb, double *ub)
+{
+    const double sigma_par = 0.4;
+    const double *N = y, *P = y + nlayer, *Z = y + 2 * nlayer, *D = y + 3 * nlayer;
+    const double *DOP = y + 4 * nlayer;
+    const double *qbN = qb, *qbP = qb + nlayer, *qbZ = qb + 2 * nlayer, *qbD = qb + 3 * nlayer;
+    const double *qbO = qb + 4 * nlayer;
+    double *Nb = yb, *Pb = yb + nlayer, *Zb = yb + 2 * nlayer, *Db = yb + 3 * nlayer, *Ob = yb + 4 * nlayer;
+    double kw = u[0], muP = 360.0 * u[1], KN = u[2], KI = u[3], muZ = 360.0 * u[4];
+    double KP = u[5], eps = u[6], lP = 360.0 * u[7], kZ = 360.0 * u[8], lZ = 360.0 * u[9];
+    double lD = 360.0 * u[10], lO = 360.0 * u[11], wD = 360.0 * u[12];
+    int neu = nlayer < 2 ? nlayer : 2;
+    for (int k = 0; k < nlayer; k++) {
+        /* sinking: S_k = w_D D_k (k + 1 < nlayer) leaves layer k and enters layer k + 1 */
+        if (k + 1 < nlayer) {
+            double Sb = -qbD[k] / h[k] + qbD[k + 1] / h[k + 1];
+            Db[k] += wD * Sb;
+            ub[12] += 360.0 * D[k] * Sb;
+        }
+        /* linear and quadratic losses */
+        double mPb = -qbP[k] + qbD[k];
+        Pb[k] += lP * mPb;
+        ub[7] += 360.0 * mPb * P[k];
+        double mZb = -qbZ[k] + qbD[k];
+        Zb[k] += 2.0 * kZ * Z[k] * mZb;
+        ub[8] += 360.0 * mZb * Z[k] * Z[k];
+        double eZb = -qbZ[k] + qbO[k];
+        Zb[k] += lZ * eZb;
+        ub[9] += 360.0 * eZb * Z[k];
+        double rDb = -qbD[k] + qbO[k];
+        Db[k] += lD * rDb;
+        ub[10] += 360.0 * rDb * D[k];
+        double rOb = qbN[k] - qbO[k];
+        Ob[k] += lO * rOb;
+        ub[11] += 360.0 * rOb * DOP[k];
+        /* grazing G = mu_Z Z P/(K_P + P), assimilated fraction epsilon */
+        double R = P[k] / (KP + P[k]);
+        double G = muZ * Z[k] * R;
+        double Gb = -qbP[k] + eps * qbZ[k] + (1.0 - eps) * qbO[k];
+        ub[6] += G * (qbZ[k] - qbO[k]);
+        Zb[k] += Gb * muZ * R;
+        Pb[k] += Gb * muZ * Z[k] * KP / ((KP + P[k]) * (KP + P[k]));
+        ub[4] += Gb * 360.0 * Z[k] * R;
+        ub[5] += Gb * muZ * Z[k] * (-P[k] / ((KP + P[k]) * (KP + P[k])));
+        /* uptake U = mu_P P M LF in the euphotic layers */
+        if (k < neu) {
+            double I = insol * sigma_par * (1.0 - ice) * exp(-kw * d[k]);
+            double LF = I / (KI + I), M = N[k] / (N[k] + KN);
+            double Ub = -qbN[k] + qbP[k];
+            Pb[k] += Ub * muP * M * LF;
+            Nb[k] += Ub * muP * P[k] * LF * KN / ((N[k] + KN) * (N[k] + KN));
+            ub[1] += Ub * 360.0 * P[k] * M * LF;
+            ub[2] += Ub * muP * P[k] * LF * (-N[k] / ((N[k] + KN) * (N[k] + KN)));
+            ub[3] += Ub * muP * P[k] * M * (-I / ((KI + I) * (KI + I)));
+            ub[0] += Ub * muP * P[k] * M * (KI / ((KI + I) * (KI + I))) * (-d[k] * I);
+        }
+    }
+}
+
+/* Reverse of q for any model: cotangent qb of q (ntracer, nlayer) at y; yb, ub accumulated. */
+static int model_q_adjoint(int model, int ntracer, int nparam, int nlayer, const double *h, const double *d,
+                           double insol, double ice, const double *y, const double *u, const double *qb, double *yb,
+                           double *ub)
+{
+    if (model == ORACLE_MODEL_NDOP && ntracer == 2 && nparam == 7) {
+        ndop_q_adjoint(nlayer, h, d, insol, ice, y, y + nlayer, u, qb, qb + nlayer, yb, yb + nlayer, ub);
+        return 0;
+    }
+    if (model == ORACLE_MODEL_N && ntracer == 1 && nparam == 5) {
+        n_q_adjoint(nlayer, h, d, insol, ice, y, u, qb, yb, ub);
+        return 0;
+    }
+    if (model == ORACLE_MODEL_PHY && ntracer == 3 && nparam == 11) {
+        phy_q_adjoint(nlayer, h, d, insol, ice, y, u, qb, yb, ub);
+        return 0;
+    }
+    if (model == ORACLE_MODEL_NPZD && ntracer == 5 && nparam == 13) {
+        npzd_q_adjoint(nlayer, h, d, insol, ice, y, u, qb, yb, ub);
+        return 0;
+    }
+    return -1;
+}
+
 /* Reverse of the model interface: given ybgc_bar (cotangent of ybgc), add the cotangent of
  * y into ybar and of u into ubar (both accumulated). */
 int oracle_bgc_adjoint(int model, double dt, double insol, double ice, int ntracer, int nlayer,
@@ -735,27 +1091,26 @@ int oracle_bgc_adjoint(int model, double dt, double insol, double ice, int ntrac
 {
     if (nlayer < 1 || nlayer > ORACLE_MAX_LAYER || nsub < 1 || nsub > 64) return -1;
     if (model == ORACLE_MODEL_NONE) return 0;
-    if (model != ORACLE_MODEL_NDOP || ntracer != 2 || nparam != 7) return -1;
+    if (ntracer < 1 || ntracer > ORACLE_MAX_TRACER) return -1;
+    int len = ntracer * nlayer;
     /* forward internal states y^(0..nsub-1) */
-    static __thread double st[64][2 * ORACLE_MAX_LAYER];
-    double qN[ORACLE_MAX_LAYER], qD[ORACLE_MAX_LAYER];
+    static __thread double st[64][ORACLE_MAX_TRACER * ORACLE_MAX_LAYER];
+    double q[ORACLE_MAX_TRACER * ORACLE_MAX_LAYER];
     double ds = dt / nsub;
-    memcpy(st[0], y, sizeof(double) * 2 * nlayer);
+    memcpy(st[0], y, sizeof(double) * len);
     for (int s = 0; s + 1 < nsub; s++) {
-        ndop_q(nlayer, h, d, insol, ice, st[s], st[s] + nlayer, u, qN, qD);
-        for (int k = 0; k < nlayer; k++) {
-            st[s + 1][k] = st[s][k] + ds * qN[k];
-            st[s + 1][nlayer + k] = st[s][nlayer + k] + ds * qD[k];
-        }
+        if (model_q(model, ntracer, nparam, nlayer, h, d, insol, ice, st[s], u, q) != 0) return -1;
+        for (int i = 0; i < len; i++) st[s + 1][i] = st[s][i] + ds * q[i];
     }
-    /* ybgc = y^(nsub) - y^(0): ybar^(nsub) = ybgc_bar, and -ybgc_bar goes to y^(0) */
-    double yb[2 * ORACLE_MAX_LAYER], qbN[ORACLE_MAX_LAYER], qbD[ORACLE_MAX_LAYER];
-    memcpy(yb, ybgc_bar, sizeof(double) * 2 * nlayer);
+    /* ybgc = y^(nsub) - y^(0): ybar^(nsub) = ybgc_bar, and -ybgc_bar goes to y^(0); each
+     * internal step y^(s+1) = y^(s) + ds q(y^(s)) passes ybar^(s) = ybar^(s+1) + (ds dq/dy)^T ybar^(s+1) */
+    double yb[ORACLE_MAX_TRACER * ORACLE_MAX_LAYER], qb[ORACLE_MAX_TRACER * ORACLE_MAX_LAYER];
+    memcpy(yb, ybgc_bar, sizeof(double) * len);
     for (int s = nsub - 1; s >= 0; s--) {
-        for (int k = 0; k < nlayer; k++) { qbN[k] = ds * yb[k]; qbD[k] = ds * yb[nlayer + k]; }
-        ndop_q_adjoint(nlayer, h, d, insol, ice, st[s], st[s] + nlayer, u, qbN, qbD, yb, yb + nlayer, ubar);
+        for (int i = 0; i < len; i++) qb[i] = ds * yb[i];
+        if (model_q_adjoint(model, ntracer, nparam, nlayer, h, d, insol, ice, st[s], u, qb, yb, ubar) != 0) return -1;
     }
-    for (int i = 0; i < 2 * nlayer; i++) ybar[i] += yb[i] - ybgc_bar[i];
+    for (int i = 0; i < len; i++) ybar[i] += yb[i] - ybgc_bar[i];
     return 0;
 }
 

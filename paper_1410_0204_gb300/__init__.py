@@ -9,6 +9,7 @@ from .binding import (Context, Metos3dError, bgc, declared_symbols, load, librar
                       M3D_ERR_TIMEOUT, M3D_ERR_UNSUPPORTED, M3D_NOT_CONVERGED, OPT_YEAR_PLAN,
                       OPT_WAIT_TIMEOUT_NS, OPT_TEST_WITHHOLD_TILE, OPT_NTILES, PLAN_PERSISTENT, PLAN_GRAPH,
                       PLAN_RESIDENT, OPT_IMPLICIT_FORM, OPT_ADJOINT_PLAN, OPT_STEP_OPERATORS,
-                      OPT_STEP_OPERATOR_BYTES, OPT_KERNEL_TIMING, OPT_LAST_KERNEL_NS, IMPLICIT_DENSE, IMPLICIT_TRIDIAGONAL,
+                      OPT_STEP_OPERATOR_BYTES, OPT_KERNEL_TIMING, OPT_LAST_KERNEL_NS,
+                      OPT_TANGENT_FORM, TANGENT_DUAL, TANGENT_LINEARISED, IMPLICIT_DENSE, IMPLICIT_TRIDIAGONAL,
                       JV_FD, JV_TANGENT, NewtonOptions, NewtonReport, GradientOptions, GradientReport,
                       year_map_autograd, Ensemble, MODEL_N, MODEL_PHY, MODEL_NPZD, MODEL_NTRACER)

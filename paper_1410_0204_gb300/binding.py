@@ -33,6 +33,9 @@ OPT_STEP_OPERATORS = 7
 OPT_STEP_OPERATOR_BYTES = 8
 OPT_KERNEL_TIMING = 9
 OPT_LAST_KERNEL_NS = 10
+OPT_TANGENT_FORM = 11
+TANGENT_DUAL = 0
+TANGENT_LINEARISED = 1
 IMPLICIT_DENSE = 0
 IMPLICIT_TRIDIAGONAL = 1
 PLAN_PERSISTENT = 0

@@ -69,6 +69,13 @@ struct m3d_ctx {
     m3d::AdjointParams A{};
     size_t adj_smem_dense = 0, adj_smem_tri = 0;
     double *mfrac_b = nullptr;
+    // PO4-DOP linearised about a recorded trajectory (one internal step, resident plan): the
+    // linearised year kernels, whether they fit, which form metos3d_year_tangent uses, and the
+    // recorded df/dN of metos3d_year_tangent's own forward pass ([nstep][n_eu], made on demand)
+    ResidentKernels rk_lin{};
+    int lin_ok = 0, lin_tri_ok = 0;
+    int tangent_form = 0;               // M3D_TANGENT_DUAL or M3D_TANGENT_LINEARISED
+    double *fn_buf = nullptr;
     YearVariant tan;                    // the model with its tangent (PO4-DOP only)
     m3d::ResidentParams R_tan{};        // resident layout of the tangent (its own Thomas chains)
     int tan_ok = 0;
@@ -110,6 +117,10 @@ m3d_status m3d_year_device(m3d_ctx *c, const double *y0, double *y1);
 m3d_status m3d_set_params(m3d_ctx *c, const double *u, cudaMemcpyKind kind);
 // phi(y0) and phi'(y0) v with the parameters already in c->u_dev.
 m3d_status m3d_year_tangent_device(m3d_ctx *c, const double *y0, const double *v, double *phi, double *jv);
+// The year map recording df/dN of every euphotic cell and step into fn ([nstep][n_eu]); the
+// linearised year map phi'(y) v about the trajectory recorded in fn (c->lin_ok contexts).
+m3d_status m3d_year_record_device(m3d_ctx *c, const double *y0, double *y1, double *fn);
+m3d_status m3d_year_linear_device(m3d_ctx *c, const double *fn, const double *v, double *jv);
 // One TMM step j in the caller's layout (the step kernel; parameters already in c->u_dev and
 // the per-call tables made).
 m3d_status m3d_step_device(m3d_ctx *c, int j, const double *y, double *yn);

@@ -946,6 +946,7 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
     UP(upload_vec(c, &P.m0tab, m0tab));
     UP(upload_vec(c, &P.wtab, wtab));
     UP(upload_vec(c, &P.eu_list, eu_list));
+    P.n_eu = (int)eu_list.size();
     UP(upload_vec(c, &P.ap_list, ap_list));
     UP(upload_vec(c, &P.sh_list, sh_list));
     {
@@ -1134,6 +1135,25 @@ m3d_status metos3d_init(m3d_ctx **out, const m3d_grid *g, const m3d_matrices *mt
             c->tri_resident_ok = (long long)rps * prop.multiProcessorCount >= ntiles;
         }
         if (c->tri_resident_ok && !c->resident_ok) c->resident_ok = 1;
+        if (c->model == M3D_MODEL_NDOP && c->nsub == 1 && coop) {
+            // the linearised year kernels: the forward model's tiles, layouts and shared memory
+            c->rk_lin = resident_kernels<2, m3d::kModelNdopLinear>();
+            int rps = 0;
+            if (c->resident_smem <= (size_t)prop.sharedMemPerBlockOptin) {
+                UP(cudaFuncSetAttribute((const void *)c->rk_lin.year, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)c->resident_smem));
+                UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rps, (const void *)c->rk_lin.year, m3d::kThreads,
+                                                                 c->resident_smem));
+                c->lin_ok = (long long)rps * prop.multiProcessorCount >= ntiles;
+            }
+            if (c->tri_ok && c->resident_tri_smem <= (size_t)prop.sharedMemPerBlockOptin) {
+                UP(cudaFuncSetAttribute((const void *)c->rk_lin.year_tri, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)c->resident_tri_smem));
+                UP(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rps, (const void *)c->rk_lin.year_tri, m3d::kThreads,
+                                                                 c->resident_tri_smem));
+                c->lin_tri_ok = (long long)rps * prop.multiProcessorCount >= ntiles;
+            }
+        }
         c->plan = c->resident_ok ? M3D_PLAN_RESIDENT : (c->persistent_ok ? M3D_PLAN_PERSISTENT : M3D_PLAN_GRAPH);
         // the Thomas form wherever the plan in use can apply it
         const bool tri_here = c->plan == M3D_PLAN_RESIDENT ? c->tri_resident_ok : c->tri_stream_ok;
@@ -1399,6 +1419,45 @@ m3d_status run_year_tangent(m3d_ctx *c, double *out_y, double *out_v)
     return M3D_OK;
 }
 
+// The linearised year from ybuf[0] = v ([2][n]) about the trajectory recorded in fn; result
+// phi'(y) v into out (device).  Resident plan, the forward model's tiles and layouts.
+m3d_status run_year_linear(m3d_ctx *c, const double *fn, double *out)
+{
+    const bool tri = c->implicit_form == M3D_IMPLICIT_TRIDIAGONAL && c->lin_tri_ok && c->tri_resident_ok;
+    if (!(tri || (c->lin_ok && c->implicit_form == M3D_IMPLICIT_DENSE)))
+        return fail(c, M3D_ERR_UNSUPPORTED, "the linearised year kernel does not serve this context's plan");
+    m3d_status st = launch_prologue(c, c->u_dev);
+    if (st != M3D_OK) return st;
+    const int nb = (c->n + 255) / 256;
+    c->rk.to_interleaved<<<nb, 256, 0, c->stream>>>(c->n, c->ybuf[0], c->ybuf[1]);
+    CUDA_OR_FAIL(c, cudaGetLastError());
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.flags, 0, sizeof(int) * c->ntiles, c->stream));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.status, 0, sizeof(int) * 4, c->stream));
+    StepParams P = c->P;
+    P.fn_in = fn;
+    P.fn_out = nullptr;
+    m3d::ResidentParams R = c->R;
+    m3d::SyncParams S = c->S;
+    double *b0 = c->ybuf[1], *b1 = c->ybuf[0];
+    long long stride = -c->ybuf_cap;
+    int period = 2, j0 = 0, nsteps = c->nstep;
+    void *args[] = {&P, &R, &S, &b0, &stride, &period, &j0, &nsteps};
+    if (c->time_kernel) CUDA_OR_FAIL(c, cudaEventRecord(c->kev[0], c->stream));
+    CUDA_OR_FAIL(c, cudaLaunchCooperativeKernel((const void *)(tri ? c->rk_lin.year_tri : c->rk_lin.year),
+                                                dim3(c->ntiles), dim3(m3d::kThreads), args,
+                                                tri ? c->resident_tri_smem : c->resident_smem, c->stream));
+    if (c->time_kernel) {
+        CUDA_OR_FAIL(c, cudaEventRecord(c->kev[1], c->stream));
+        c->kev_recorded = 1;
+    }
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->status_host, c->S.status, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+    double *res = (nsteps & 1) ? b1 : b0;
+    c->rk.from_interleaved<<<nb, 256, 0, c->stream>>>(c->n, res, out);
+    CUDA_OR_FAIL(c, cudaGetLastError());
+    c->last_launches = 4;
+    return M3D_OK;
+}
+
 m3d_status reduce(m3d_ctx *c, int mode, const double *a, const double *b, double *out)
 {
     long long len = (long long)c->ntr * c->n;
@@ -1537,6 +1596,14 @@ m3d_status metos3d_set_option(m3d_ctx *c, int option, long long value)
         if (value == 1 && !c->resident_ok)
             return fail(c, M3D_ERR_UNSUPPORTED, "per-step operators serve the resident year kernel only");
         return set_step_operators(c, value == 1);
+    case M3D_OPT_TANGENT_FORM:
+        if (value != M3D_TANGENT_DUAL && value != M3D_TANGENT_LINEARISED)
+            return fail(c, M3D_ERR_ARG, "tangent form: M3D_TANGENT_DUAL or M3D_TANGENT_LINEARISED");
+        if (value == M3D_TANGENT_LINEARISED && (c->plan != M3D_PLAN_RESIDENT || !(c->lin_ok || c->lin_tri_ok)))
+            return fail(c, M3D_ERR_UNSUPPORTED, "the linearised tangent needs PO4-DOP, one internal step and the "
+                                                "resident plan");
+        c->tangent_form = (int)value;
+        return M3D_OK;
     case M3D_OPT_KERNEL_TIMING:
         if (value != 0 && value != 1) return fail(c, M3D_ERR_ARG, "kernel timing: 0 or 1");
         for (int i = 0; i < 2 && value == 1; i++)
@@ -1568,6 +1635,7 @@ long long metos3d_get_option(const m3d_ctx *c, int option)
     case M3D_OPT_STEP_OPERATORS: return c->sp_b != nullptr ? 1 : 0;
     case M3D_OPT_STEP_OPERATOR_BYTES: return (long long)c->sp_b_bytes;
     case M3D_OPT_KERNEL_TIMING: return c->time_kernel;
+    case M3D_OPT_TANGENT_FORM: return c->tangent_form;
     case M3D_OPT_LAST_KERNEL_NS: {
         float ms = 0.0f;
         if (!c->kev_recorded || cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]) != cudaSuccess) return -1;
@@ -1672,8 +1740,36 @@ cudaError_t m3d_alloc(m3d_ctx *c, void **p, size_t bytes)
     return e;
 }
 
+m3d_status m3d_year_record_device(m3d_ctx *c, const double *y0, double *y1, double *fn)
+{
+    if (!c->lin_ok && !c->lin_tri_ok) return fail(c, M3D_ERR_UNSUPPORTED, "this context has no linearised year map");
+    if (c->plan != M3D_PLAN_RESIDENT) return fail(c, M3D_ERR_UNSUPPORTED, "recording needs the resident plan");
+    double *saved = c->P.fn_out;
+    c->P.fn_out = fn;
+    m3d_status st = m3d_year_device(c, y0, y1);
+    c->P.fn_out = saved;
+    return st;
+}
+
+m3d_status m3d_year_linear_device(m3d_ctx *c, const double *fn, const double *v, double *jv)
+{
+    const size_t len = sizeof(double) * (size_t)c->ntr * c->n;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], v, len, cudaMemcpyDeviceToDevice, c->stream));
+    return run_year_linear(c, fn, jv);
+}
+
 m3d_status m3d_year_tangent_device(m3d_ctx *c, const double *y0, const double *v, double *phi, double *jv)
 {
+    if (c->tangent_form == M3D_TANGENT_LINEARISED) {
+        if (!c->fn_buf) {
+            void *p = nullptr;
+            CUDA_OR_FAIL(c, m3d_alloc(c, &p, sizeof(double) * (size_t)c->nstep * (size_t)std::max(c->P.n_eu, 1)));
+            c->fn_buf = (double *)p;
+        }
+        m3d_status st = m3d_year_record_device(c, y0, phi, c->fn_buf);
+        if (st != M3D_OK) return st;
+        return m3d_year_linear_device(c, c->fn_buf, v, jv);
+    }
     if (!c->tan_ok) return fail(c, M3D_ERR_UNSUPPORTED, "this model has no tangent year kernel");
     const size_t half = sizeof(double) * (size_t)c->ntr * c->n;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], y0, half, cudaMemcpyDeviceToDevice, c->stream));

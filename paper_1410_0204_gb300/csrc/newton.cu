@@ -120,6 +120,7 @@ struct Workspace {
     double *H = nullptr;        // [m+1][m] column-major Hessenberg (device)
     double *part = nullptr, *scal = nullptr;
     double *g = nullptr, *cs = nullptr, *sn = nullptr, *yk = nullptr;   // [m+1], [m], [m], [m] (device)
+    double *fn_cur = nullptr, *fn_next = nullptr;   // recorded source-term Jacobians (linearised tangent)
     KrylovStatus *kst = nullptr;              // device
     KrylovStatus *kst_host = nullptr;         // pinned, three slots
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -131,6 +132,7 @@ struct Solver {
     long long N;
     int grid;
     bool tangent = false;           // Jacobian-vector products by the tangent year map
+    bool linear = false;            // ... by the linearised sweep about the recorded trajectory
     int applies = 0;                // operator applications a GMRES call carried out
 
     m3d_status launch_ok() { CUDA_OR_FAIL(c, cudaGetLastError()); return M3D_OK; }
@@ -185,6 +187,12 @@ struct Solver {
 m3d_status apply_jacobian(Solver &S, const double *y, const double *py, double ynorm, double eps,
                           const double *v, double vnorm, double *w, int *year_maps)
 {
+    if (S.linear) {
+        m3d_status st = m3d_year_linear_device(S.c, S.W.fn_cur, v, S.W.tmp);
+        if (st != M3D_OK) return st;
+        k_axpby<<<S.grid, 256, 0, S.c->stream>>>(w, 1.0, v, -1.0, S.W.tmp, S.N);
+        return S.launch_ok();
+    }
     if (S.tangent) {
         m3d_status st = m3d_year_tangent_device(S.c, y, v, S.W.phv, S.W.tmp);
         if (st != M3D_OK) return st;
@@ -450,7 +458,8 @@ void release_workspace(m3d_ctx *c, Workspace &W)
     if (W.kst_host) cudaFreeHost(W.kst_host);
     for (cudaEvent_t e : W.ev)
         if (e) cudaEventDestroy(e);
-    void *ptrs[] = {W.V, W.w, W.F, W.py, W.s, W.y, W.yn, W.pyn, W.tmp, W.phv, W.x, W.H, W.part, W.scal, W.g, W.kst};
+    void *ptrs[] = {W.V, W.w, W.F, W.py, W.s, W.y, W.yn, W.pyn, W.tmp, W.phv, W.x, W.H, W.part, W.scal, W.g, W.kst,
+                    W.fn_cur, W.fn_next};
     for (void *p : ptrs) {
         if (!p) continue;
         for (size_t i = 0; i < c->allocs.size(); i++)
@@ -534,9 +543,26 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
     memset(&R, 0, sizeof R);
     Solver S{c, {}, 0, 0};
     S.tangent = o.jv == M3D_JV_TANGENT;
+    // exact products by the linearised sweep where the context has it: the line search records
+    // the source term's Jacobian along the year maps it evaluates anyway
+    S.linear = S.tangent && c->plan == M3D_PLAN_RESIDENT && (c->lin_ok || c->lin_tri_ok);
     m3d_status st = ensure_workspace(c, S, o.restart);
+    if (st == M3D_OK && S.linear) {
+        void *p = nullptr;
+        const size_t fnb = sizeof(double) * (size_t)c->nstep * (size_t)std::max(c->P.n_eu, 1);
+        cudaError_t e = m3d_alloc(c, &p, fnb);
+        if (e == cudaSuccess) { S.W.fn_cur = (double *)p; e = m3d_alloc(c, &p, fnb); }
+        if (e == cudaSuccess) S.W.fn_next = (double *)p;
+        if (e != cudaSuccess) st = fail(c, M3D_ERR_CUDA, "metos3d_newton_solve: %s", cudaGetErrorString(e));
+    }
     if (st != M3D_OK) { release_workspace(c, S.W); return st; }
     Workspace &W = S.W;
+    // phi(y), recording the source term's Jacobian into fn when the products are linearised sweeps
+    auto phi_rec = [&](const double *yy, double *out, double *fn) -> m3d_status {
+        if (!S.linear) return S.phi(yy, out, &R.year_maps);
+        R.year_maps++;
+        return m3d_year_record_device(c, yy, out, fn);
+    };
     const long long N = S.N;
     auto finish = [&](m3d_status s) {
         R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -552,7 +578,7 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
     TRY(S.dot_dev(c->vol, c->vol, W.scal, false, c->n));
     TRY(S.read(W.scal, &wsum, 1));
     wsum *= c->ntr;
-    TRY(S.phi(W.y, W.py, &R.year_maps));
+    TRY(phi_rec(W.y, W.py, W.fn_cur));
     TRY(metos3d_sync(c));
     TRY(S.axpby(W.F, 1.0, W.y, -1.0, W.py));
     double r = 0.0;
@@ -595,7 +621,7 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
         int trials = 0;
         while (true) {
             TRY(S.axpby(W.yn, 1.0, W.y, lam, W.s));
-            TRY(S.phi(W.yn, W.pyn, &R.year_maps));
+            TRY(phi_rec(W.yn, W.pyn, W.fn_next));
             TRY(metos3d_sync(c));
             TRY(S.axpby(W.tmp, 1.0, W.yn, -1.0, W.pyn));
             double rn = 0.0;
@@ -613,6 +639,7 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
         std::swap(W.y, W.yn);
         std::swap(W.py, W.pyn);
         std::swap(W.F, W.tmp);
+        std::swap(W.fn_cur, W.fn_next);
         r_prev = r;
         eta_prev = eta;
         r = std::sqrt(2.0 * fn);

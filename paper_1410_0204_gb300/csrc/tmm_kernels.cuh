@@ -30,6 +30,9 @@ static_assert(kSpThreads % 128 == 0, "the explicit group must span the four SM s
 constexpr int kModelNone = 0;
 constexpr int kModelNdop = 2;
 constexpr int kModelNdopTangent = 102;   // PO4-DOP with its tangent: state (N, DOP, dN, dDOP)
+// The PO4-DOP model linearised about a trajectory recorded beforehand: state (dN, dDOP); the
+// source term's Jacobian comes from the recorded df/dN of every euphotic cell and step.
+constexpr int kModelNdopLinear = 103;
 constexpr double kSigmaPar = 0.4;    // photosynthetically available fraction of I_SWR
 constexpr int kEuphotic = 2;         // euphotic layers (Section 7: two)
 
@@ -89,6 +92,12 @@ struct StepParams {
     const double *mfrac;                   // [n] Martin deposition profile (aphotic cells; per call)
     const double *I0tab;                   // [nstep][nulat] daily-mean I_SWR at t_j
     const double *qpar;                    // [kQCount] model scalars (per call)
+    // Linearisation of the PO4-DOP source term (one internal step): df/dN of every entry e of
+    // eu_list at step j, [nstep][n_eu].  fn_out (null: not recorded) receives it while a year
+    // map runs; the linearised year kernel reads fn_in.
+    double *fn_out;
+    const double *fn_in;
+    int n_eu;
 };
 
 // Month weights (Section 3): month m is centred at t = (m + 1/2)/nmonth; t_j = j/nstep.
@@ -321,6 +330,14 @@ template <> struct ModelState<Dual> {
     __device__ __forceinline__ static Dual get_e(const double *ek, int zmax, int i) { return {ek[i], ek[zmax + i]}; }
 };
 
+// Whether the source term of scalar type T records its Jacobian for a linearised sweep (the
+// plain model does; its tangent on dual numbers does not).
+template <class T> struct ModelTraits_record { static constexpr bool ok = false; };
+template <> struct ModelTraits_record<double> {
+    static constexpr bool ok = true;
+    __device__ __forceinline__ static double value(double v) { return v; }
+};
+
 // The source-minus-sink increment of the PO4-DOP model (Section 2.2.1) for every cell of a
 // tile, computed from y_j and written to dq[t * zmax + i].  Reads only the tile's own cells.
 // Run by threads [tid0, tid0 + nthr) of the CTA, which synchronise on barrier `bar`:
@@ -361,8 +378,17 @@ __device__ __forceinline__ void ndop_source_tile(const StepParams &P, const Tile
             }
         } else {
             T dN, dD, fsum;
-            ndop_euphotic<T>(MS::get(Y, cell, 0), MS::get(Y, cell, 1), I0 * __ldg(P.atten + cell), alpha, sigma,
+            const double I = I0 * __ldg(P.atten + cell);
+            ndop_euphotic<T>(MS::get(Y, cell, 0), MS::get(Y, cell, 1), I, alpha, sigma,
                              lambda, KN, KI, ds, nsub, dN, dD, fsum);
+            if constexpr (ModelTraits_record<T>::ok) {
+                if (P.fn_out && nsub == 1) {
+                    // df/dN = alpha I K_N / ((N + K_N)^2 (I + K_I)), the Jacobian a linearised sweep needs
+                    const double N = ModelTraits_record<T>::value(MS::get(Y, cell, 0));
+                    const double d = N + KN;
+                    P.fn_out[(size_t)j * P.n_eu + e] = (alpha * I * KN) / (d * d * (I + KI));
+                }
+            }
             MS::put(dq, zmax, i, 0, dN);
             MS::put(dq, zmax, i, 1, dD);
             MS::put_e(ek, zmax, i, oms * fsum * __ldg(P.h + cell));
@@ -389,10 +415,57 @@ __device__ __forceinline__ void ndop_source_tile(const StepParams &P, const Tile
     }
 }
 
+// The PO4-DOP increment linearised about a recorded trajectory (one internal step): for the
+// perturbation (dN, dDOP) of y_j, with f_N = df/dN recorded at step j,
+//   euphotic: df = f_N dN,  d(dq_N) = ds (lambda dDOP - df),  d(dq_DOP) = ds (sigma df - lambda dDOP),
+//   export:   dE = (1 - sigma) sum over the column's euphotic cells of df h,
+//   aphotic:  d(dq_N) = ds (lambda dDOP + mfrac dE),  d(dq_DOP) = -ds lambda dDOP,
+//   shallow column: its bottom layer also gets ds dE / h.
+// The same structure and threads as ndop_source_tile.
+template <class SV>
+__device__ __forceinline__ void ndop_source_tile_linear(const StepParams &P, const Tile &T_, int j, const SV &Y,
+                                                        double *dq, double *ek, int nthr, int bar, int tid0 = 0)
+{
+    const int tid = (int)threadIdx.x - tid0;
+    const int zmax = P.zmax;
+    const double sigma = __ldg(P.qpar + kQSigma), lambda = __ldg(P.qpar + kQLambda);
+    const double oms = __ldg(P.qpar + kQOneMinusSigma);
+    const double ds = P.ds;
+    const double *fn = P.fn_in + (size_t)j * P.n_eu;
+    for (int e = T_.eu0 + tid; e < T_.eu1; e += nthr) {
+        const int i = __ldg(P.eu_list + e);
+        const int cell = T_.cell0 + i;
+        const double dN = Y.get(cell, 0), dD = Y.get(cell, 1);
+        const double df = __ldg(fn + e) * dN;
+        const double lD = lambda * dD;
+        dq[i] = ds * (lD - df);
+        dq[zmax + i] = ds * (sigma * df - lD);
+        ek[i] = oms * df * __ldg(P.h + cell);
+    }
+    barrier_sub(bar);
+    for (int a = T_.ap0 + tid; a < T_.ap1; a += nthr) {
+        const int i = __ldg(P.ap_list + a);
+        const int cell = T_.cell0 + i;
+        const int k = __ldg(P.cell_kl + cell) & 0xff;
+        const double Esum = ek[i - k] + ek[i - k + 1];
+        const double lD = lambda * Y.get(cell, 1);
+        dq[i] = ds * (lD + __ldg(P.mfrac + cell) * Esum);
+        dq[zmax + i] = ds * (-lD);
+    }
+    for (int b = T_.sh0 + tid; b < T_.sh1; b += nthr) {
+        const int i = __ldg(P.sh_list + b);
+        const int cell = T_.cell0 + i;
+        const int k = __ldg(P.cell_kl + cell) & 0xff;
+        const double Esum = (k == 0) ? ek[i] : ek[i - 1] + ek[i];
+        dq[i] += ds * (Esum / __ldg(P.h + cell));
+    }
+}
+
 // Whether a model has a source term, and its scalar type.
 template <int MODEL> struct ModelTraits { static constexpr bool has_q = false; typedef double scalar; };
 template <> struct ModelTraits<kModelNdop> { static constexpr bool has_q = true; typedef double scalar; };
 template <> struct ModelTraits<kModelNdopTangent> { static constexpr bool has_q = true; typedef Dual scalar; };
+template <> struct ModelTraits<kModelNdopLinear> { static constexpr bool has_q = true; typedef double scalar; };
 
 // One TMM step on one tile.  smem: (NTR + 2) * zmax doubles.
 // Order: q increment of the tile's own cells into z (no neighbour data needed), then

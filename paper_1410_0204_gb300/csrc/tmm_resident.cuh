@@ -421,7 +421,10 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
         // forms z = A_exp y.  The source term's divisions and sums are latency-bound and the
         // explicit part is FP64-throughput-bound, so together they keep the FP64 pipes busier.
         if ((int)threadIdx.x >= kSpThreads) {
-            if (ModelTraits<MODEL>::has_q) {
+            if (MODEL == kModelNdopLinear) {
+                const StateView<NTR, true, true> Y{y, P.n};
+                ndop_source_tile_linear(P, T, j, Y, M.dq, M.ek, kQThreads, 2, kSpThreads);
+            } else if (ModelTraits<MODEL>::has_q) {
                 const StateView<NTR, true, true> Y{y, P.n};
                 ndop_source_tile<typename ModelTraits<MODEL>::scalar>(P, T, j, Y, M.dq, M.ek, kQThreads, 2,
                                                                       kSpThreads);

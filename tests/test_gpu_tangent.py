@@ -80,3 +80,43 @@ def test_year_tangent_matches_oracle_benchmark_grid(m3d):
     assert rel_err(phi.cpu().numpy(), want_phi) < 1e-10
     assert rel_err(jv.cpu().numpy(), want_jv) < 1e-10
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["tiny_6x4x4", "tiny_4x3x3", "ndop_64x32x8", "ndop_128x64x15"])
+def test_linearised_tangent_matches_oracle(m3d, name):
+    """phi'(y) v by the linearised sweep (the year map recording df/dN, then one sweep of the
+    perturbation alone) against the oracle's tangent year map, and against the one-pass
+    tangent on dual numbers."""
+    import os
+    p = mi.make_problem(name)
+    P = oracle.Problem(p)
+    u = mi.default_params_ndop()
+    y = mi.random_state(p)
+    v = mi.random_state(p, seed=5) - mi.random_state(p, seed=6)
+    ctx = m3d.Context.from_problem(p)
+    phi = torch.empty((2, p.n), dtype=torch.float64, device="cuda")
+    jv = torch.empty_like(phi)
+    ctx.year_tangent(cuda(y), cuda(v), cuda(u), phi, jv)          # dual numbers (default)
+    ctx.sync()
+    jv_dual = jv.cpu().numpy()
+    assert ctx.get_option(m3d.OPT_TANGENT_FORM) == m3d.TANGENT_DUAL
+    ctx.set_option(m3d.OPT_TANGENT_FORM, m3d.TANGENT_LINEARISED)
+    ctx.year_tangent(cuda(y), cuda(v), cuda(u), phi, jv)
+    ctx.sync()
+    oracle.set_threads(os.cpu_count() or 1)
+    try:
+        want_phi, want_jv = oracle.year_tangent(P, y, v, u)
+    finally:
+        oracle.set_threads(1)
+    assert rel_err(phi.cpu().numpy(), want_phi) < 1e-10
+    assert rel_err(jv.cpu().numpy(), want_jv) < 1e-10
+    assert rel_err(jv.cpu().numpy(), jv_dual) < 1e-10
+    ctx.close()
+
+
+def test_linearised_tangent_needs_one_internal_step(m3d):
+    p = mi.make_problem("tiny_6x4x4")
+    ctx = m3d.Context.from_problem(p, nsub=8)
+    with pytest.raises(m3d.Metos3dError):
+        ctx.set_option(m3d.OPT_TANGENT_FORM, m3d.TANGENT_LINEARISED)
+    ctx.close()
