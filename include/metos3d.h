@@ -45,8 +45,9 @@ typedef enum {
 /*
  * Biogeochemical models (Section 2.2).  A single context (metos3d_init) runs every model: NONE
  * and NDOP with the tiled year kernels (and, for NDOP, the tangent and adjoint), N, PHY and
- * NPZD through a one-member ensemble (year map, steps, spin-up, Newton-Krylov with
- * finite-difference products, diagnostics).  Ensembles (metos3d_ensemble_init) run N, NDOP,
+ * NPZD through a one-member ensemble (year map, steps, spin-up, the tangent year map by a
+ * one-member tangent ensemble, Newton-Krylov with finite-difference or tangent products,
+ * diagnostics).  Ensembles (metos3d_ensemble_init) run N, NDOP,
  * PHY and NPZD members side by side.  The parameters of each model are listed with the
  * ensemble calls below.
  */
@@ -149,9 +150,11 @@ m3d_status metos3d_year_map_host(m3d_ctx *ctx, const double *y0_host, double *y1
  * by algorithmic differentiation as the alternative to finite differences):
  * phi_out = phi(y0) and jv_out = phi'(y0) v in one pass over the year, the state and its
  * direction advanced together through every step, so each matrix entry is read once for
- * both.  The source term's tangent is the model code evaluated on dual numbers.
- * PO4-DOP only (M3D_ERR_UNSUPPORTED otherwise).  Device arrays [ntracer][n]; u: device
- * [nparam].  Asynchronous.
+ * both.  The source term's tangent is the model code evaluated on dual numbers.  Every
+ * model: PO4-DOP by the tiled tangent kernels (or the linearised sweep, M3D_OPT_TANGENT_FORM),
+ * N, PO4-DOP-PHY and NPZD-DOP by a one-member tangent ensemble (metos3d_ensemble_init_tangent;
+ * synchronous for those, as it hands the parameters to the ensemble).  Device arrays
+ * [ntracer][n]; u: device [nparam].  Asynchronous.
  */
 m3d_status metos3d_year_tangent(m3d_ctx *ctx, const double *y0, const double *v, const double *u,
                                 double *phi_out, double *jv_out);
@@ -462,8 +465,23 @@ m3d_status metos3d_ensemble_init(m3d_ensemble **ens, const m3d_grid *grid, const
                                  void *stream);
 
 /*
- * Sizes: members, W (total tracers), n, 32-lane groups.  offsets (may be NULL) receives
- * nmember + 1 row offsets of the members in the [W][n] state.
+ * A tangent ensemble (Section 6: exact derivatives, the tangent-linear model): every member
+ * carries its state and a perturbation of it, and each step advances both, the perturbation
+ * through the step's derivative (the models' source terms on dual numbers, the transport as
+ * it is).  The state arrays of its calls are [2W][n]: rows 0 .. W-1 the members' states
+ * (member m's at offset_m as above), rows W .. 2W-1 their perturbations in the same order.
+ * metos3d_ensemble_year_map on it returns [phi(y); phi'(y) v] for every member at once, the
+ * Jacobian-vector products of a Newton-Krylov solve per member.  Otherwise as
+ * metos3d_ensemble_init (a member takes twice its tracer count of lanes).
+ */
+m3d_status metos3d_ensemble_init_tangent(m3d_ensemble **ens, const m3d_grid *grid, const m3d_matrices *mats,
+                                         int nmember, const m3d_member *members, int nsub, int nstep,
+                                         void *stream);
+
+/*
+ * Sizes: members, the state rows of the calls (W, the total tracer count; 2W for a tangent
+ * ensemble), n, 32-lane groups.  offsets (may be NULL) receives nmember + 1 row offsets of
+ * the members' states.
  */
 m3d_status metos3d_ensemble_layout(const m3d_ensemble *ens, int *nmember, int *width, int *n,
                                    int *ngroup, int *offsets);

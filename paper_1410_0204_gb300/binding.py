@@ -188,6 +188,8 @@ def load(build_if_missing: bool = False):
     L.metos3d_residual_static_error.restype = C.c_char_p
     L.metos3d_ensemble_init.argtypes = [C.POINTER(vp), C.POINTER(_Grid), C.POINTER(_Matrices), C.c_int,
                                         C.POINTER(_Member), C.c_int, C.c_int, vp]
+    L.metos3d_ensemble_init_tangent.argtypes = [C.POINTER(vp), C.POINTER(_Grid), C.POINTER(_Matrices), C.c_int,
+                                                C.POINTER(_Member), C.c_int, C.c_int, vp]
     L.metos3d_ensemble_layout.argtypes = [vp, ip, ip, ip, ip, ip]
     L.metos3d_ensemble_set_stream.argtypes = [vp, vp]
     L.metos3d_ensemble_set_params.argtypes = [vp, C.c_int, dp]
@@ -506,11 +508,13 @@ class Ensemble:
 
     ``members``: a sequence of (model_id, u) pairs or of objects with ``model`` and ``u``.
     States are CUDA float64 tensors of shape (W, n): member m's tracers are rows
-    ``offsets[m]:offsets[m + 1]``.
+    ``offsets[m]:offsets[m + 1]``.  ``tangent=True`` makes a tangent ensemble
+    (metos3d_ensemble_init_tangent): states of shape (2W, n), the members' states on top of
+    their perturbations; ``year_map`` then returns [phi(y); phi'(y) v].
     """
 
     def __init__(self, *, col_start, h, zc, vol, lat, exp_rowptr, exp_colidx, exp_val, imp_blk, members,
-                 nsub=1, nstep=2880, stream=None):
+                 nsub=1, nstep=2880, stream=None, tangent=False):
         torch = _torch()
         L = load()
         self._L = L
@@ -533,8 +537,10 @@ class Ensemble:
             stream = torch.cuda.current_stream()
         self._stream = stream
         e = C.c_void_p()
-        _echeck(L.metos3d_ensemble_init(C.byref(e), C.byref(g), C.byref(m), len(specs), mem, int(nsub), int(nstep),
-                                        C.c_void_p(stream.cuda_stream)))
+        init = L.metos3d_ensemble_init_tangent if tangent else L.metos3d_ensemble_init
+        _echeck(init(C.byref(e), C.byref(g), C.byref(m), len(specs), mem, int(nsub), int(nstep),
+                     C.c_void_p(stream.cuda_stream)))
+        self.tangent = bool(tangent)
         self._e = e
         self.models = [mdl for mdl, _ in specs]
         self.nparams = [u.shape[0] for _, u in specs]

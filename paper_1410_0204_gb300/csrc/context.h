@@ -98,6 +98,12 @@ struct m3d_ctx {
     m3d_ensemble *ens = nullptr;
     std::vector<double> ens_u;          // the parameters last given to it
     int ens_u_valid = 0;
+    // ... and its tangent: a one-member tangent ensemble (state and perturbation), the
+    // parameters last given to it, and a staging pair of [2 ntracer][n] arrays
+    m3d_ensemble *ens_tan = nullptr;
+    std::vector<double> ens_tan_u;
+    int ens_tan_u_valid = 0;
+    double *tan_buf = nullptr;
 };
 
 // Record a failure on c (or for metos3d_init when c is null) and return s.

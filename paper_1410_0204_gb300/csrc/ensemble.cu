@@ -85,6 +85,171 @@ __host__ __device__ inline size_t ens_smem_bytes(int nnz_blk_max, int cells_blk_
            sizeof(int) * ((size_t)nnz_blk_max + 4);
 }
 
+// A member's tracer t at layer k of the column's staging array st: the value, or for a
+// member that carries its tangent (T = Dual) the value and its perturbation, which sits
+// ntr lanes further on.
+template <class T> struct EnsLane;
+template <> struct EnsLane<double> {
+    __device__ __forceinline__ static double get(const double *st, int k, int l0, int t, int)
+    {
+        return st[k * kLanes + l0 + t];
+    }
+    // the increment: z += ds q (one internal step) or q into the substep buffer
+    template <bool SUB1>
+    __device__ __forceinline__ static void emit(double *zs, double *qs, double ds, int k, int l0, int t, int, double q)
+    {
+        if (SUB1) zs[k * kLanes + l0 + t] = fma(ds, q, zs[k * kLanes + l0 + t]);
+        else qs[k * kLanes + l0 + t] = q;
+    }
+    __device__ __forceinline__ static double madd(double a, double b, double c) { return fma(a, b, c); }
+    __device__ __forceinline__ static double partner_sum(double e) { return e + __shfl_xor_sync(kFull, e, 1); }
+    __device__ __forceinline__ static void put_export(double *Es, int ml, double v) { Es[ml] = v; }
+    __device__ __forceinline__ static double get_export(const double *Es, int ml) { return Es[ml]; }
+};
+template <> struct EnsLane<m3d::Dual> {
+    __device__ __forceinline__ static m3d::Dual get(const double *st, int k, int l0, int t, int ntr)
+    {
+        return {st[k * kLanes + l0 + t], st[k * kLanes + l0 + ntr + t]};
+    }
+    template <bool SUB1>
+    __device__ __forceinline__ static void emit(double *zs, double *qs, double ds, int k, int l0, int t, int ntr,
+                                                m3d::Dual q)
+    {
+        EnsLane<double>::emit<SUB1>(zs, qs, ds, k, l0, t, 0, q.v);
+        EnsLane<double>::emit<SUB1>(zs, qs, ds, k, l0 + ntr, t, 0, q.d);
+    }
+    __device__ __forceinline__ static m3d::Dual madd(m3d::Dual a, double b, m3d::Dual c) { return a * b + c; }
+    __device__ __forceinline__ static m3d::Dual partner_sum(m3d::Dual e)
+    {
+        return {e.v + __shfl_xor_sync(kFull, e.v, 1), e.d + __shfl_xor_sync(kFull, e.d, 1)};
+    }
+    __device__ __forceinline__ static void put_export(double *Es, int ml, m3d::Dual v)
+    {
+        Es[2 * ml] = v.v;
+        Es[2 * ml + 1] = v.d;
+    }
+    __device__ __forceinline__ static m3d::Dual get_export(const double *Es, int ml) { return {Es[2 * ml], Es[2 * ml + 1]}; }
+};
+
+// The source terms of one segment (members of one model in one lane group) on one column,
+// the warp's lanes dealt to (member, layer) pairs.  T = double: the models; T = Dual: the
+// models and their tangents, for members that carry a perturbation in the ntr lanes after
+// their state.
+template <class T, bool SUB1>
+__device__ __forceinline__ void ens_segment_q(const EnsParams &E, const int4 &S, int c, int s0, int L, double I0,
+                                              int lane, const double *st, double *zs, double *qs, double *Es)
+{
+    typedef EnsLane<T> A;
+    const int model = S.x, nm = S.z - S.y;
+    const int neu = L < 2 ? L : 2, na = L - neu;
+    const double ds = E.ds;
+    if (model == M3D_MODEL_NPZD) {
+        const int ntr = 5;
+        for (int base = 0; base < nm * L; base += kLanes) {
+            const int p = base + lane;
+            if (p >= nm * L) continue;
+            const int ml = p / L, k = p - ml * L, mi = S.y + ml;
+            const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
+            const double *mp = E.mpar + (size_t)pid * kParSlots;
+            const T N = A::get(st, k, l0, 0, ntr), P = A::get(st, k, l0, 1, ntr);
+            const T Z = A::get(st, k, l0, 2, ntr), D = A::get(st, k, l0, 3, ntr);
+            const T DOP = A::get(st, k, l0, 4, ntr);
+            // one division for both rates: U = mu_P P N/(N+K_N) I/(I+K_I) (I = 0 below
+            // the euphotic zone) and G = mu_Z Z P/(K_P+P)
+            const double I = k < neu ? I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k] : 0.0;
+            const T dN = N + mp[3];
+            const double dI = I + mp[4];
+            const T dP = mp[6] + P;
+            const T dNI = dN * dI;
+            const T r = 1.0 / (dNI * dP);
+            const T U = mp[2] * P * N * I * dP * r;
+            const T G = mp[5] * Z * P * dNI * r;
+            const T mP = mp[8] * P, mZ = mp[9] * Z * Z, eZ = mp[10] * Z;
+            const T rD = mp[11] * D, rO = mp[12] * DOP;
+            const T zero{};
+            const T Sin = k > 0 ? mp[13] * A::get(st, k - 1, l0, 3, ntr) : zero;
+            const T Sout = k + 1 < L ? mp[13] * D : zero;
+            const double hk = E.h[s0 + k];
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 0, ntr, -U + rO);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 1, ntr, U - G - mP);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 2, ntr, mp[7] * G - mZ - eZ);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 3, ntr, mP + mZ - rD + (Sin - Sout) / hk);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 4, ntr, mp[14] * G + eZ + rD - rO);
+        }
+        return;
+    }
+    // Martin models (N, NDOP, PHY): euphotic pairs, export E reduced over the member's
+    // euphotic layers (adjacent lanes), then the aphotic pairs
+    const int ntr = model == M3D_MODEL_N ? 1 : model == M3D_MODEL_NDOP ? 2 : 3;
+    for (int base = 0; base < nm * neu; base += kLanes) {
+        const int p = base + lane;
+        const bool act = p < nm * neu;
+        const int ml = act ? p / neu : 0, k = act ? p - ml * neu : 0, mi = S.y + ml;
+        T e{}, q0{}, q1{}, q2{};
+        int l0 = 0, pid = 0;
+        if (act) {
+            l0 = E.mem_lane0[mi];
+            pid = E.mem_pidx[mi];
+            const double *mp = E.mpar + (size_t)pid * kParSlots;
+            const double I = I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k];
+            const double hk = E.h[s0 + k];
+            const T N = A::get(st, k, l0, 0, ntr);
+            // both half-saturation factors with one division
+            const T lim = (N * I) / ((N + mp[3]) * (I + mp[4]));
+            if (model == M3D_MODEL_N) {
+                const T f = mp[2] * lim;
+                q0 = -f;
+                e = f * hk;
+            } else if (model == M3D_MODEL_NDOP) {
+                const T DOP = A::get(st, k, l0, 1, ntr);
+                const T f = mp[2] * lim;
+                q0 = -f + mp[6] * DOP;
+                q1 = mp[5] * f - mp[6] * DOP;
+                e = mp[7] * f * hk;
+            } else {                                   // PHY
+                const T DOP = A::get(st, k, l0, 1, ntr), PHY = A::get(st, k, l0, 2, ntr);
+                const T f1 = mp[2] * PHY * lim;
+                const T f3 = mp[10] * f1;
+                const T loss = mp[7] * PHY + mp[8] * PHY * PHY;
+                q0 = -f1 + mp[5] * DOP;
+                q1 = mp[6] * f3 + loss - mp[5] * DOP + mp[9] * PHY;
+                q2 = mp[11] * f1 - loss - mp[9] * PHY;
+                e = mp[12] * f3 * hk;
+            }
+        }
+        const T Eg = neu == 2 ? A::partner_sum(e) : e;
+        if (act) {
+            if (L <= 2 && k == L - 1) q0 = A::madd(Eg, E.mfrac[(size_t)pid * E.n + s0 + k], q0);
+            if (k == 0) A::put_export(Es, ml, Eg);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 0, ntr, q0);
+            if (model != M3D_MODEL_N) A::template emit<SUB1>(zs, qs, ds, k, l0, 1, ntr, q1);
+            if (model == M3D_MODEL_PHY) A::template emit<SUB1>(zs, qs, ds, k, l0, 2, ntr, q2);
+        }
+    }
+    __syncwarp();
+    for (int base = 0; base < nm * na; base += kLanes) {
+        const int p = base + lane;
+        if (p >= nm * na) continue;
+        const int ml = p / na, k = neu + (p - ml * na), mi = S.y + ml;
+        const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
+        const double *mp = E.mpar + (size_t)pid * kParSlots;
+        const T dep = A::get_export(Es, ml) * E.mfrac[(size_t)pid * E.n + s0 + k];
+        if (model == M3D_MODEL_N) {
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 0, ntr, dep);
+        } else if (model == M3D_MODEL_NDOP) {
+            const T DOP = A::get(st, k, l0, 1, ntr);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 0, ntr, dep + mp[6] * DOP);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 1, ntr, -(mp[6] * DOP));
+        } else {
+            const T DOP = A::get(st, k, l0, 1, ntr), PHY = A::get(st, k, l0, 2, ntr);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 0, ntr, dep + mp[5] * DOP);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 1, ntr, -(mp[5] * DOP) + mp[9] * PHY);
+            A::template emit<SUB1>(zs, qs, ds, k, l0, 2, ntr, -(mp[9] * PHY));
+        }
+    }
+    __syncwarp();
+}
+
 template <bool SUB1>
 __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, int j, const double *__restrict__ X,
                                                                  double *__restrict__ Xn)
@@ -161,119 +326,13 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, in
 
         // 2. source terms, lanes over (member, layer) pairs
         const double I0 = E.I0tab[(size_t)j * E.nulat + E.col_ulat[c]];
-        const int neu = L < 2 ? L : 2, na = L - neu;
         const int sg0 = E.grp_seg_off[g], sg1 = E.grp_seg_off[g + 1];
         for (int sub = 0; sub < (SUB1 ? 1 : E.nsub); sub++) {
             const double *st = SUB1 ? ys : yw;
-            // emit q of tracer t of the member whose first lane is l0, layer k
-            auto emit = [&](int k, int l0, int t, double q) {
-                if (SUB1) zs[k * kLanes + l0 + t] = fma(E.ds, q, zs[k * kLanes + l0 + t]);
-                else qs[k * kLanes + l0 + t] = q;
-            };
             for (int sg = sg0; sg < sg1; sg++) {
                 const int4 S = E.segs[sg];
-                const int model = S.x, nm = S.z - S.y;
-                if (model == M3D_MODEL_NPZD) {
-                    for (int base = 0; base < nm * L; base += kLanes) {
-                        const int p = base + lane;
-                        if (p >= nm * L) continue;
-                        const int ml = p / L, k = p - ml * L, mi = S.y + ml;
-                        const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
-                        const double *mp = E.mpar + (size_t)pid * kParSlots;
-                        const double N = st[k * kLanes + l0], P = st[k * kLanes + l0 + 1];
-                        const double Z = st[k * kLanes + l0 + 2], D = st[k * kLanes + l0 + 3];
-                        const double DOP = st[k * kLanes + l0 + 4];
-                        // one division for both rates: U = mu_P P N/(N+K_N) I/(I+K_I) (I = 0 below
-                        // the euphotic zone) and G = mu_Z Z P/(K_P+P)
-                        const double I = k < neu ? I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k] : 0.0;
-                        const double dN = N + mp[3], dI = I + mp[4], dP = mp[6] + P;
-                        const double dNI = dN * dI;
-                        const double r = 1.0 / (dNI * dP);
-                        const double U = mp[2] * P * N * I * dP * r;
-                        const double G = mp[5] * Z * P * dNI * r;
-                        const double mP = mp[8] * P, mZ = mp[9] * Z * Z, eZ = mp[10] * Z;
-                        const double rD = mp[11] * D, rO = mp[12] * DOP;
-                        const double Sin = k > 0 ? mp[13] * st[(k - 1) * kLanes + l0 + 3] : 0.0;
-                        const double Sout = k + 1 < L ? mp[13] * D : 0.0;
-                        const double hk = E.h[s0 + k];
-                        emit(k, l0, 0, -U + rO);
-                        emit(k, l0, 1, U - G - mP);
-                        emit(k, l0, 2, mp[7] * G - mZ - eZ);
-                        emit(k, l0, 3, mP + mZ - rD + (Sin - Sout) / hk);
-                        emit(k, l0, 4, mp[14] * G + eZ + rD - rO);
-                    }
-                    continue;
-                }
-                // Martin models (N, NDOP, PHY): euphotic pairs, export E reduced over the member's
-                // euphotic layers (adjacent lanes), then the aphotic pairs
-                for (int base = 0; base < nm * neu; base += kLanes) {
-                    const int p = base + lane;
-                    const bool act = p < nm * neu;
-                    const int ml = act ? p / neu : 0, k = act ? p - ml * neu : 0, mi = S.y + ml;
-                    double e = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0;
-                    int l0 = 0, pid = 0;
-                    if (act) {
-                        l0 = E.mem_lane0[mi];
-                        pid = E.mem_pidx[mi];
-                        const double *mp = E.mpar + (size_t)pid * kParSlots;
-                        const double I = I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k];
-                        const double hk = E.h[s0 + k];
-                        const double N = st[k * kLanes + l0];
-                        // both half-saturation factors with one division
-                        const double lim = (N * I) / ((N + mp[3]) * (I + mp[4]));
-                        if (model == M3D_MODEL_N) {
-                            const double f = mp[2] * lim;
-                            q0 = -f;
-                            e = f * hk;
-                        } else if (model == M3D_MODEL_NDOP) {
-                            const double DOP = st[k * kLanes + l0 + 1];
-                            const double f = mp[2] * lim;
-                            q0 = -f + mp[6] * DOP;
-                            q1 = mp[5] * f - mp[6] * DOP;
-                            e = mp[7] * f * hk;
-                        } else {                                   // PHY
-                            const double DOP = st[k * kLanes + l0 + 1], PHY = st[k * kLanes + l0 + 2];
-                            const double f1 = mp[2] * PHY * lim;
-                            const double f3 = mp[10] * f1;
-                            const double loss = mp[7] * PHY + mp[8] * PHY * PHY;
-                            q0 = -f1 + mp[5] * DOP;
-                            q1 = mp[6] * f3 + loss - mp[5] * DOP + mp[9] * PHY;
-                            q2 = mp[11] * f1 - loss - mp[9] * PHY;
-                            e = mp[12] * f3 * hk;
-                        }
-                    }
-                    double Eg = e;
-                    if (neu == 2) Eg += __shfl_xor_sync(kFull, e, 1);
-                    if (act) {
-                        if (L <= 2 && k == L - 1) q0 = fma(Eg, E.mfrac[(size_t)pid * E.n + s0 + k], q0);
-                        if (k == 0) Es[ml] = Eg;
-                        emit(k, l0, 0, q0);
-                        if (model != M3D_MODEL_N) emit(k, l0, 1, q1);
-                        if (model == M3D_MODEL_PHY) emit(k, l0, 2, q2);
-                    }
-                }
-                __syncwarp();
-                for (int base = 0; base < nm * na; base += kLanes) {
-                    const int p = base + lane;
-                    if (p >= nm * na) continue;
-                    const int ml = p / na, k = neu + (p - ml * na), mi = S.y + ml;
-                    const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
-                    const double *mp = E.mpar + (size_t)pid * kParSlots;
-                    const double dep = Es[ml] * E.mfrac[(size_t)pid * E.n + s0 + k];
-                    if (model == M3D_MODEL_N) {
-                        emit(k, l0, 0, dep);
-                    } else if (model == M3D_MODEL_NDOP) {
-                        const double DOP = st[k * kLanes + l0 + 1];
-                        emit(k, l0, 0, dep + mp[6] * DOP);
-                        emit(k, l0, 1, -mp[6] * DOP);
-                    } else {
-                        const double DOP = st[k * kLanes + l0 + 1], PHY = st[k * kLanes + l0 + 2];
-                        emit(k, l0, 0, dep + mp[5] * DOP);
-                        emit(k, l0, 1, -mp[5] * DOP + mp[9] * PHY);
-                        emit(k, l0, 2, -mp[9] * PHY);
-                    }
-                }
-                __syncwarp();
+                if (S.w) ens_segment_q<m3d::Dual, SUB1>(E, S, c, s0, L, I0, lane, st, zs, qs, Es);
+                else ens_segment_q<double, SUB1>(E, S, c, s0, L, I0, lane, st, zs, qs, Es);
             }
             if (!SUB1) {
                 __syncwarp();
@@ -421,6 +480,7 @@ struct m3d_ensemble {
     cudaStream_t stream = nullptr;
     int n = 0, ncol = 0, nstep = 0, nmonth = 0, nsub = 1, nmember = 0, width = 0, ngroup = 0, wp = 0, zmax = 0;
     int cpb = 0, nwarps = 0, nblocks = 0;
+    int tangent = 0;                           // members carry a perturbation (tangent ensembles)
     size_t smem = 0, smem_optin = 0;
     std::vector<int> col_start;
     std::vector<int> rowptr;
@@ -600,10 +660,27 @@ m3d_status upload_params(m3d_ensemble *e)
 
 }  // namespace
 
+m3d_status ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3d_matrices *mt, int nmember,
+                         const m3d_member *members, int nsub, int nstep, void *stream, bool tangent);
+
 extern "C" {
 
 m3d_status metos3d_ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3d_matrices *mt, int nmember,
                                  const m3d_member *members, int nsub, int nstep, void *stream)
+{
+    return ensemble_init(out, g, mt, nmember, members, nsub, nstep, stream, false);
+}
+
+m3d_status metos3d_ensemble_init_tangent(m3d_ensemble **out, const m3d_grid *g, const m3d_matrices *mt, int nmember,
+                                         const m3d_member *members, int nsub, int nstep, void *stream)
+{
+    return ensemble_init(out, g, mt, nmember, members, nsub, nstep, stream, true);
+}
+
+}  // extern "C"
+
+m3d_status ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3d_matrices *mt, int nmember,
+                         const m3d_member *members, int nsub, int nstep, void *stream, bool tangent)
 {
     if (!out) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_init: out is null");
     *out = nullptr;
@@ -646,6 +723,8 @@ m3d_status metos3d_ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3
     e->nmonth = mt->nmonth;
     e->nsub = nsub;
     e->nmember = nmember;
+    e->tangent = tangent ? 1 : 0;
+    const int lanes_per_tracer = tangent ? 2 : 1;
     e->col_start.assign(g->col_start, g->col_start + g->ncol + 1);
     e->rowptr.assign(mt->exp_rowptr, mt->exp_rowptr + g->n + 1);
     for (int c = 0; c < g->ncol; c++) e->zmax = std::max(e->zmax, g->col_start[c + 1] - g->col_start[c]);
@@ -659,7 +738,8 @@ m3d_status metos3d_ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3
         e->offsets[m + 1] = e->offsets[m] + model_ntracer(members[m].model_id);
         derive_params(members[m].model_id, members[m].u, &e->mpar_host[(size_t)m * kParSlots]);
     }
-    e->width = e->offsets[nmember];
+    const int W = e->offsets[nmember];
+    e->width = lanes_per_tracer * W;
     std::vector<int> order(nmember);
     for (int m = 0; m < nmember; m++) order[m] = m;
     std::stable_sort(order.begin(), order.end(),
@@ -667,7 +747,7 @@ m3d_status metos3d_ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3
     std::vector<int> fill;                       // lanes used per group
     std::vector<int> grp(nmember), lane0(nmember);
     for (int m : order) {
-        int nt = model_ntracer(e->models[m]), gsel = -1;
+        int nt = lanes_per_tracer * model_ntracer(e->models[m]), gsel = -1;
         for (int gi = 0; gi < (int)fill.size() && gsel < 0; gi++)
             if (fill[gi] + nt <= kLanes) gsel = gi;
         if (gsel < 0) {
@@ -694,18 +774,24 @@ m3d_status metos3d_ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3
         mem_lane0[s] = lane0[m];
         mem_pidx[s] = m;
         if (s == 0 || grp[slots[s - 1]] != grp[m] || e->models[slots[s - 1]] != e->models[m])
-            segs.push_back(make_int4(e->models[m], s, s, 0));
+            segs.push_back(make_int4(e->models[m], s, s, e->tangent));
         segs.back().z = s + 1;
         seg_off[grp[m] + 1] = (int)segs.size();
     }
     for (int gi = 1; gi <= e->ngroup; gi++) seg_off[gi] = std::max(seg_off[gi], seg_off[gi - 1]);
     std::vector<int> lane_tracer(e->wp, -1), tracer_lane(e->width);
-    for (int m = 0; m < nmember; m++)
-        for (int t = 0; t < model_ntracer(e->models[m]); t++) {
+    for (int m = 0; m < nmember; m++) {
+        const int nt = model_ntracer(e->models[m]);
+        for (int t = 0; t < nt; t++) {
             int l = grp[m] * kLanes + lane0[m] + t;
             lane_tracer[l] = e->offsets[m] + t;
             tracer_lane[e->offsets[m] + t] = l;
+            if (tangent) {                    // the perturbation: nt lanes on, rows W on
+                lane_tracer[l + nt] = W + e->offsets[m] + t;
+                tracer_lane[W + e->offsets[m] + t] = l + nt;
+            }
         }
+    }
 
     // ---- Thomas factors of every monthly implicit block (required)
     std::vector<double> tri((size_t)mt->nmonth * 3 * g->n);
@@ -818,6 +904,8 @@ m3d_status metos3d_ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3
     return M3D_OK;
 #undef ENS_UP
 }
+
+extern "C" {
 
 m3d_status metos3d_ensemble_layout(const m3d_ensemble *e, int *nmember, int *width, int *n, int *ngroup, int *offsets)
 {

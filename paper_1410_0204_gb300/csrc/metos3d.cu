@@ -346,42 +346,31 @@ bool all_finite(const double *p, size_t count)
     return true;
 }
 
-// Contiguous partition of the water columns into tiles of about equal FP64 work.  With
-// max_cells > 0 no tile may hold more cells than that: when the equal-work partition breaks
-// the cap, the tiles are the greedy packing (each tile takes columns while its work stays
-// within W and its cells within max_cells) for the smallest W that needs at most ntiles tiles,
-// which is the smallest largest tile work any contiguous partition under the cap can reach.
+// Contiguous partition of the water columns into tiles whose largest step time is as small as
+// a contiguous partition allows.  The neighbour-synchronised year kernels run at the pace of
+// their slowest tile, so the partition minimises the largest tile cost (greedy packing: each
+// tile takes columns while its cost stays within W, for the smallest W that needs at most
+// ntiles tiles), with no tile above max_cells cells when max_cells > 0.  A column's cost is
+// ntr (0.165 nnz + 1.54 L + 13.4): per tracer, its explicit entries, its cells (Thomas solves
+// and source term) and a per-column share (its chains and euphotic cells), the coefficients
+// of a least-squares fit of the resident kernel's per-tile step time (nanoseconds, PO4-DOP,
+// 128 x 64 x 15, GB300) to those three counts.
 std::vector<int> partition_columns(const m3d_grid *g, const int *rowptr, int ntr, int ntiles, int max_cells = 0)
 {
     std::vector<double> work(g->ncol);
     for (int c = 0; c < g->ncol; c++) {
-        int s = g->col_start[c], e = g->col_start[c + 1], L = e - s;
-        double nnz = rowptr[e] - rowptr[s];
-        // FP64 lane-operations: interpolation plus one FMA per tracer for every matrix entry,
-        // about 32 per euphotic cell (a division is about 10) and 6 per aphotic cell
-        int neu = std::min(L, 2);
-        work[c] = (1.0 + ntr) * (nnz + (double)L * L) + 32.0 * neu + 6.0 * (L - neu);
+        const int s = g->col_start[c], e = g->col_start[c + 1], L = e - s;
+        const double nnz = rowptr[e] - rowptr[s];
+        work[c] = ntr * (0.165 * nnz + 1.54 * L + 13.4);
     }
-    double total = std::accumulate(work.begin(), work.end(), 0.0);
-    std::vector<int> bounds{0};
-    double acc = 0.0;
-    for (int c = 0; c < g->ncol; c++) {
-        acc += work[c];
-        int t = (int)bounds.size();
-        if (t < ntiles && acc >= total * t / ntiles && c + 1 < g->ncol) bounds.push_back(c + 1);
-    }
-    bounds.push_back(g->ncol);
-    int widest = 0;
-    for (size_t t = 0; t + 1 < bounds.size(); t++)
-        widest = std::max(widest, g->col_start[bounds[t + 1]] - g->col_start[bounds[t]]);
-    if (max_cells <= 0 || widest <= max_cells) return bounds;
+    const double total = std::accumulate(work.begin(), work.end(), 0.0);
     auto greedy = [&](double W, std::vector<int> *out) {
         int tiles = 0, cells = 0;
         double acc = 0.0;
         if (out) out->assign(1, 0);
         for (int c = 0; c < g->ncol; c++) {
             const int L = g->col_start[c + 1] - g->col_start[c];
-            if (c > 0 && (acc + work[c] > W || cells + L > max_cells)) {
+            if (c > 0 && (acc + work[c] > W || (max_cells > 0 && cells + L > max_cells))) {
                 tiles++;
                 if (out) out->push_back(c);
                 acc = 0.0;
@@ -394,15 +383,18 @@ std::vector<int> partition_columns(const m3d_grid *g, const int *rowptr, int ntr
         return tiles + 1;
     };
     double lo = *std::max_element(work.begin(), work.end()), hi = total;
-    if (greedy(hi, nullptr) > ntiles) return bounds;      // the cap alone needs more tiles
+    std::vector<int> bounds;
+    if (greedy(hi, nullptr) > ntiles) {      // the cell cap alone needs more tiles
+        greedy(hi, &bounds);
+        return bounds;
+    }
     for (int it = 0; it < 60 && hi - lo > 1e-9 * hi; it++) {
         const double mid = 0.5 * (lo + hi);
         if (greedy(mid, nullptr) <= ntiles) hi = mid;
         else lo = mid;
     }
-    std::vector<int> capped;
-    greedy(hi, &capped);
-    return capped;
+    greedy(hi, &bounds);
+    return bounds;
 }
 
 // Deal the slices [s0, s1) (cost = slot count) to the warps of one tile: longest first to
@@ -457,6 +449,7 @@ m3d_status init_ensemble_backed(m3d_ctx **out, const m3d_grid *g, const m3d_matr
     auto bail = [&](m3d_status s) {
         g_init_error = c->err;
         if (c->ens) metos3d_ensemble_free(c->ens);
+        if (c->ens_tan) metos3d_ensemble_free(c->ens_tan);
         release(c);
         delete c;
         cudaGetLastError();
@@ -481,9 +474,18 @@ m3d_status init_ensemble_backed(m3d_ctx **out, const m3d_grid *g, const m3d_matr
         fail(c, st, "%s", metos3d_ensemble_last_error(nullptr));
         return bail(st);
     }
+    // its tangent (exact Jacobian-vector products, Section 6): the same member with a perturbation
+    st = metos3d_ensemble_init_tangent(&c->ens_tan, g, mt, 1, &mem, md->nsub, md->nstep, stream);
+    if (st != M3D_OK) {
+        c->ens_tan = nullptr;
+        fail(c, st, "%s", metos3d_ensemble_last_error(nullptr));
+        return bail(st);
+    }
+    c->tan_ok = 1;
     cudaError_t e;
 #define UPE(...) do { e = (__VA_ARGS__); if (e != cudaSuccess) { fail(c, M3D_ERR_CUDA, "device set-up (%s): %s", #__VA_ARGS__, cudaGetErrorString(e)); return bail(M3D_ERR_CUDA); } } while (0)
     const size_t len = (size_t)c->ntr * c->n;
+    UPE(upload(c, &c->tan_buf, (const double *)nullptr, 4 * len));
     UPE(upload(c, &c->u_dev, (const double *)nullptr, (size_t)std::max(1, c->nparam)));
     UPE(upload(c, &c->vol, g->vol, (size_t)c->n));
     UPE(upload(c, &c->ybuf[0], (const double *)nullptr, 2 * len));
@@ -632,6 +634,7 @@ void metos3d_free(m3d_ctx *ctx)
     for (cudaEvent_t e : ctx->kev)
         if (e) cudaEventDestroy(e);
     if (ctx->ens) metos3d_ensemble_free(ctx->ens);
+    if (ctx->ens_tan) metos3d_ensemble_free(ctx->ens_tan);
     cudaSetDevice(prev);
     delete ctx;
 }
@@ -641,6 +644,7 @@ m3d_status metos3d_set_stream(m3d_ctx *ctx, void *stream)
     if (!ctx) return fail(nullptr, M3D_ERR_ARG, "metos3d_set_stream: null context");
     ctx->stream = (cudaStream_t)stream;
     if (ctx->ens) metos3d_ensemble_set_stream(ctx->ens, stream);
+    if (ctx->ens_tan) metos3d_ensemble_set_stream(ctx->ens_tan, stream);
     return M3D_OK;
 }
 
@@ -1234,6 +1238,38 @@ m3d_status ens_sync_params(m3d_ctx *c)
     return M3D_OK;
 }
 
+// The same for the tangent ensemble of an ensemble-backed context.
+m3d_status ens_tan_sync_params(m3d_ctx *c)
+{
+    std::vector<double> u((size_t)c->nparam);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(u.data(), c->u_dev, sizeof(double) * u.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    if (c->ens_tan_u_valid && u == c->ens_tan_u) return M3D_OK;
+    m3d_status st = metos3d_ensemble_set_params(c->ens_tan, 0, u.data());
+    if (st != M3D_OK) return fail(c, st, "%s", metos3d_ensemble_last_error(c->ens_tan));
+    c->ens_tan_u = u;
+    c->ens_tan_u_valid = 1;
+    return M3D_OK;
+}
+
+// phi(y0) and phi'(y0) v of an ensemble-backed context by its tangent ensemble.
+m3d_status ens_tangent_run(m3d_ctx *c, const double *y0, const double *v, double *phi, double *jv)
+{
+    m3d_status st = ens_tan_sync_params(c);
+    if (st != M3D_OK) return st;
+    const size_t len = (size_t)c->ntr * c->n;
+    double *in = c->tan_buf, *out = c->tan_buf + 2 * len;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(in, y0, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(in + len, v, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+    st = metos3d_ensemble_set_stream(c->ens_tan, c->stream);
+    if (st == M3D_OK) st = metos3d_ensemble_year_map(c->ens_tan, in, out);
+    if (st != M3D_OK) return fail(c, st, "%s", metos3d_ensemble_last_error(c->ens_tan));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(phi, out, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(jv, out + len, sizeof(double) * len, cudaMemcpyDeviceToDevice, c->stream));
+    c->last_launches = metos3d_ensemble_last_launch_count(c->ens_tan);
+    return M3D_OK;
+}
+
 // The year (or nsteps steps from j0) of an ensemble-backed context, device arrays.
 m3d_status ens_run(m3d_ctx *c, int j0, int nsteps, const double *y0, double *y1)
 {
@@ -1770,6 +1806,7 @@ m3d_status m3d_year_tangent_device(m3d_ctx *c, const double *y0, const double *v
         if (st != M3D_OK) return st;
         return m3d_year_linear_device(c, c->fn_buf, v, jv);
     }
+    if (c->ens_tan) return ens_tangent_run(c, y0, v, phi, jv);
     if (!c->tan_ok) return fail(c, M3D_ERR_UNSUPPORTED, "this model has no tangent year kernel");
     const size_t half = sizeof(double) * (size_t)c->ntr * c->n;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(c->ybuf[0], y0, half, cudaMemcpyDeviceToDevice, c->stream));

@@ -150,6 +150,13 @@ __device__ __forceinline__ Dual operator/(Dual a, Dual b)
     const double q = a.v / b.v;
     return {q, (a.d - q * b.d) / b.v};
 }
+__device__ __forceinline__ Dual operator/(double c, Dual b)
+{
+    const double q = c / b.v;
+    return {q, -(q * b.d) / b.v};
+}
+__device__ __forceinline__ Dual operator-(double c, Dual a) { return {c - a.v, -a.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, double c) { return {a.v - c, a.d}; }
 __device__ __forceinline__ Dual &operator+=(Dual &a, Dual b) { a = a + b; return a; }
 
 template <class T> __device__ __forceinline__ T zero_of();

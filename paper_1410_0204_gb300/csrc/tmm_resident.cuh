@@ -45,6 +45,9 @@ struct ResidentParams {
     long long sp_bstride;
 };
 
+// Thomas chains of at most this many layers run in registers (deeper ones through shared memory).
+constexpr int kChainRegs = 16;
+
 // A chain packs: tile-local first cell of the column | layers << 16 | tracer << 23 | month << 27.
 __host__ __device__ inline int pack_chain(int cb, int L, int t, int h) { return cb | (L << 16) | (t << 23) | (h << 27); }
 
@@ -304,7 +307,7 @@ __device__ __forceinline__ void implicit_dense_resident(const StepParams &P, con
 // weights (1 - w)/d_k and w/d_k of every cell; one combining pass then writes
 // (1 - w)/d0_k u0_k + w/d1_k u1_k.  Equal to (B_m0 + w (B_m1 - B_m0)) z up to rounding,
 // because the monthly blocks are the inverses B_m = M_m^{-1}.
-template <int NTR>
+template <int NTR, bool ADD_DQ>
 __device__ __forceinline__ void implicit_tri_resident(const StepParams &P, const ResidentParams &R, const Tile &T,
                                                       double w, const TileSmem &M, double *__restrict__ yn)
 {
@@ -320,11 +323,35 @@ __device__ __forceinline__ void implicit_tri_resident(const StepParams &P, const
             const double *nl = M.tl + (3 * h + 0) * zmax + cb;
             const double *ne = M.tl + (3 * h + 2) * zmax + cb;
             const double *zc = M.z + t * zmax + cb;
+            const double *dqc = M.dq + t * zmax + cb;
             double *x = M.yt + (h * NTR + t) * zmax + cb;
+            // the right-hand side A_exp y_j + dt q(y_j): the explicit part and the source term's
+            // increment, added here (off the chain's dependency) rather than in a pass of their own
+            auto rhs = [&](int k) { return ADD_DQ ? zc[k] + dqc[k] : zc[k]; };
+            if (L <= kChainRegs) {
+                // the chain in registers, unrolled: every factor and right-hand side is loaded
+                // ahead of the dependent multiply-adds, which then run back to back
+                double gk[kChainRegs];
+                double g = 0.0;
+#pragma unroll
+                for (int k = 0; k < kChainRegs; k++)
+                    if (k < L) {
+                        g = fma(nl[k], g, rhs(k));
+                        gk[k] = g;
+                    }
+                double u = 0.0;
+#pragma unroll
+                for (int k = kChainRegs - 1; k >= 0; k--)
+                    if (k < L) {
+                        u = fma(ne[k], u, gk[k]);
+                        x[k] = u;
+                    }
+                continue;
+            }
             // forward: g_k = z_k - l_k g_{k-1} (l_0 = 0)
             double g = 0.0;
             for (int k = 0; k < L; k++) {
-                g = fma(nl[k], g, zc[k]);
+                g = fma(nl[k], g, rhs(k));
                 x[k] = g;
             }
             // back: u_k = g_k - (e_k / d_{k+1}) u_{k+1} (nothing below the bottom layer)
@@ -352,12 +379,23 @@ __device__ __forceinline__ void implicit_tri_resident(const StepParams &P, const
     }
 }
 
-template <int NTR, bool TRI>
+template <int NTR, bool TRI, bool ADD_DQ = false>
 __device__ __forceinline__ void implicit_resident(const StepParams &P, const ResidentParams &R, const Tile &T,
                                                   double w, const TileSmem &M, double *__restrict__ yn)
 {
-    if (TRI) implicit_tri_resident<NTR>(P, R, T, w, M, yn);
-    else implicit_dense_resident<NTR>(P, T, w, M, yn);
+    if (TRI) {
+        implicit_tri_resident<NTR, ADD_DQ>(P, R, T, w, M, yn);
+    } else {
+        if (ADD_DQ) {           // the dense form reads z once per block entry: add the increment first
+            const int nc = T.ncell, zmax = P.zmax;
+            for (int e = threadIdx.x; e < NTR * nc; e += blockDim.x) {
+                const int t = e / nc, i = e - t * nc;
+                M.z[t * zmax + i] += M.dq[t * zmax + i];
+            }
+            __syncthreads();
+        }
+        implicit_dense_resident<NTR>(P, T, w, M, yn);
+    }
 }
 
 // The year (or nsteps steps from step j0) with the tiles' months resident in shared memory.
@@ -471,18 +509,12 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
             return;
         }
         if (stepop && threadIdx.x == copier && s + 1 < nsteps) fetch_operator(s + 1);
-        if (ModelTraits<MODEL>::has_q) {
-            const int nc = T.ncell, zmax = P.zmax;
-            for (int e = threadIdx.x; e < NTR * nc; e += blockDim.x) {
-                const int t = e / nc, i = e - t * nc;
-                M.z[t * zmax + i] += M.dq[t * zmax + i];
-            }
-            __syncthreads();
-        }
-        implicit_resident<NTR, TRI>(P, R, T, w, M, yn);
-        // the CTA barrier orders every thread's stores of y_{j+1} before thread 0's release
+        implicit_resident<NTR, TRI, ModelTraits<MODEL>::has_q>(P, R, T, w, M, yn);
+        // The CTA barrier orders every thread's stores of y_{j+1} before the release.  A thread
+        // of the source-term group releases, so that warp 0 (which polls the neighbours next)
+        // does not wait for the release's fence first.
         __syncthreads();
-        if (threadIdx.x == 0 && tile != S.withhold_tile) store_release(S.flags + tile, s + 1);
+        if (threadIdx.x == kSpThreads && tile != S.withhold_tile) store_release(S.flags + tile, s + 1);
     }
 }
 

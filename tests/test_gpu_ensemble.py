@@ -11,7 +11,7 @@ import pytest
 
 import m3d_inputs as mi
 import oracle
-from tests._util import rel_err
+from tests._util import normwise_err, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -211,4 +211,27 @@ def test_rejects_oversized_tiling(m3d):
     with pytest.raises(m3d.Metos3dError) as ei:
         ens.set_tiling(4000, 16)
     assert ei.value.status == m3d.M3D_ERR_ARG
+    ens.close()
+
+
+@pytest.mark.parametrize("grid,nsub", [("tiny_6x4x4", 1), ("tiny_6x4x4", 3), ("ndop_64x32x8", 1)])
+def test_tangent_ensemble_matches_oracle_tangent(m3d, grid, nsub):
+    """A tangent ensemble (every model, several lane groups) returns each member's phi(y) and
+    phi'(y) v, checked against the oracle's tangent year map of that member."""
+    p, P = problem(grid)
+    members = mi.make_ensemble(SMALL_MIX, seed=13)
+    ens = m3d.Ensemble.from_problem(p, members, tangent=True, nsub=nsub)
+    W = sum(m.ntracer for m in members)
+    assert ens.width == 2 * W
+    ys = initial_states(p, members, seed=40)
+    r = np.random.default_rng(5)
+    vs = [r.standard_normal(y.shape) for y in ys]
+    Y = stack(ys + vs)
+    Y1 = ens.year_map(Y, torch.empty_like(Y)).cpu().numpy()
+    for m, (y, v, mem) in enumerate(zip(ys, vs, members)):
+        a, b = ens.offsets[m], ens.offsets[m + 1]
+        want_phi, want_jv = oracle.year_tangent(P, y, v, mem.u, model=mem.model, nsub=nsub)
+        assert rel_err(Y1[a:b], want_phi) < YEAR_TOL, m
+        # a signed perturbation field: normwise
+        assert normwise_err(Y1[W + a:W + b], want_jv) < YEAR_TOL, m
     ens.close()

@@ -8,7 +8,7 @@ import pytest
 
 import m3d_inputs as mi
 import oracle
-from tests._util import rel_err
+from tests._util import normwise_err, rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -23,6 +23,10 @@ def m3d():
     import paper_1410_0204_gb300 as m
     m.load()
     return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
 def context(m3d, p, model):
@@ -51,10 +55,7 @@ def test_year_map_and_step_match_oracle(m3d, model):
     Y = torch.from_numpy(y0).cuda()
     assert np.array_equal(ens.year_map(Y, torch.empty_like(Y)).cpu().numpy(), y1)
     ens.close()
-    # the derivatives are PO4-DOP only; the plan options belong to the tiled kernels
-    with pytest.raises(m3d.Metos3dError) as ei:
-        ctx.year_tangent(Y, Y, torch.from_numpy(u).cuda(), torch.empty_like(Y), torch.empty_like(Y))
-    assert ei.value.status == m3d.M3D_ERR_UNSUPPORTED
+    # the plan options belong to the tiled kernels
     with pytest.raises(m3d.Metos3dError) as ei:
         ctx.set_option(m3d.OPT_YEAR_PLAN, m3d.PLAN_RESIDENT)
     assert ei.value.status == m3d.M3D_ERR_UNSUPPORTED
@@ -81,4 +82,31 @@ def test_phy_periodic_solution_newton_against_spinup(m3d):
     ysp = torch.from_numpy(y0).cuda()
     res = ctx.spinup(ysp, torch.from_numpy(u).cuda(), 50)
     assert res.size == 50 and res[-1] < res[0] and res[-1] > 1e-8
+    ctx.close()
+
+
+@pytest.mark.parametrize("model", [mi.MODEL_N, mi.MODEL_PHY, mi.MODEL_NPZD])
+def test_single_context_tangent_of_every_model(m3d, model):
+    """metos3d_year_tangent of an N, PO4-DOP-PHY or NPZD-DOP context (a one-member tangent
+    ensemble) against the oracle's tangent year map; Newton-Krylov with those products."""
+    p = mi.make_problem("tiny_6x4x4")
+    P = oracle.Problem(p)
+    ntr = len(mi.MODELS[model].tracers)
+    u = np.asarray(mi.default_params(model), dtype=np.float64)
+    ctx = context(m3d, p, model)
+    y = mi.initial_state(p, ntr, mi.model_initial_values(model)) * (0.5 + np.random.default_rng(1).random((ntr, p.n)))
+    v = np.random.default_rng(2).standard_normal((ntr, p.n))
+    phi = torch.empty((ntr, p.n), dtype=torch.float64, device="cuda")
+    jv = torch.empty_like(phi)
+    ctx.year_tangent(cuda(y), cuda(v), cuda(u), phi, jv)
+    ctx.sync()
+    want_phi, want_jv = oracle.year_tangent(P, y, v, u, model=model)
+    assert rel_err(phi.cpu().numpy(), want_phi) < 1e-10
+    assert normwise_err(jv.cpu().numpy(), want_jv) < 1e-10
+    y0 = mi.initial_state(p, ntr, mi.model_initial_values(model))
+    yN = cuda(y0)
+    st, rep = ctx.newton_solve(yN, cuda(u), tol=1e-8, jv=m3d.JV_TANGENT)
+    assert st == m3d.M3D_OK and rep["tangent_maps"] > 0, rep
+    got = yN.cpu().numpy()
+    assert np.linalg.norm((oracle.year_map(P, got, u, model=model) - got).ravel()) < 2e-8
     ctx.close()

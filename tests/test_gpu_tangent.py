@@ -5,7 +5,7 @@ import pytest
 import m3d_inputs as mi
 import oracle
 from oracle import newton as on
-from tests._util import rel_err
+from tests._util import normwise_err, rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -78,7 +78,9 @@ def test_year_tangent_matches_oracle_benchmark_grid(m3d):
     finally:
         oracle.set_threads(1)
     assert rel_err(phi.cpu().numpy(), want_phi) < 1e-10
-    assert rel_err(jv.cpu().numpy(), want_jv) < 1e-10
+    # phi'(y) v of a signed v changes sign across the grid: measured normwise (an element near
+    # a sign change shows rounding of 1e-15 max|o| as a relative error of 1e-9)
+    assert normwise_err(jv.cpu().numpy(), want_jv) < 1e-10
     ctx.close()
 
 
@@ -109,8 +111,8 @@ def test_linearised_tangent_matches_oracle(m3d, name):
     finally:
         oracle.set_threads(1)
     assert rel_err(phi.cpu().numpy(), want_phi) < 1e-10
-    assert rel_err(jv.cpu().numpy(), want_jv) < 1e-10
-    assert rel_err(jv.cpu().numpy(), jv_dual) < 1e-10
+    assert normwise_err(jv.cpu().numpy(), want_jv) < 1e-10
+    assert normwise_err(jv.cpu().numpy(), jv_dual) < 1e-10
     ctx.close()
 
 
