@@ -667,6 +667,44 @@ def run_scale_1deg(args):
     Y1 = torch.empty_like(Y0)
     cpb, nw, ms = ens.autotune(Y0, nsteps=5)
     t_ens = timed(lambda: ens.year_map(Y0, Y1), reps)
+    # the ensemble's derivatives: one tangent-ensemble year map (phi and phi' v of all 16 members:
+    # one Krylov iteration of all members' Newton-Krylov solves), the reverse sweep (checkpoint
+    # every 480 steps), and a bounded batched Newton-Krylov run (tangent products) from a state
+    # spun up for a few years
+    deriv = {}
+    if not args.no_adjoint:
+        tan = m3d.Ensemble.from_problem(prob, members, tangent=True)
+        tan.set_tiling(*ens.get_tiling())
+        V = torch.from_numpy(np.random.default_rng(5).standard_normal(tuple(Y0.shape))).cuda()
+        YV = torch.cat([Y0, V])
+        t_tan = timed(lambda: tan.year_map(YV, torch.empty_like(YV)), 1)
+        Wb = torch.ones_like(Y0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ens.year_adjoint(Y0, Wb, torch.empty_like(Y0), ckpt_every=480)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        Ys = Y0.clone()
+        for _ in range(args.scale_spinup_years):
+            ens.year_map(Ys, Ys)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, reps_n = ens.newton_solve(Ys, prob.vol, tangent_ensemble=tan, tol=1e-8, jv=m3d.JV_TANGENT,
+                                      max_newton=args.scale_newton_steps, max_krylov=args.scale_krylov,
+                                      restart=args.scale_krylov)
+        torch.cuda.synchronize()
+        t_newton = time.perf_counter() - t0
+        tan.close()
+        deriv = {"tangent_year_map_s": t_tan, "tangent_over_forward": t_tan / t_ens,
+                 "adjoint_s": t_adj, "adjoint_over_forward": t_adj / t_ens, "ckpt_every": 480,
+                 "newton": {"seconds": t_newton, "spinup_years_before": args.scale_spinup_years,
+                            "max_newton": args.scale_newton_steps, "max_krylov": args.scale_krylov,
+                            "krylov_iterations_all_members": max(r["krylov_total"] for r in reps_n),
+                            "tangent_year_maps": reps_n[0]["tangent_maps"], "year_maps": reps_n[0]["year_maps"],
+                            "residual0": [r["residual0"] for r in reps_n], "residual": [r["residual"] for r in reps_n],
+                            "seconds_per_krylov_iteration": t_newton / max(1, max(r["krylov_total"] for r in reps_n)),
+                            "how": "every member's Newton-Krylov in lockstep, one tangent-ensemble year map per Krylov "
+                                   "iteration of all 16 members, bounded (max_newton, max_krylov)"}}
     ens.close()
     f_ens = ensemble_flops_per_step(prob, members) * prob.nstep
     line = {"metric": METRIC, "value": 1.0 / t_single, "unit": UNIT, "n_gpus": 1, "steps": reps,
@@ -684,6 +722,7 @@ def run_scale_1deg(args):
             "tangent": {"seconds": t_tan, "tangent_over_forward": t_tan / t_single},
             "ensemble": {"workload": "16 NPZD-DOP members (5 tracers), parameters within +-50% of the defaults",
                          "member_years_per_s": len(members) / t_ens, "seconds_per_ensemble_year": t_ens,
+                         "derivatives": deriv,
                          "tiling": {"cols_per_block": cpb, "warps_per_block": nw, "autotune_ms_per_step": ms},
                          "roofline": {"bound": "alu", "achieved": f_ens / t_ens / 1e12, "peak": FP64_PEAK_TFLOPS,
                                       "unit": "TFLOP/s", "frac": f_ens / t_ens / 1e12 / FP64_PEAK_TFLOPS}}}
@@ -731,6 +770,12 @@ def main():
     ap.add_argument("--profile-grid", default=WORKLOAD, help="grid of --profile-years")
     ap.add_argument("--scale-1deg", action="store_true",
                     help="time the 1-degree grid (single context and 16-member ensemble) instead")
+    ap.add_argument("--scale-spinup-years", type=int, default=2,
+                    help="--scale-1deg: years of spin-up before the bounded ensemble Newton-Krylov run")
+    ap.add_argument("--scale-newton-steps", type=int, default=1,
+                    help="--scale-1deg: Newton steps of the bounded ensemble Newton-Krylov run")
+    ap.add_argument("--scale-krylov", type=int, default=4,
+                    help="--scale-1deg: Krylov iterations per Newton step of that run")
     args = ap.parse_args()
     if args.scale_1deg:
         return run_scale_1deg(args)

@@ -169,8 +169,10 @@ m3d_status metos3d_year_tangent(m3d_ctx *ctx, const double *y0, const double *v,
  * reverse sweep: about four year maps of work and ckpt_every + 1 states of memory,
  * allocated for the call.  ckpt_every >= nstep keeps the whole trajectory (nstep + 1
  * states; 2.4 GB for 52,749 cells and two tracers) and recomputes nothing, about three year
- * maps of work.  PO4-DOP with one internal step and a structurally symmetric explicit pattern
- * only (M3D_ERR_UNSUPPORTED otherwise); see M3D_OPT_ADJOINT_PLAN.  Synchronous.
+ * maps of work.  PO4-DOP by the tiled reverse kernels (see M3D_OPT_ADJOINT_PLAN); N,
+ * PO4-DOP-PHY and NPZD-DOP by the context's one-member ensemble (metos3d_ensemble_year_adjoint,
+ * whose checkpoint rule applies).  One internal step and a structurally symmetric explicit
+ * pattern only (M3D_ERR_UNSUPPORTED otherwise).  Synchronous.
  */
 m3d_status metos3d_year_adjoint(m3d_ctx *ctx, const double *y0, const double *u, const double *ybar1,
                                 double *ybar0, double *ubar_host, int ckpt_every);
@@ -522,7 +524,44 @@ m3d_status metos3d_ensemble_get_tiling(const m3d_ensemble *ens, int *cols_per_bl
 m3d_status metos3d_ensemble_autotune(m3d_ensemble *ens, const double *Y, int nsteps,
                                      int *cols_per_block, int *warps_per_block, double *ms_per_step);
 
-/* Kernel launches of the last steps or year-map call. */
+/*
+ * The adjoint of every member's year map (the gradients of the parameter optimisation of
+ * Sections 1 and 9, by hand-written reverse models, Section 6): for Y1 = phi(Y0) and the
+ * cotangents Ybar1, Ybar0 = phi_y^T Ybar1 per member (device [W][n]; may alias Ybar1) and
+ * ubar_host = phi_u^T Ybar1 (host, the members' parameters in member order, each in its
+ * model's parameter order, sum of the nparam; may be NULL).  The forward sweep keeps a
+ * checkpoint every ckpt_every steps (<= 0: 240); each segment is recomputed before its
+ * reverse steps, keeping every state of the segment when that fits in half of the free
+ * device memory and otherwise a second level of checkpoints inside it.  Two launches per
+ * reverse step (the transposed implicit part; the transposed explicit part with the reverse
+ * source terms).  Plain ensembles (not tangent) with one internal model step and a
+ * structurally symmetric explicit pattern (M3D_ERR_UNSUPPORTED otherwise).  Allocates its
+ * checkpoints for the call.  Synchronous.
+ */
+m3d_status metos3d_ensemble_year_adjoint(m3d_ensemble *ens, const double *Y0, const double *Ybar1,
+                                         double *Ybar0, double *ubar_host, int ckpt_every);
+
+/*
+ * The periodic solve of every member of an ensemble (Sections 4, 6, 7): for each member m,
+ * Newton-Krylov on F_m(y_m) = y_m - phi_m(y_m) exactly as metos3d_newton_solve states it (its
+ * own GMRES(MGS) cycle to its Eisenstat-Walker tolerance, zero-mass projection of its step,
+ * its own backtracking line search), all members advancing in lockstep.  One Krylov
+ * iteration of all members takes one year map of ens_tan (a tangent ensemble of the same
+ * members: metos3d_ensemble_init_tangent) for opts->jv = M3D_JV_TANGENT, or one year map of
+ * ens at y + h v for M3D_JV_FD; a line-search trial of all members is one year map of ens.
+ * A member that has converged stops iterating while the others go on.  The restart length
+ * is min(restart, max_krylov), one cycle per Newton step.  Y: device [W][n] (ens's layout),
+ * the initial states on entry and the solutions on exit; vol_host: host [n] cell volumes (for
+ * the zero-mass projection); reports: host [nmember] (may be NULL), each with the member's
+ * counts (year_maps and tangent_maps count the ensemble year maps, shared by all members).
+ * Allocates (restart + 10) ensemble states for the call.  Synchronous; returns
+ * M3D_NOT_CONVERGED unless every member reached the tolerance.
+ */
+m3d_status metos3d_ensemble_newton_solve(m3d_ensemble *ens, m3d_ensemble *ens_tan, double *Y,
+                                         const double *vol_host, const m3d_newton_opts *opts,
+                                         m3d_newton_report *reports);
+
+/* Kernel launches of the last steps, year-map or adjoint call. */
 long long metos3d_ensemble_last_launch_count(const m3d_ensemble *ens);
 
 /* Message for the last failure on ens, or on metos3d_ensemble_init when ens is NULL. */

@@ -190,6 +190,9 @@ def load(build_if_missing: bool = False):
                                         C.POINTER(_Member), C.c_int, C.c_int, vp]
     L.metos3d_ensemble_init_tangent.argtypes = [C.POINTER(vp), C.POINTER(_Grid), C.POINTER(_Matrices), C.c_int,
                                                 C.POINTER(_Member), C.c_int, C.c_int, vp]
+    L.metos3d_ensemble_year_adjoint.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_double), C.c_int]
+    L.metos3d_ensemble_newton_solve.argtypes = [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(NewtonOptions),
+                                                C.POINTER(NewtonReport)]
     L.metos3d_ensemble_layout.argtypes = [vp, ip, ip, ip, ip, ip]
     L.metos3d_ensemble_set_stream.argtypes = [vp, vp]
     L.metos3d_ensemble_set_params.argtypes = [vp, C.c_int, dp]
@@ -587,6 +590,38 @@ class Ensemble:
         _echeck(self._L.metos3d_ensemble_year_map(self._e, _dev_ptr(Y0, self.numel, "Y0"),
                                                   _dev_ptr(Y1, self.numel, "Y1", True)), self._e)
         return Y1
+
+    def year_adjoint(self, Y0, Ybar1, Ybar0, ckpt_every=240):
+        """Reverse sweep of every member's year map (metos3d_ensemble_year_adjoint): Ybar0 receives
+        phi_y^T Ybar1; returns the list of the members' parameter gradients phi_u^T Ybar1."""
+        self._sync_stream()
+        ub = np.zeros(sum(self.nparams))
+        _echeck(self._L.metos3d_ensemble_year_adjoint(self._e, _dev_ptr(Y0, self.numel, "Y0"),
+                                                      _dev_ptr(Ybar1, self.numel, "Ybar1"),
+                                                      _dev_ptr(Ybar0, self.numel, "Ybar0", True), _dp(ub),
+                                                      int(ckpt_every)), self._e)
+        out, at = [], 0
+        for k in self.nparams:
+            out.append(ub[at:at + k].copy())
+            at += k
+        return out
+
+    def newton_solve(self, Y, vol, tangent_ensemble=None, **opts):
+        """Periodic solve of every member in place on Y (metos3d_ensemble_newton_solve), with
+        tangent products from ``tangent_ensemble`` (jv=JV_TANGENT) or finite differences;
+        returns (status, list of the members' report dicts)."""
+        self._sync_stream()
+        o = NewtonOptions()
+        self._L.metos3d_newton_default_options(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        reps = (NewtonReport * self.nmember)()
+        vol = np.ascontiguousarray(vol, dtype=np.float64)
+        st = self._L.metos3d_ensemble_newton_solve(self._e, tangent_ensemble._e if tangent_ensemble else None,
+                                                   _dev_ptr(Y, self.numel, "Y", True), _dp(vol), C.byref(o), reps)
+        if st not in (M3D_OK, M3D_NOT_CONVERGED):
+            raise Metos3dError(st, "metos3d_ensemble_newton_solve failed")
+        return st, [r.to_dict() for r in reps]
 
     def set_params(self, m, u):
         u = np.ascontiguousarray(u, dtype=np.float64)

@@ -10,7 +10,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libmetos3d.so")
 SOURCES = [os.path.join(CSRC, "metos3d.cu"), os.path.join(CSRC, "residual_static.cu"),
            os.path.join(CSRC, "newton.cu"), os.path.join(CSRC, "adjoint.cu"),
-           os.path.join(CSRC, "ensemble.cu")]
+           os.path.join(CSRC, "ensemble.cu"), os.path.join(CSRC, "ensemble_newton.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + \
     [os.path.join(ROOT, "include", "metos3d.h")]
 

@@ -427,6 +427,16 @@ extern "C" m3d_status metos3d_year_adjoint(m3d_ctx *c, const double *y0, const d
 {
     if (!c) return fail(nullptr, M3D_ERR_ARG, "metos3d_year_adjoint: null context");
     if (!y0 || !u || !ybar1 || !ybar0) return fail(c, M3D_ERR_ARG, "metos3d_year_adjoint: null pointer");
+    if (c->ens) {
+        // N, PO4-DOP-PHY and NPZD-DOP: the reverse sweep of the context's one-member ensemble
+        m3d_status st = m3d_set_params(c, u, cudaMemcpyDeviceToDevice);
+        if (st == M3D_OK) st = m3d_ens_sync_params(c);
+        if (st != M3D_OK) return st;
+        st = metos3d_ensemble_year_adjoint(c->ens, y0, ybar1, ybar0, ubar_host, ckpt_every);
+        if (st != M3D_OK) return fail(c, st, "%s", metos3d_ensemble_last_error(c->ens));
+        c->last_launches = metos3d_ensemble_last_launch_count(c->ens);
+        return M3D_OK;
+    }
     AdjointSweep A;
     m3d_status st = A.begin(c, ckpt_every);
     if (st == M3D_OK) st = A.forward(y0, u);

@@ -130,6 +130,9 @@ m3d_status m3d_year_linear_device(m3d_ctx *c, const double *fn, const double *v,
 // One TMM step j in the caller's layout (the step kernel; parameters already in c->u_dev and
 // the per-call tables made).
 m3d_status m3d_step_device(m3d_ctx *c, int j, const double *y, double *yn);
+// An ensemble-backed context (N, PO4-DOP-PHY, NPZD-DOP): hand the parameters in c->u_dev to its
+// one-member ensemble (synchronous; nothing to do when they did not change).
+m3d_status m3d_ens_sync_params(m3d_ctx *c);
 // The per-call model tables (attenuation, Martin profile, model scalars) from c->u_dev.
 m3d_status m3d_prologue(m3d_ctx *c);
 // Device allocation owned by the context (freed by metos3d_free).

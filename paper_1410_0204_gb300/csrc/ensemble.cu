@@ -370,13 +370,407 @@ __global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_step(EnsParams E, in
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Reverse (adjoint) ensemble step, one internal model step (Section 6's exact derivatives, by
+// hand).  For y_{j+1} = B_j (A_j y_j + ds q(y_j)) and the cotangent ybar_{j+1}:
+//   zbar_j = B_j^T ybar_{j+1}                                   (k_ens_adj_implicit)
+//   ybar_j = A_j^T zbar_j + ds (dq/dy)^T zbar_j,  ubar += ds (dq/du)^T zbar_j   (k_ens_adj_explicit)
+// A_j^T has the explicit pattern's transpose, which the structurally symmetric pattern shares:
+// its values sit in the same CSR slots.  B_j^T = (1 - w) T0^-T + w T1^-T with T_h^T tridiagonal.
+struct EnsAdjParams {
+    const double *eat, *edt;              // [nmonth][nnz] A_m^T and A_{m+1}^T - A_m^T in the CSR slots
+    const double *trit;                   // [nmonth][3][n] Thomas factors of T_m^T (back-substitution form)
+    const double *mfrac_b;                // [nmember][n] d mfrac / d b (Martin models)
+    double *ub_part;                      // [nblocks][nmember][kParSlots] gradient in the derived slots
+    int nmember;
+};
+
+// zbar_j = B_j^T ybar on every (column, group) item; ybar, zbar packed [n][wp].
+__global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_adj_implicit(EnsParams E, EnsAdjParams A, int j,
+                                                                         const double *__restrict__ Yb,
+                                                                         double *__restrict__ Zb)
+{
+    extern __shared__ double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * E.cpb, c1 = min(c0 + E.cpb, E.ncol);
+    const int cell0 = E.col_start[c0], cell1 = E.col_start[c1];
+    const int cbm = E.cells_blk_max, zm = E.zmax;
+    double *stri = smem;
+    double *wb = stri + 6 * cbm + (size_t)warp * 2 * zm * kLanes;
+    double *ys = wb, *zs = ys + zm * kLanes;
+    int *counter = (int *)(stri + 6 * cbm + (size_t)(blockDim.x >> 5) * 2 * zm * kLanes);
+    const int m0 = E.m0tab[j], m1 = (m0 + 1) % E.nmonth;
+    const double w = E.wtab[j];
+    {
+        const double *t0 = A.trit + (size_t)m0 * E.tri_mstride, *t1 = A.trit + (size_t)m1 * E.tri_mstride;
+        for (int i = threadIdx.x; i < cell1 - cell0; i += blockDim.x)
+            for (int f = 0; f < 3; f++) {
+                const double a = t0[(size_t)f * E.n + cell0 + i], b = t1[(size_t)f * E.n + cell0 + i];
+                stri[f * cbm + i] = f == 1 ? (1.0 - w) * a : a;
+                stri[(3 + f) * cbm + i] = f == 1 ? w * b : b;
+            }
+        if (threadIdx.x == 0) *counter = 0;
+    }
+    __syncthreads();
+    const int nitems = (c1 - c0) * E.ngroup;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= nitems) break;
+        const int c = c0 + item / E.ngroup, g = item - (item / E.ngroup) * E.ngroup;
+        const int s0 = E.col_start[c], L = E.col_start[c + 1] - s0, sl = s0 - cell0;
+        const size_t gl = (size_t)g * kLanes + lane;
+        const double *nl0 = stri + sl, *rd0 = stri + cbm + sl, *ne0 = stri + 2 * cbm + sl;
+        const double *nl1 = stri + 3 * cbm + sl, *rd1 = stri + 4 * cbm + sl, *ne1 = stri + 5 * cbm + sl;
+        double g0 = 0.0, g1 = 0.0;
+        for (int k = 0; k < L; k++) {
+            const double yb = Yb[(size_t)(s0 + k) * E.wp + gl];
+            g0 = fma(nl0[k], g0, yb);
+            g1 = fma(nl1[k], g1, yb);
+            ys[k * kLanes + lane] = g0;
+            zs[k * kLanes + lane] = g1;
+        }
+        double u0 = 0.0, u1 = 0.0;
+        for (int k = L - 1; k >= 0; k--) {
+            u0 = fma(ne0[k], u0, ys[k * kLanes + lane]);
+            u1 = fma(ne1[k], u1, zs[k * kLanes + lane]);
+            Zb[(size_t)(s0 + k) * E.wp + gl] = fma(rd0[k], u0, rd1[k] * u1);
+        }
+        __syncwarp();
+    }
+}
+
+// The sums over the lanes of each member of a pass: lanes p = base + lane belong to member
+// (p / per) of the pass, contiguous; after the segmented suffix sums the first lane of each
+// member's run in this warp holds the run's total.
+__device__ __forceinline__ double member_run_sum(double v, int key, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double other = __shfl_down_sync(kFull, v, o);
+        const int okey = __shfl_down_sync(kFull, key, o);
+        if (lane + o < 32 && okey == key) v += other;
+    }
+    return v;
+}
+
+// Add a pass's per-lane parameter gradients g[0..np) of member slot mi (key = member within the
+// pass, -1 for idle lanes) into the block's accumulators ub[mi][slot].
+__device__ __forceinline__ void add_member_gradients(double *ub, const double *gv, int np, int key, int mi, int lane)
+{
+    const int prev = __shfl_up_sync(kFull, key, 1);
+    const bool head = key >= 0 && (lane == 0 || prev != key);
+    for (int q = 0; q < np; q++) {
+        const double v = member_run_sum(key >= 0 ? gv[q] : 0.0, key, lane);
+        if (head && v != 0.0) atomicAdd(ub + (size_t)mi * kParSlots + q, v);
+    }
+}
+
+// Reverse of one segment's source terms on one column: qb = ds zbar (own column, zbs), the
+// state y_j (ys); adds (dq/dy)^T qb into ybs and (dq/du)^T qb into ub[member slot][derived slot],
+// slot 0 holding d/dk_w (through the light attenuation) and slot 1 d/db (through the Martin
+// profile).
+__device__ __forceinline__ void ens_segment_qadj(const EnsParams &E, const EnsAdjParams &A, const int4 &S, int c,
+                                                 int s0, int L, double I0, int lane, const double *ys,
+                                                 const double *zbs, double *ybs, double *Es, double *Ebs, double *ub)
+{
+    const int model = S.x, nm = S.z - S.y;
+    const int neu = L < 2 ? L : 2, na = L - neu;
+    const double ds = E.ds;
+    const double *zc = E.h + E.n;
+    auto st = [&](int k, int l0, int t) { return ys[k * kLanes + l0 + t]; };
+    auto qb = [&](int k, int l0, int t) { return ds * zbs[k * kLanes + l0 + t]; };
+    auto addy = [&](int k, int l0, int t, double v) { ybs[k * kLanes + l0 + t] += v; };
+    if (model == M3D_MODEL_NPZD) {
+        for (int base = 0; base < nm * L; base += kLanes) {
+            const int p = base + lane;
+            const bool act = p < nm * L;
+            const int ml = act ? p / L : -1, k = act ? p - ml * L : 0, mi = S.y + (act ? ml : 0);
+            double gv[15];
+#pragma unroll
+            for (int q = 0; q < 15; q++) gv[q] = 0.0;
+            if (act) {
+                const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
+                const double *mp = E.mpar + (size_t)pid * kParSlots;
+                const double N = st(k, l0, 0), P = st(k, l0, 1), Z = st(k, l0, 2), D = st(k, l0, 3);
+                const double DOP = st(k, l0, 4);
+                const double bN = qb(k, l0, 0), bP = qb(k, l0, 1), bZ = qb(k, l0, 2), bD = qb(k, l0, 3);
+                const double bO = qb(k, l0, 4);
+                const double at = k < neu ? E.atten[((size_t)pid * E.ncol + c) * 2 + k] : 0.0;
+                const double I = I0 * at;
+                const double dN = N + mp[3], dI = I + mp[4], dP = mp[6] + P;
+                // U = mu_P P N I / (dN dI), G = mu_Z Z P / dP
+                const double PNI = P * N * I / (dN * dI);
+                const double U = mp[2] * PNI;
+                const double R = P / dP;
+                const double G = mp[5] * Z * R;
+                const double Ub = -bN + bP;
+                const double Gb = -bP + mp[7] * bZ + mp[14] * bO;
+                const double mPb = -bP + bD, mZb = -bZ + bD, eZb = -bZ + bO, rDb = -bD + bO, rOb = bN - bO;
+                double yN = 0.0, yP = 0.0, yZ = 0.0, yD = 0.0, yO = 0.0;
+                if (k < neu) {
+                    yN += Ub * mp[2] * P * I * mp[3] / (dN * dN * dI);
+                    yP += Ub * mp[2] * N * I / (dN * dI);
+                    gv[2] += Ub * PNI;
+                    gv[3] += -Ub * U / dN;
+                    gv[4] += -Ub * U / dI;
+                    // dU/dI = mu_P P N K_I / (dN dI^2), dI/dk_w = -zc I
+                    gv[0] += Ub * (mp[2] * P * N * mp[4] / (dN * dI * dI)) * (-zc[s0 + k] * I);
+                }
+                yZ += Gb * mp[5] * R;
+                yP += Gb * mp[5] * Z * mp[6] / (dP * dP);
+                gv[5] += Gb * Z * R;
+                gv[6] += -Gb * G / dP;
+                gv[7] += G * bZ;
+                gv[14] += G * bO;
+                yP += mp[8] * mPb;
+                gv[8] += mPb * P;
+                yZ += 2.0 * mp[9] * Z * mZb + mp[10] * eZb;
+                gv[9] += mZb * Z * Z;
+                gv[10] += eZb * Z;
+                yD += mp[11] * rDb;
+                gv[11] += rDb * D;
+                yO += mp[12] * rOb;
+                gv[12] += rOb * DOP;
+                if (k + 1 < L) {        // S_k = w_D D_k leaves layer k into layer k + 1
+                    const double Sb = -bD / E.h[s0 + k] + qb(k + 1, l0, 3) / E.h[s0 + k + 1];
+                    yD += mp[13] * Sb;
+                    gv[13] += D * Sb;
+                }
+                addy(k, l0, 0, yN);
+                addy(k, l0, 1, yP);
+                addy(k, l0, 2, yZ);
+                addy(k, l0, 3, yD);
+                addy(k, l0, 4, yO);
+            }
+            add_member_gradients(ub, gv, 15, ml, mi, lane);
+        }
+        return;
+    }
+    // Martin models: (1) the euphotic lanes recompute the export E of each member, (2) the
+    // aphotic lanes (and a shallow column's bottom layer) reverse their terms and sum the
+    // export's cotangent Ebar per member, (3) the euphotic lanes reverse with Ebar
+    for (int base = 0; base < nm * neu; base += kLanes) {
+        const int p = base + lane;
+        const bool act = p < nm * neu;
+        const int ml = act ? p / neu : 0, k = act ? p - ml * neu : 0, mi = S.y + ml;
+        double e = 0.0;
+        if (act) {
+            const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
+            const double *mp = E.mpar + (size_t)pid * kParSlots;
+            const double I = I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k];
+            const double N = st(k, l0, 0);
+            const double lim = (N * I) / ((N + mp[3]) * (I + mp[4]));
+            const double hk = E.h[s0 + k];
+            if (model == M3D_MODEL_N) e = mp[2] * lim * hk;
+            else if (model == M3D_MODEL_NDOP) e = mp[7] * (mp[2] * lim) * hk;
+            else e = mp[12] * (mp[10] * (mp[2] * st(k, l0, 2) * lim)) * hk;
+        }
+        const double Eg = neu == 2 ? e + __shfl_xor_sync(kFull, e, 1) : e;
+        if (act && k == 0) {
+            Es[ml] = Eg;
+            Ebs[ml] = 0.0;
+        }
+    }
+    __syncwarp();
+    // aphotic layers, and the bottom layer of a shallow column (its export stays there)
+    const int nap = na > 0 ? na : 1;
+    for (int base = 0; base < nm * nap; base += kLanes) {
+        const int p = base + lane;
+        const bool act = p < nm * nap;
+        const int ml = act ? p / nap : -1, mi = S.y + (act ? ml : 0);
+        const int k = na > 0 ? neu + (p - (act ? ml : 0) * nap) : L - 1;
+        double gv[13];
+#pragma unroll
+        for (int q = 0; q < 13; q++) gv[q] = 0.0;
+        if (act) {
+            const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
+            const double *mp = E.mpar + (size_t)pid * kParSlots;
+            const double Ev = Es[ml];
+            const double mf = E.mfrac[(size_t)pid * E.n + s0 + k];
+            const double b0 = qb(k, l0, 0);
+            double Ebp = b0 * mf;
+            gv[1] += b0 * Ev * A.mfrac_b[(size_t)pid * E.n + s0 + k];
+            if (na > 0) {
+                if (model == M3D_MODEL_NDOP) {
+                    const double b1 = qb(k, l0, 1), DOP = st(k, l0, 1);
+                    addy(k, l0, 1, mp[6] * (b0 - b1));
+                    gv[6] += (b0 - b1) * DOP;
+                } else if (model == M3D_MODEL_PHY) {
+                    const double b1 = qb(k, l0, 1), b2 = qb(k, l0, 2);
+                    const double DOP = st(k, l0, 1), PHY = st(k, l0, 2);
+                    addy(k, l0, 1, mp[5] * (b0 - b1));
+                    gv[5] += (b0 - b1) * DOP;
+                    addy(k, l0, 2, mp[9] * (b1 - b2));
+                    gv[9] += (b1 - b2) * PHY;
+                }
+            }
+            atomicAdd(Ebs + ml, Ebp);
+        }
+        add_member_gradients(ub, gv, 13, ml, mi, lane);
+    }
+    __syncwarp();
+    for (int base = 0; base < nm * neu; base += kLanes) {
+        const int p = base + lane;
+        const bool act = p < nm * neu;
+        const int ml = act ? p / neu : -1, k = act ? p - ml * neu : 0, mi = S.y + (act ? ml : 0);
+        double gv[13];
+#pragma unroll
+        for (int q = 0; q < 13; q++) gv[q] = 0.0;
+        if (act) {
+            const int l0 = E.mem_lane0[mi], pid = E.mem_pidx[mi];
+            const double *mp = E.mpar + (size_t)pid * kParSlots;
+            const double Eb = Ebs[ml];
+            const double I = I0 * E.atten[((size_t)pid * E.ncol + c) * 2 + k];
+            const double hk = E.h[s0 + k];
+            const double N = st(k, l0, 0);
+            const double dN = N + mp[3], dI = I + mp[4];
+            const double lim = (N * I) / (dN * dI);
+            const double b0 = qb(k, l0, 0);
+            double limb = 0.0;
+            if (model == M3D_MODEL_N) {
+                const double fb = -b0 + Eb * hk;
+                gv[2] += fb * lim;
+                limb = fb * mp[2];
+            } else if (model == M3D_MODEL_NDOP) {
+                const double b1 = qb(k, l0, 1), DOP = st(k, l0, 1);
+                const double f = mp[2] * lim;
+                const double fb = -b0 + mp[5] * b1 + Eb * mp[7] * hk;
+                gv[5] += b1 * f;
+                gv[7] += Eb * f * hk;
+                addy(k, l0, 1, mp[6] * (b0 - b1));
+                gv[6] += (b0 - b1) * DOP;
+                gv[2] += fb * lim;
+                limb = fb * mp[2];
+            } else {
+                const double b1 = qb(k, l0, 1), b2 = qb(k, l0, 2);
+                const double DOP = st(k, l0, 1), PHY = st(k, l0, 2);
+                const double f1 = mp[2] * PHY * lim, f3 = mp[10] * f1;
+                const double f3b = mp[6] * b1 + Eb * mp[12] * hk;
+                gv[6] += b1 * f3;
+                gv[12] += Eb * f3 * hk;
+                const double f1b = -b0 + mp[11] * b2 + mp[10] * f3b;
+                gv[10] += f3b * f1;
+                gv[11] += b2 * f1;
+                const double lossb = b1 - b2;
+                addy(k, l0, 2, lossb * (mp[7] + 2.0 * mp[8] * PHY) + mp[9] * (b1 - b2) + f1b * mp[2] * lim);
+                gv[7] += lossb * PHY;
+                gv[8] += lossb * PHY * PHY;
+                gv[9] += (b1 - b2) * PHY;
+                addy(k, l0, 1, mp[5] * (b0 - b1));
+                gv[5] += (b0 - b1) * DOP;
+                gv[2] += f1b * PHY * lim;
+                limb = f1b * mp[2] * PHY;
+            }
+            // lim = N I / ((N + K) (I + K_I))
+            addy(k, l0, 0, limb * I * mp[3] / (dN * dN * dI));
+            gv[3] += -limb * lim / dN;
+            gv[4] += -limb * lim / dI;
+            gv[0] += limb * (N * mp[4] / (dN * dI * dI)) * (-zc[s0 + k] * I);
+        }
+        add_member_gradients(ub, gv, 13, ml, mi, lane);
+    }
+    __syncwarp();
+}
+
+// ybar_j = A_j^T zbar_j + ds (dq/dy)^T zbar_j on every (column, group) item, the parameter
+// gradient into the block's accumulators and, at the end, into the block's own partial sums.
+// X: the forward state y_j, packed.
+__global__ void __launch_bounds__(kMaxWarps * kLanes) k_ens_adj_explicit(EnsParams E, EnsAdjParams A, int j,
+                                                                         const double *__restrict__ X,
+                                                                         const double *__restrict__ Zb,
+                                                                         double *__restrict__ Yb)
+{
+    extern __shared__ double smem[];
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * E.cpb, c1 = min(c0 + E.cpb, E.ncol);
+    const int cell0 = E.col_start[c0], cell1 = E.col_start[c1];
+    const int p0 = E.rowptr[cell0], p1 = E.rowptr[cell1];
+    const int zm = E.zmax;
+    double *sval = smem;
+    double *ub = sval + E.nnz_blk_max;                                    // [nmember][kParSlots]
+    double *wb = ub + (size_t)A.nmember * kParSlots + (size_t)warp * (3 * zm * kLanes + 2 * kLanes);
+    double *ys = wb, *zbs = ys + zm * kLanes, *ybs = zbs + zm * kLanes;
+    double *Es = ybs + zm * kLanes, *Ebs = Es + kLanes;
+    int *scol = (int *)(ub + (size_t)A.nmember * kParSlots + (size_t)nw * (3 * zm * kLanes + 2 * kLanes));
+    int *counter = scol + E.nnz_blk_max;
+    const int m0 = E.m0tab[j];
+    const double w = E.wtab[j];
+    {
+        const double *a0 = A.eat + (size_t)m0 * E.e_mstride, *d0 = A.edt + (size_t)m0 * E.e_mstride;
+        for (int p = threadIdx.x; p < p1 - p0; p += blockDim.x) {
+            sval[p] = fma(w, d0[p0 + p], a0[p0 + p]);
+            scol[p] = E.colidx[p0 + p];
+        }
+        for (int i = threadIdx.x; i < A.nmember * kParSlots; i += blockDim.x) ub[i] = 0.0;
+        if (threadIdx.x == 0) *counter = 0;
+    }
+    __syncthreads();
+    const int nitems = (c1 - c0) * E.ngroup;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= nitems) break;
+        const int c = c0 + item / E.ngroup, g = item - (item / E.ngroup) * E.ngroup;
+        const int s0 = E.col_start[c], L = E.col_start[c + 1] - s0;
+        const size_t gl = (size_t)g * kLanes + lane;
+        for (int k = 0; k < L; k++) {
+            ys[k * kLanes + lane] = X[(size_t)(s0 + k) * E.wp + gl];
+            zbs[k * kLanes + lane] = Zb[(size_t)(s0 + k) * E.wp + gl];
+            const int pb = E.rowptr[s0 + k] - p0, pe = E.rowptr[s0 + k + 1] - p0;
+            double z = 0.0;
+            for (int p = pb; p < pe; p++) z = fma(sval[p], Zb[(size_t)scol[p] * E.wp + gl], z);
+            ybs[k * kLanes + lane] = z;
+        }
+        __syncwarp();
+        const double I0 = E.I0tab[(size_t)j * E.nulat + E.col_ulat[c]];
+        for (int sg = E.grp_seg_off[g]; sg < E.grp_seg_off[g + 1]; sg++)
+            ens_segment_qadj(E, A, E.segs[sg], c, s0, L, I0, lane, ys, zbs, ybs, Es, Ebs, ub);
+        __syncwarp();
+        for (int k = 0; k < L; k++) Yb[(size_t)(s0 + k) * E.wp + gl] = ybs[k * kLanes + lane];
+        __syncwarp();
+    }
+    __syncthreads();
+    double *part = A.ub_part + (size_t)blockIdx.x * A.nmember * kParSlots;
+    for (int i = threadIdx.x; i < A.nmember * kParSlots; i += blockDim.x) part[i] += ub[i];
+}
+
+__host__ __device__ inline size_t ens_adj_smem_bytes(int nnz_blk_max, int zmax, int nwarps, int nmember)
+{
+    return sizeof(double) * ((size_t)nnz_blk_max + (size_t)nmember * kParSlots +
+                             (size_t)nwarps * (3 * (size_t)zmax * kLanes + 2 * kLanes)) +
+           sizeof(int) * ((size_t)nnz_blk_max + 4);
+}
+
+// out[m][p] = in[m][sym[p]]: the transposed matrix's values in the pattern's own slots.
+__global__ void k_ens_transpose_values(long long nnz, int nmonth, const int *sym, const double *in, double *out)
+{
+    const long long tot = nnz * nmonth;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+        const long long m = i / nnz, p = i - m * nnz;
+        out[i] = in[m * nnz + sym[p]];
+    }
+}
+
+// ubar[m][q] = sum over blocks of part[b][m][q] (fixed order).
+__global__ void k_ens_ubar_reduce(int nblocks, int nm, const double *part, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm * kParSlots) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; b++) s += part[(size_t)b * nm * kParSlots + i];
+    out[i] = s;
+}
+
 // Per-member tables from the derived scalars: light attenuation of the euphotic cells and the
 // Martin deposition profile (F(z_top) - F(z_bot)) / (E h) of the aphotic cells, with the
 // sea-floor rule (nothing leaves the bottom interface; a column without aphotic layers keeps
 // its export in its bottom layer, 1/h there).
 __global__ void k_ens_tables(int nmember, int ncol, int n, const int *col_start, const double *h,
                              const double *zc, const int *mem_model, const double *mpar, double *atten,
-                             double *mfrac)
+                             double *mfrac, double *mfrac_b)
 {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)nmember * ncol) return;
@@ -389,13 +783,22 @@ __global__ void k_ens_tables(int nmember, int ncol, int n, const int *col_start,
     if (model == M3D_MODEL_NPZD) return;
     double zeu = 0.0;
     for (int k = 0; k < neu; k++) zeu += h[s0 + k];
-    for (int k = 0; k < neu; k++) mfrac[(size_t)m * n + s0 + k] = (L <= 2 && k == L - 1) ? 1.0 / h[s0 + k] : 0.0;
+    for (int k = 0; k < neu; k++) {
+        mfrac[(size_t)m * n + s0 + k] = (L <= 2 && k == L - 1) ? 1.0 / h[s0 + k] : 0.0;
+        if (mfrac_b) mfrac_b[(size_t)m * n + s0 + k] = 0.0;
+    }
     double ztop = zeu;
     for (int k = neu; k < L; k++) {
         const double zbot = ztop + h[s0 + k];
         const double top = pow(ztop / zeu, -b);
         const double bot = k + 1 < L ? pow(zbot / zeu, -b) : 0.0;
         mfrac[(size_t)m * n + s0 + k] = (top - bot) / h[s0 + k];
+        // d mfrac / d b, for the reverse sweep: d (z/z_eu)^-b / d b = -ln(z/z_eu) (z/z_eu)^-b
+        if (mfrac_b) {
+            const double dtop = -log(ztop / zeu) * top;
+            const double dbot = k + 1 < L ? -log(zbot / zeu) * bot : 0.0;
+            mfrac_b[(size_t)m * n + s0 + k] = (dtop - dbot) / h[s0 + k];
+        }
         ztop = zbot;
     }
 }
@@ -493,6 +896,11 @@ struct m3d_ensemble {
     double *mpar_dev = nullptr, *atten_dev = nullptr, *mfrac_dev = nullptr;
     int *lane_tracer = nullptr, *tracer_lane = nullptr;
     double *xbuf[2] = {nullptr, nullptr};
+    // the reverse sweep (non-tangent ensembles whose explicit pattern is structurally
+    // symmetric): transposed operators, d mfrac / d b, the members' parameter counts
+    int adj_ok = 0;
+    double *eat = nullptr, *edt = nullptr, *trit = nullptr, *mfrac_b_dev = nullptr;
+    std::vector<int> nparams;
     cudaGraphExec_t graph = nullptr;
     long long last_launches = 0;
     std::string err;
@@ -597,7 +1005,7 @@ m3d_status launch_tables(m3d_ensemble *e)
     long long tot = (long long)e->nmember * e->ncol;
     k_ens_tables<<<(unsigned)((tot + 255) / 256), 256, 0, e->stream>>>(
         e->nmember, e->ncol, e->n, e->P.col_start, e->P.h, e->P.h + e->n, e->mem_model_dev, e->mpar_dev, e->atten_dev,
-        e->mfrac_dev);
+        e->mfrac_dev, e->mfrac_b_dev);
     ENS_CUDA(e, cudaGetLastError());
     return M3D_OK;
 }
@@ -891,6 +1299,61 @@ m3d_status ensemble_init(m3d_ensemble **out, const m3d_grid *g, const m3d_matric
         e->xbuf[0] = xb;
         e->xbuf[1] = xb + (size_t)g->n * e->wp;
     }
+    // ---- the reverse sweep's operators: A_m^T in the pattern's slots (a structurally
+    // symmetric pattern holds the transpose's entries), Thomas factors of every T_m^T
+    e->nparams.resize(nmember);
+    for (int m = 0; m < nmember; m++) e->nparams[m] = model_nparam(e->models[m]);
+    if (!tangent) {
+        std::vector<int> sym(nnz);
+        bool symmetric = true;
+        for (int i = 0; i < g->n && symmetric; i++)
+            for (int q = mt->exp_rowptr[i]; q < mt->exp_rowptr[i + 1] && symmetric; q++) {
+                const int k = mt->exp_colidx[q];
+                const int *b = mt->exp_colidx + mt->exp_rowptr[k], *en = mt->exp_colidx + mt->exp_rowptr[k + 1];
+                const int *f = std::lower_bound(b, en, i);
+                if (f == en || *f != i) symmetric = false;
+                else sym[q] = (int)(f - mt->exp_colidx);
+            }
+        std::vector<double> trit;
+        bool tri_t = symmetric;
+        if (tri_t) {
+            trit.assign((size_t)mt->nmonth * 3 * g->n, 0.0);
+            std::vector<double> bt;
+            long long off = 0;
+            std::vector<long long> blk_off(g->ncol + 1, 0);
+            for (int c = 0; c < g->ncol; c++) {
+                long long L = g->col_start[c + 1] - g->col_start[c];
+                blk_off[c + 1] = blk_off[c] + L * L;
+            }
+            (void)off;
+            for (int m = 0; m < mt->nmonth && tri_t; m++) {
+                double *base = trit.data() + (size_t)m * 3 * g->n;
+                for (int c = 0; c < g->ncol && tri_t; c++) {
+                    const int L = g->col_start[c + 1] - g->col_start[c], s0 = g->col_start[c];
+                    const double *B = mt->imp_blk + (size_t)m * mt->s_imp + blk_off[c];
+                    bt.assign((size_t)L * L, 0.0);
+                    for (int r = 0; r < L; r++)
+                        for (int k = 0; k < L; k++) bt[(size_t)k * L + r] = B[(size_t)r * L + k];
+                    tri_t = tridiagonal_factors(bt.data(), L, base + s0, base + g->n + s0, base + 2 * (size_t)g->n + s0);
+                }
+            }
+            for (int m = 0; m < mt->nmonth && tri_t; m++)
+                thomas_backsubstitution_form(trit.data() + (size_t)m * 3 * g->n, g->n, g->col_start, g->ncol);
+        }
+        if (symmetric && tri_t) {
+            int *sym_dev;
+            ENS_UP(ens_upload(e, &sym_dev, sym.data(), sym.size()));
+            ENS_UP(ens_upload(e, &e->eat, (const double *)nullptr, (size_t)mt->nmonth * nnz));
+            ENS_UP(ens_upload(e, &e->edt, (const double *)nullptr, (size_t)mt->nmonth * nnz));
+            k_ens_transpose_values<<<1024, 256>>>((long long)nnz, mt->nmonth, sym_dev, P.ea, e->eat);
+            k_ens_transpose_values<<<1024, 256>>>((long long)nnz, mt->nmonth, sym_dev, P.ed, e->edt);
+            ENS_UP(cudaGetLastError());
+            ENS_UP(ens_upload(e, &e->trit, trit.data(), trit.size()));
+            ENS_UP(ens_upload(e, &e->mfrac_b_dev, (const double *)nullptr, (size_t)nmember * g->n));
+            ENS_UP(cudaMemset(e->mfrac_b_dev, 0, sizeof(double) * (size_t)nmember * g->n));
+            e->adj_ok = 1;
+        }
+    }
     ENS_UP(cudaDeviceSynchronize());
     m3d_status st = upload_params(e);
     if (st != M3D_OK) return bail(st);
@@ -1025,6 +1488,165 @@ m3d_status metos3d_ensemble_autotune(m3d_ensemble *e, const double *Y, int nstep
     if (nw_out) *nw_out = best_w;
     if (ms_out) *ms_out = best;
     return M3D_OK;
+}
+
+// The gradient in the derived slots of one member (slot 0: d/dk_w, slot 1: d/db, the others
+// d/dmp[s] of derive_params) to the gradient in the user's parameters (the chain rule of
+// derive_params: the rates per day times 360, the complements 1 - sigma).
+static void derived_to_user(int model, const double *g, double *ub)
+{
+    switch (model) {
+    case M3D_MODEL_N:
+        ub[0] = g[0]; ub[1] = 360.0 * g[2]; ub[2] = g[3]; ub[3] = g[4]; ub[4] = g[1];
+        break;
+    case M3D_MODEL_NDOP:
+        ub[0] = g[0]; ub[1] = 360.0 * g[2]; ub[2] = g[5] - g[7]; ub[3] = g[6]; ub[4] = g[3]; ub[5] = g[4];
+        ub[6] = g[1];
+        break;
+    case M3D_MODEL_PHY:
+        ub[0] = 360.0 * g[2]; ub[1] = g[0]; ub[2] = g[3]; ub[3] = g[4]; ub[4] = 360.0 * g[5]; ub[5] = g[6] - g[12];
+        ub[6] = 360.0 * g[7]; ub[7] = 360.0 * g[8]; ub[8] = 360.0 * g[9]; ub[9] = g[10] - g[11]; ub[10] = g[1];
+        break;
+    case M3D_MODEL_NPZD:
+        ub[0] = g[0]; ub[1] = 360.0 * g[2]; ub[2] = g[3]; ub[3] = g[4]; ub[4] = 360.0 * g[5]; ub[5] = g[6];
+        ub[6] = g[7] - g[14]; ub[7] = 360.0 * g[8]; ub[8] = 360.0 * g[9]; ub[9] = 360.0 * g[10];
+        ub[10] = 360.0 * g[11]; ub[11] = 360.0 * g[12]; ub[12] = 360.0 * g[13];
+        break;
+    }
+}
+
+m3d_status metos3d_ensemble_year_adjoint(m3d_ensemble *e, const double *Y0, const double *Ybar1, double *Ybar0,
+                                         double *ubar_host, int ckpt_every)
+{
+    if (!e) return efail(nullptr, M3D_ERR_ARG, "metos3d_ensemble_year_adjoint: null ensemble");
+    if (!Y0 || !Ybar1 || !Ybar0) return efail(e, M3D_ERR_ARG, "year_adjoint: null state");
+    if (!e->adj_ok)
+        return efail(e, M3D_ERR_UNSUPPORTED, "year_adjoint: needs a plain (not tangent) ensemble whose explicit "
+                                             "pattern is structurally symmetric");
+    if (e->nsub != 1) return efail(e, M3D_ERR_UNSUPPORTED, "year_adjoint: one internal model step only");
+    const size_t smem_adj = ens_adj_smem_bytes(e->P.nnz_blk_max, e->zmax, e->nwarps, e->nmember);
+    if (smem_adj > e->smem_optin)
+        return efail(e, M3D_ERR_UNSUPPORTED, "year_adjoint: %zu bytes of shared memory needed (%zu available); "
+                                             "choose a smaller tiling", smem_adj, e->smem_optin);
+    ENS_CUDA(e, cudaFuncSetAttribute((const void *)k_ens_adj_explicit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_adj));
+    const size_t smem_imp = sizeof(double) * (6 * (size_t)e->P.cells_blk_max + (size_t)e->nwarps * 2 * e->zmax * kLanes) +
+                            sizeof(int) * 4;
+    ENS_CUDA(e, cudaFuncSetAttribute((const void *)k_ens_adj_implicit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_imp));
+    const int nstep = e->nstep;
+    const int K = ckpt_every <= 0 ? 240 : std::min(ckpt_every, nstep);
+    const int nseg = (nstep + K - 1) / K;
+    const size_t state = sizeof(double) * (size_t)e->n * e->wp;
+    // within a segment the states are kept every K2 steps and each K2-step piece recomputed
+    // in full before its reverse steps: K2 = K unless K states would take more than half of
+    // the free device memory (two levels of checkpoints, each step recomputed at most twice)
+    size_t free_b = 0, total_b = 0;
+    ENS_CUDA(e, cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = free_b / 2 > (size_t)nseg * state ? free_b / 2 - (size_t)nseg * state : 0;
+    long long K2 = std::min<long long>(K, (long long)(budget / state) / 2);
+    if (K2 < 1) return efail(e, M3D_ERR_CUDA, "year_adjoint: not enough device memory for the checkpoints");
+    const int nsub_max = (int)((K + K2 - 1) / K2);
+    double *chk = nullptr, *sub = nullptr, *traj = nullptr, *ybw = nullptr, *zb = nullptr, *upart = nullptr, *ured = nullptr;
+    auto cleanup = [&]() {
+        for (double *q : {chk, sub, traj, ybw, zb, upart, ured})
+            if (q) cudaFree(q);
+    };
+    cudaError_t r = cudaMalloc(&chk, state * nseg);
+    if (r == cudaSuccess) r = cudaMalloc(&sub, state * nsub_max);
+    if (r == cudaSuccess) r = cudaMalloc(&traj, state * K2);
+    if (r == cudaSuccess) r = cudaMalloc(&ybw, 2 * state);
+    if (r == cudaSuccess) r = cudaMalloc(&zb, state);
+    if (r == cudaSuccess) r = cudaMalloc(&upart, sizeof(double) * (size_t)e->nblocks * e->nmember * kParSlots);
+    if (r == cudaSuccess) r = cudaMalloc(&ured, sizeof(double) * (size_t)e->nmember * kParSlots);
+    if (r != cudaSuccess) {
+        cleanup();
+        return efail(e, M3D_ERR_CUDA, "year_adjoint: %s", cudaGetErrorString(r));
+    }
+    EnsAdjParams A{e->eat, e->edt, e->trit, e->mfrac_b_dev, upart, e->nmember};
+    long long launches = 0;
+    auto run = [&]() -> m3d_status {
+        ENS_CUDA(e, cudaMemsetAsync(upart, 0, sizeof(double) * (size_t)e->nblocks * e->nmember * kParSlots, e->stream));
+        ENS_CUDA(e, cudaMemsetAsync(ybw, 0, 2 * state, e->stream));
+        ENS_CUDA(e, cudaMemsetAsync(zb, 0, state, e->stream));
+        // forward sweep: a checkpoint at the start of every segment
+        m3d_status st = pack(e, Y0, chk);
+        launches++;
+        for (int sg = 0; sg + 1 < nseg && st == M3D_OK; sg++) {
+            double *a = chk + (size_t)sg * e->n * e->wp, *b = chk + (size_t)(sg + 1) * e->n * e->wp;
+            for (int jj = sg * K; jj < (sg + 1) * K && st == M3D_OK; jj++) {
+                const int s = jj - sg * K;
+                const double *in = s == 0 ? a : e->xbuf[s & 1];
+                double *out = jj + 1 == (sg + 1) * K ? b : e->xbuf[(s + 1) & 1];
+                st = launch_step(e, jj, in, out);
+                launches++;
+            }
+        }
+        if (st != M3D_OK) return st;
+        st = pack(e, Ybar1, ybw);
+        launches++;
+        int cur = 0;
+        for (int sg = nseg - 1; sg >= 0 && st == M3D_OK; sg--) {
+            const int j0 = sg * K, j1 = std::min(j0 + K, nstep);
+            const int nsub_seg = (int)((j1 - j0 + K2 - 1) / K2);
+            // sub-checkpoints of the segment
+            ENS_CUDA(e, cudaMemcpyAsync(sub, chk + (size_t)sg * e->n * e->wp, state, cudaMemcpyDeviceToDevice,
+                                        e->stream));
+            for (int q = 0; q + 1 < nsub_seg && st == M3D_OK; q++) {
+                const int a0 = j0 + (int)(q * K2), a1 = j0 + (int)((q + 1) * K2);
+                for (int jj = a0; jj < a1 && st == M3D_OK; jj++) {
+                    const int s = jj - a0;
+                    const double *in = s == 0 ? sub + (size_t)q * e->n * e->wp : e->xbuf[s & 1];
+                    double *out = jj + 1 == a1 ? sub + (size_t)(q + 1) * e->n * e->wp : e->xbuf[(s + 1) & 1];
+                    st = launch_step(e, jj, in, out);
+                    launches++;
+                }
+            }
+            for (int q = nsub_seg - 1; q >= 0 && st == M3D_OK; q--) {
+                const int a0 = j0 + (int)(q * K2), a1 = std::min(j1, j0 + (int)((q + 1) * K2));
+                ENS_CUDA(e, cudaMemcpyAsync(traj, sub + (size_t)q * e->n * e->wp, state, cudaMemcpyDeviceToDevice,
+                                            e->stream));
+                for (int jj = a0; jj + 1 < a1 && st == M3D_OK; jj++) {
+                    st = launch_step(e, jj, traj + (size_t)(jj - a0) * e->n * e->wp,
+                                     traj + (size_t)(jj - a0 + 1) * e->n * e->wp);
+                    launches++;
+                }
+                for (int jj = a1 - 1; jj >= a0 && st == M3D_OK; jj--) {
+                    double *yin = ybw + (size_t)cur * e->n * e->wp, *yout = ybw + (size_t)(1 - cur) * e->n * e->wp;
+                    k_ens_adj_implicit<<<e->nblocks, e->nwarps * kLanes, smem_imp, e->stream>>>(e->P, A, jj, yin, zb);
+                    k_ens_adj_explicit<<<e->nblocks, e->nwarps * kLanes, smem_adj, e->stream>>>(
+                        e->P, A, jj, traj + (size_t)(jj - a0) * e->n * e->wp, zb, yout);
+                    ENS_CUDA(e, cudaGetLastError());
+                    launches += 2;
+                    cur = 1 - cur;
+                }
+            }
+        }
+        if (st != M3D_OK) return st;
+        st = unpack(e, ybw + (size_t)cur * e->n * e->wp, Ybar0);
+        launches++;
+        if (st != M3D_OK) return st;
+        const int nm = e->nmember;
+        k_ens_ubar_reduce<<<(nm * kParSlots + 127) / 128, 128, 0, e->stream>>>(e->nblocks, nm, upart, ured);
+        ENS_CUDA(e, cudaGetLastError());
+        launches++;
+        std::vector<double> g((size_t)nm * kParSlots);
+        ENS_CUDA(e, cudaMemcpyAsync(g.data(), ured, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, e->stream));
+        ENS_CUDA(e, cudaStreamSynchronize(e->stream));
+        if (ubar_host) {
+            size_t at = 0;
+            for (int m = 0; m < nm; m++) {
+                derived_to_user(e->models[m], g.data() + (size_t)m * kParSlots, ubar_host + at);
+                at += (size_t)e->nparams[m];
+            }
+        }
+        return M3D_OK;
+    };
+    m3d_status st = run();
+    cudaStreamSynchronize(e->stream);
+    cleanup();
+    e->last_launches = launches;
+    return st;
 }
 
 long long metos3d_ensemble_last_launch_count(const m3d_ensemble *e) { return e ? e->last_launches : -1; }

@@ -1827,4 +1827,6 @@ extern "C" m3d_status metos3d_year_tangent(m3d_ctx *c, const double *y0, const d
 
 m3d_status m3d_prologue(m3d_ctx *c) { return launch_prologue(c, c->u_dev); }
 
+m3d_status m3d_ens_sync_params(m3d_ctx *c) { return ens_sync_params(c); }
+
 m3d_status m3d_step_device(m3d_ctx *c, int j, const double *y, double *yn) { return launch_step(c, j, y, yn); }

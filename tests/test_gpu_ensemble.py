@@ -235,3 +235,58 @@ def test_tangent_ensemble_matches_oracle_tangent(m3d, grid, nsub):
         # a signed perturbation field: normwise
         assert normwise_err(Y1[W + a:W + b], want_jv) < YEAR_TOL, m
     ens.close()
+
+
+@pytest.mark.parametrize("grid,ckpt", [("tiny_6x4x4", 240), ("tiny_6x4x4", 7), ("ndop_64x32x8", 480)])
+def test_ensemble_adjoint_matches_oracle_adjoint(m3d, grid, ckpt):
+    """The reverse sweep of a mixed ensemble (every model) against each member's own adjoint
+    year map in the oracle: the state cotangent normwise, the parameter gradient relative to
+    its largest entry."""
+    p, P = problem(grid)
+    members = mi.make_ensemble(SMALL_MIX, seed=17)
+    ens = m3d.Ensemble.from_problem(p, members)
+    ys = initial_states(p, members, seed=60)
+    r = np.random.default_rng(9)
+    wbars = [r.standard_normal(y.shape) for y in ys]
+    Yb0 = torch.empty((ens.width, p.n), dtype=torch.float64, device="cuda")
+    ubs = ens.year_adjoint(stack(ys), stack(wbars), Yb0, ckpt_every=ckpt)
+    Yb0 = Yb0.cpu().numpy()
+    for m, (y, wb, mem) in enumerate(zip(ys, wbars, members)):
+        a, b = ens.offsets[m], ens.offsets[m + 1]
+        want_y, want_u = oracle.year_adjoint(P, y, mem.u, wb, model=mem.model)
+        assert normwise_err(Yb0[a:b], want_y) < 1e-10, m
+        assert np.abs(ubs[m] - want_u).max() <= 1e-9 * np.abs(want_u).max(), (m, ubs[m], want_u)
+    ens.close()
+
+
+@pytest.mark.parametrize("jv", ["tangent", "fd"])
+def test_ensemble_newton_every_member_periodic(m3d, jv):
+    """Every member's periodic solve at once (one year map of the tangent ensemble per Krylov
+    iteration of all members): each member reaches ||phi(y) - y|| < 1e-8 by its own oracle
+    year map, keeps its mass, and matches the oracle's Newton-Krylov of that member alone."""
+    from oracle import newton as on
+    import math
+    p, P = problem("tiny_6x4x4")
+    # N, PO4-DOP and PO4-DOP-PHY members (NPZD-DOP's periodic solve from its constant start
+    # takes hundreds of Krylov iterations per Newton step in the oracle as on the GPU)
+    members = mi.make_ensemble(((mi.MODEL_N, 2), (mi.MODEL_NDOP, 3), (mi.MODEL_PHY, 2)), seed=23)
+    ens = m3d.Ensemble.from_problem(p, members)
+    tan = m3d.Ensemble.from_problem(p, members, tangent=True) if jv == "tangent" else None
+    ys = initial_states(p, members)
+    Y = stack(ys)
+    st, reps = ens.newton_solve(Y, p.vol, tangent_ensemble=tan, tol=1e-8,
+                                jv=m3d.JV_TANGENT if jv == "tangent" else m3d.JV_FD)
+    assert st == m3d.M3D_OK, [r["residual"] for r in reps]
+    got = Y.cpu().numpy()
+    for m, (y0, mem) in enumerate(zip(ys, members)):
+        a, b = ens.offsets[m], ens.offsets[m + 1]
+        gm = got[a:b]
+        assert reps[m]["converged"] and reps[m]["residual"] < 1e-8
+        assert np.linalg.norm((oracle.year_map(P, gm, mem.u, model=mem.model) - gm).ravel()) < 2e-8, m
+        m0 = math.fsum((p.vol * y0).ravel())
+        assert abs(math.fsum((p.vol * gm).ravel()) / m0 - 1) < 1e-12, m
+        want, _ = on.newton_krylov(P, y0, mem.u, tol=1e-8, model=mem.model)
+        assert np.abs(gm - want).max() / np.abs(want).max() < 1e-6, m
+    ens.close()
+    if tan:
+        tan.close()

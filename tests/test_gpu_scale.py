@@ -155,3 +155,64 @@ def test_adjoint_gradient_matches_central_differences(m3d, grid):
         fd = (J(up) - J(um)) / (2 * e)
         assert abs(grad[k] - fd) <= 1e-5 * abs(fd) + 1e-9 * J0, (k, grad[k], fd)
     ctx.close()
+
+
+def test_npzd_tangent_ensemble_matches_differences(m3d, grid):
+    """The 16-member NPZD-DOP tangent ensemble over a few steps against central differences of
+    the plain ensemble's steps (whose parity with the oracle the tests above check)."""
+    p, _ = grid
+    members = mi.make_ensemble(((mi.MODEL_NPZD, 16),), seed=5)
+    ens = m3d.Ensemble.from_problem(p, members)
+    tan = m3d.Ensemble.from_problem(p, members, tangent=True)
+    ys = [mi.random_state(p, 5, seed=300 + i, scale=(4.4, 0.07, 0.07, 0.07, 0.05)) for i in range(16)]
+    r = np.random.default_rng(12)
+    Y = torch.from_numpy(np.vstack(ys)).cuda()
+    V = torch.from_numpy(r.standard_normal((80, p.n))).cuda()
+    j0, nsteps = 700, 4
+    out = tan.steps(j0, nsteps, torch.cat([Y, V]), torch.empty((160, p.n), dtype=torch.float64, device="cuda"))
+    jv = out[80:].cpu().numpy()
+    h = 1e-6 * float(torch.linalg.norm(Y)) / float(torch.linalg.norm(V))
+    yp = ens.steps(j0, nsteps, Y + h * V, torch.empty_like(Y)).cpu().numpy()
+    ym = ens.steps(j0, nsteps, Y - h * V, torch.empty_like(Y)).cpu().numpy()
+    fd = (yp - ym) / (2 * h)
+    assert rel_err(out[:80].cpu().numpy(), ens.steps(j0, nsteps, Y, torch.empty_like(Y)).cpu().numpy()) < 1e-13
+    for m in range(16):
+        a = slice(5 * m, 5 * m + 5)
+        assert np.abs(jv[a] - fd[a]).max() <= 1e-6 * np.abs(fd[a]).max(), m
+    ens.close()
+    tan.close()
+
+
+def test_npzd_ensemble_adjoint_gradient_matches_differences(m3d, grid):
+    """The 16-member NPZD-DOP ensemble's reverse sweep at 1 degree (checkpoint every 480 steps):
+    the gradient of J = 1/2 |M (phi(Y; u) - obs)|^2 (M: a random 10 % of the cells) in a few
+    parameters of two members, against central differences of the ensemble year map."""
+    p, _ = grid
+    members = mi.make_ensemble(((mi.MODEL_NPZD, 16),), seed=7)
+    ens = m3d.Ensemble.from_problem(p, members)
+    r = mi.rng(1410, "observations")
+    ys = [mi.initial_state(p, 5, mi.model_initial_values(mi.MODEL_NPZD)) for _ in range(16)]
+    Y0 = torch.from_numpy(np.vstack(ys)).cuda()
+    mask = torch.from_numpy((r.random((80, p.n)) < 0.1).astype(np.float64)).cuda()
+    Y1 = ens.year_map(Y0, torch.empty_like(Y0))
+    obs = Y1 * torch.from_numpy(1.0 + 0.05 * r.standard_normal((80, p.n))).cuda()
+
+    def J():
+        y1 = ens.year_map(Y0, torch.empty_like(Y0))
+        return 0.5 * float(torch.sum((mask * (y1 - obs)) ** 2))
+
+    grads = ens.year_adjoint(Y0, mask * mask * (Y1 - obs), torch.empty_like(Y0), ckpt_every=480)
+    J0 = J()
+    for m, k in ((0, 0), (0, 1), (9, 12)):
+        u0 = np.asarray(members[m].u, dtype=np.float64)
+        e = 1e-6 * u0[k]
+        vals = []
+        for sgn in (1.0, -1.0):
+            uu = u0.copy()
+            uu[k] += sgn * e
+            ens.set_params(m, uu)
+            vals.append(J())
+        ens.set_params(m, u0)
+        fd = (vals[0] - vals[1]) / (2 * e)
+        assert abs(grads[m][k] - fd) <= 1e-5 * abs(fd) + 1e-9 * J0, (m, k, grads[m][k], fd)
+    ens.close()
