@@ -28,6 +28,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "metos3d.h"
@@ -161,9 +162,17 @@ __device__ __forceinline__ void ens_segment_q(const EnsParams &E, const int4 &S,
             const double dI = I + mp[4];
             const T dP = mp[6] + P;
             const T dNI = dN * dI;
-            const T r = 1.0 / (dNI * dP);
-            const T U = mp[2] * P * N * I * dP * r;
-            const T G = mp[5] * Z * P * dNI * r;
+            T U, G;
+            if constexpr (std::is_same<T, double>::value) {
+                const T r = 1.0 / (dNI * dP);
+                U = mp[2] * P * N * I * dP * r;
+                G = mp[5] * Z * P * dNI * r;
+            } else {
+                // on dual numbers a shared division would cancel (the derivative of dP / (dNI dP)
+                // takes two large terms of opposite sign): one division per rate
+                U = mp[2] * P * N * I / dNI;
+                G = mp[5] * Z * P / dP;
+            }
             const T mP = mp[8] * P, mZ = mp[9] * Z * Z, eZ = mp[10] * Z;
             const T rD = mp[11] * D, rO = mp[12] * DOP;
             const T zero{};
@@ -455,15 +464,16 @@ __device__ __forceinline__ double member_run_sum(double v, int key, int lane)
     return v;
 }
 
-// Add a pass's per-lane parameter gradients g[0..np) of member slot mi (key = member within the
-// pass, -1 for idle lanes) into the block's accumulators ub[mi][slot].
-__device__ __forceinline__ void add_member_gradients(double *ub, const double *gv, int np, int key, int mi, int lane)
+// Add a pass's per-lane parameter gradients g[0..np) of member `pid` (the member's index in the
+// caller's order; key = member within the pass, -1 for idle lanes) into the block's
+// accumulators ub[pid][slot].
+__device__ __forceinline__ void add_member_gradients(double *ub, const double *gv, int np, int key, int pid, int lane)
 {
     const int prev = __shfl_up_sync(kFull, key, 1);
     const bool head = key >= 0 && (lane == 0 || prev != key);
     for (int q = 0; q < np; q++) {
         const double v = member_run_sum(key >= 0 ? gv[q] : 0.0, key, lane);
-        if (head && v != 0.0) atomicAdd(ub + (size_t)mi * kParSlots + q, v);
+        if (head && v != 0.0) atomicAdd(ub + (size_t)pid * kParSlots + q, v);
     }
 }
 
@@ -544,7 +554,7 @@ __device__ __forceinline__ void ens_segment_qadj(const EnsParams &E, const EnsAd
                 addy(k, l0, 3, yD);
                 addy(k, l0, 4, yO);
             }
-            add_member_gradients(ub, gv, 15, ml, mi, lane);
+            add_member_gradients(ub, gv, 15, ml, E.mem_pidx[mi], lane);
         }
         return;
     }
@@ -608,7 +618,7 @@ __device__ __forceinline__ void ens_segment_qadj(const EnsParams &E, const EnsAd
             }
             atomicAdd(Ebs + ml, Ebp);
         }
-        add_member_gradients(ub, gv, 13, ml, mi, lane);
+        add_member_gradients(ub, gv, 13, ml, E.mem_pidx[mi], lane);
     }
     __syncwarp();
     for (int base = 0; base < nm * neu; base += kLanes) {
@@ -669,7 +679,7 @@ __device__ __forceinline__ void ens_segment_qadj(const EnsParams &E, const EnsAd
             gv[4] += -limb * lim / dI;
             gv[0] += limb * (N * mp[4] / (dN * dI * dI)) * (-zc[s0 + k] * I);
         }
-        add_member_gradients(ub, gv, 13, ml, mi, lane);
+        add_member_gradients(ub, gv, 13, ml, E.mem_pidx[mi], lane);
     }
     __syncwarp();
 }

@@ -214,6 +214,25 @@ def test_rejects_oversized_tiling(m3d):
     ens.close()
 
 
+def tangent_sensitivity(P, y, v, mem, nsub, jv):
+    """How much the oracle's own phi'(y) v moves (normwise) when y moves by a rounding-level
+    1e-14 relative: two correct FP64 evaluations whose trajectories differ by rounding cannot
+    agree better.  Tiny for the transport-dominated models; NPZD-DOP's predator-prey
+    dynamics amplify it to 1e-10 .. 1e-8 on these grids."""
+    r = np.random.default_rng(77)
+    y2 = y * (1.0 + 1e-14 * r.standard_normal(y.shape))
+    _, jv2 = oracle.year_tangent(P, y2, v, mem.u, model=mem.model, nsub=nsub)
+    return normwise_err(jv2, jv)
+
+
+def adjoint_sensitivity(P, y, wb, mem, yb, ub):
+    """The same for the oracle's adjoint year map (state cotangent, parameter gradient)."""
+    r = np.random.default_rng(78)
+    y2 = y * (1.0 + 1e-14 * r.standard_normal(y.shape))
+    yb2, ub2 = oracle.year_adjoint(P, y2, mem.u, wb, model=mem.model)
+    return normwise_err(yb2, yb), float(np.abs(ub2 - ub).max() / np.abs(ub).max())
+
+
 @pytest.mark.parametrize("grid,nsub", [("tiny_6x4x4", 1), ("tiny_6x4x4", 3), ("ndop_64x32x8", 1)])
 def test_tangent_ensemble_matches_oracle_tangent(m3d, grid, nsub):
     """A tangent ensemble (every model, several lane groups) returns each member's phi(y) and
@@ -232,8 +251,9 @@ def test_tangent_ensemble_matches_oracle_tangent(m3d, grid, nsub):
         a, b = ens.offsets[m], ens.offsets[m + 1]
         want_phi, want_jv = oracle.year_tangent(P, y, v, mem.u, model=mem.model, nsub=nsub)
         assert rel_err(Y1[a:b], want_phi) < YEAR_TOL, m
-        # a signed perturbation field: normwise
-        assert normwise_err(Y1[W + a:W + b], want_jv) < YEAR_TOL, m
+        # a signed perturbation field: normwise, within the tangent's own condition
+        tol = max(YEAR_TOL, 10.0 * tangent_sensitivity(P, y, v, mem, nsub, want_jv))
+        assert normwise_err(Y1[W + a:W + b], want_jv) < tol, (m, tol)
     ens.close()
 
 
@@ -254,8 +274,9 @@ def test_ensemble_adjoint_matches_oracle_adjoint(m3d, grid, ckpt):
     for m, (y, wb, mem) in enumerate(zip(ys, wbars, members)):
         a, b = ens.offsets[m], ens.offsets[m + 1]
         want_y, want_u = oracle.year_adjoint(P, y, mem.u, wb, model=mem.model)
-        assert normwise_err(Yb0[a:b], want_y) < 1e-10, m
-        assert np.abs(ubs[m] - want_u).max() <= 1e-9 * np.abs(want_u).max(), (m, ubs[m], want_u)
+        sy, su = adjoint_sensitivity(P, y, wb, mem, want_y, want_u)
+        assert normwise_err(Yb0[a:b], want_y) < max(1e-10, 10.0 * sy), (m, sy)
+        assert np.abs(ubs[m] - want_u).max() <= max(1e-9, 10.0 * su) * np.abs(want_u).max(), (m, ubs[m], want_u)
     ens.close()
 
 
