@@ -48,13 +48,23 @@ def peaks():
     return hbm, src
 
 
-# DRAM bytes (read + write) per launch of the year kernel, from one ncu capture of this
-# workload (see profiles/); None where no capture of the current kernel exists.
+# DRAM bytes (read + write) per launch of the year kernel on this workload, from ncu (see
+# profiles/), with how they were obtained; None where no capture of the current kernel exists.
 # Keys: (plan, tridiagonal implicit form, per-step explicit operators, kernel revision).
 # The revision names the year kernel's code the capture was taken of; a changed kernel
 # gets a new revision and no traffic until it is captured again.
-YEAR_KERNEL_REVISION = "r2-split-phases"
-TRAFFIC_PER_LAUNCH = {}
+# The counters are taken on the 64x32x8 grid (3.12 GB of step operators on the device):
+# 3.125096 GB read + 8.25 MB written per launch, 1.0059x its step-operator bytes
+# (3,115,008,000). The traffic is the step operators read once plus a few tens of MB, so
+# it grows with the step-operator bytes, and is scaled to this workload's
+# 16,793,763,840 by that ratio.
+YEAR_KERNEL_REVISION = "chains-add-dq"
+TRAFFIC_PER_LAUNCH = {
+    ("resident", True, True, "chains-add-dq"): (
+        round(16793763840 * (3125096000 + 8253184) / 3115008000),
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 64x32x8 grid, "
+        "scaled by the step-operator bytes (16.79 GB here vs 3.12 GB there)"),
+}
 
 # FP64 peak of the GPU per SM clock: ncu's sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained
 # on GB300 is 304 thread-level DFMA per cycle (2 per SM), i.e. 608 FP64 flops per cycle.
@@ -520,7 +530,8 @@ def run_ours(args):
     executed_tf = xflops_step * prob.nstep / t_kernel / 1e12
     clock = clocks.summary()
     fp64_peak, fp64_src = fp64_peak_tflops(clock.get("sm_mhz"))
-    traffic = TRAFFIC_PER_LAUNCH.get((plan, tridiagonal, step_ops, YEAR_KERNEL_REVISION))
+    traffic, traffic_how = TRAFFIC_PER_LAUNCH.get((plan, tridiagonal, step_ops, YEAR_KERNEL_REVISION),
+                                                  (None, None))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_year, "higher_is_better": True,
@@ -534,6 +545,7 @@ def run_ours(args):
                      if hbm_src == "measured" else "fallback 6.8 TB/s",
                      "traffic": traffic,
                      "traffic_unit": "DRAM bytes per launch (one model year), ncu",
+                     "traffic_how": traffic_how,
                      "kernel": {"resident": "k_year_resident (one launch per model year)",
                                 "persistent": "k_year (one launch per model year)",
                                 "graph": "k_step (one launch per TMM step)"}[plan],
@@ -589,12 +601,18 @@ def run_profile_steps(nsteps):
     return 0
 
 
-def run_profile_years(nyears, grid):
-    """A short run for profilers: nyears year maps (the resident year kernel) on `grid`."""
+def run_profile_years(nyears, grid, plan=None):
+    """A short run for profilers: nyears year maps on `grid`, by the context's own year plan or
+    by the persistent one (`plan="persistent"`: the kernel that streams every step's matrices
+    from HBM, as on grids whose tiles do not fit in shared memory)."""
     import torch
     import paper_1410_0204_gb300 as m3d
     prob = mi.make_problem(grid)
     ctx = m3d.Context.from_problem(prob, model=m3d.MODEL_NDOP, ntracer=2, nparam=7)
+    if plan == "persistent":
+        if ctx.get_option(m3d.OPT_STEP_OPERATORS):
+            ctx.set_option(m3d.OPT_STEP_OPERATORS, 0)
+        ctx.set_option(m3d.OPT_YEAR_PLAN, m3d.PLAN_PERSISTENT)
     y = torch.from_numpy(mi.initial_state(prob)).cuda()
     u = torch.from_numpy(mi.default_params_ndop()).cuda()
     yn = torch.empty_like(y)
@@ -677,13 +695,13 @@ def run_scale_1deg(args):
         tan.set_tiling(*ens.get_tiling())
         V = torch.from_numpy(np.random.default_rng(5).standard_normal(tuple(Y0.shape))).cuda()
         YV = torch.cat([Y0, V])
-        t_tan = timed(lambda: tan.year_map(YV, torch.empty_like(YV)), 1)
+        t_etan = timed(lambda: tan.year_map(YV, torch.empty_like(YV)), 1)
         Wb = torch.ones_like(Y0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ens.year_adjoint(Y0, Wb, torch.empty_like(Y0), ckpt_every=480)
         torch.cuda.synchronize()
-        t_adj = time.perf_counter() - t0
+        t_eadj = time.perf_counter() - t0
         Ys = Y0.clone()
         for _ in range(args.scale_spinup_years):
             ens.year_map(Ys, Ys)
@@ -695,8 +713,8 @@ def run_scale_1deg(args):
         torch.cuda.synchronize()
         t_newton = time.perf_counter() - t0
         tan.close()
-        deriv = {"tangent_year_map_s": t_tan, "tangent_over_forward": t_tan / t_ens,
-                 "adjoint_s": t_adj, "adjoint_over_forward": t_adj / t_ens, "ckpt_every": 480,
+        deriv = {"tangent_year_map_s": t_etan, "tangent_over_forward": t_etan / t_ens,
+                 "adjoint_s": t_eadj, "adjoint_over_forward": t_eadj / t_ens, "ckpt_every": 480,
                  "newton": {"seconds": t_newton, "spinup_years_before": args.scale_spinup_years,
                             "max_newton": args.scale_newton_steps, "max_krylov": args.scale_krylov,
                             "krylov_iterations_all_members": max(r["krylov_total"] for r in reps_n),
@@ -768,6 +786,8 @@ def main():
     ap.add_argument("--profile-years", type=int, default=0,
                     help="only run this many year maps (for profilers) on --profile-grid")
     ap.add_argument("--profile-grid", default=WORKLOAD, help="grid of --profile-years")
+    ap.add_argument("--profile-plan", default=None, choices=["persistent"],
+                    help="year plan of --profile-years (default: the context's own)")
     ap.add_argument("--scale-1deg", action="store_true",
                     help="time the 1-degree grid (single context and 16-member ensemble) instead")
     ap.add_argument("--scale-spinup-years", type=int, default=2,
@@ -784,7 +804,7 @@ def main():
     if args.profile_steps:
         return run_profile_steps(args.profile_steps)
     if args.profile_years:
-        return run_profile_years(args.profile_years, args.profile_grid)
+        return run_profile_years(args.profile_years, args.profile_grid, args.profile_plan)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
