@@ -266,8 +266,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def cpu_baseline(prob, seconds=12.0, max_steps=2880):
-    """The CPU oracle as it stands, on all host cores, over a bounded sample of the year."""
+def cpu_baseline(prob, seconds=12.0, max_steps=16 * 2880):
+    """The CPU oracle as it stands, on all host cores, over a bounded sample of the workload:
+    consecutive TMM steps of the year map for about `seconds`, at most 16 model years."""
     import oracle
     threads = oracle.set_threads(os.cpu_count() or 1)
     P = oracle.Problem(prob)
@@ -291,8 +292,8 @@ def cpu_baseline(prob, seconds=12.0, max_steps=2880):
         steps1 += chunk
     dt1 = time.perf_counter() - t1
     return {"value": years / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d of the 2880 TMM steps of the %s year map, FP64 C oracle, %d OpenMP threads, %.1f s"
-                      % (steps, WORKLOAD, threads, dt),
+            "sample": "%d consecutive TMM steps (%.2f model years) of the %s year map, FP64 C oracle, "
+                      "%d OpenMP threads, %.1f s" % (steps, years, WORKLOAD, threads, dt),
             "single_thread": {"value": steps1 / prob.nstep / dt1, "unit": UNIT, "cores": 1,
                               "sample": "%d TMM steps, %.1f s" % (steps1, dt1)}}
 
@@ -319,6 +320,14 @@ def dist_env():
     return world, rank, local
 
 
+def workload_config(prob, world):
+    """The bench line's `config`, the same for both arms."""
+    return {"workload": WORKLOAD + " year map: PO4-DOP, 2 tracers, 2880 TMM steps per model year",
+            "n": prob.n, "ncol": prob.ncol, "nnz": prob.nnz, "S_imp": prob.s_imp,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between timed iterations (256 MiB write); 12 months of matrices (~270 MB) exceed L2"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -341,10 +350,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD + " year map, PO4-DOP, 2 tracers, 2880 steps/year",
-                       "sample": "each step: %d TMM steps (1/10 model year)" % sample_steps},
+            "config": workload_config(prob, args.gpus),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": "%d x %d TMM steps of the %s year map" % (args.steps, sample_steps, WORKLOAD)},
+                             "sample": "%d x %d TMM steps (each bench step 1/10 model year) of the %s year map"
+                                       % (args.steps, sample_steps, WORKLOAD)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -536,10 +545,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_year, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " year map: PO4-DOP, 2 tracers, 2880 TMM steps per model year",
-                   "n": prob.n, "ncol": prob.ncol, "nnz": prob.nnz, "S_imp": prob.s_imp,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between timed iterations (256 MiB write); 12 months of matrices (~270 MB) exceed L2"},
+        "config": workload_config(prob, world),
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src + " (MEASURED_PEAKS hbm_gbs)"
                      if hbm_src == "measured" else "fallback 6.8 TB/s",
