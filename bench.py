@@ -638,6 +638,12 @@ def run_scale_1deg(args):
     the 16-member NPZD-DOP ensemble year map, each timed with CUDA events over whole years."""
     import torch
     import paper_1410_0204_gb300 as m3d
+    t_start = time.perf_counter()
+
+    def progress(what):
+        sys.stderr.write("[scale-1deg %7.1f s] %s\n" % (time.perf_counter() - t_start, what))
+        sys.stderr.flush()
+
     name = "npzd_360x180x23"
     prob = mi.make_problem(name)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -665,6 +671,7 @@ def run_scale_1deg(args):
     u = torch.from_numpy(mi.default_params_ndop()).cuda()
     ya = torch.empty_like(y0)
     t_single = timed(lambda: ctx.year_map(y0, ya, u), reps)
+    progress("single-context year map")
     # the adjoint (streaming sweep on this grid), checkpoint every 480 steps, wall clock
     yb0 = torch.empty_like(y0)
     ybar1 = torch.ones_like(y0)
@@ -674,12 +681,14 @@ def run_scale_1deg(args):
     ctx.year_adjoint(y0, u, ybar1, yb0, 480)
     torch.cuda.synchronize()
     t_adj = time.perf_counter() - t0
+    progress("single-context adjoint")
     adj_plan = {m3d.PLAN_RESIDENT: "resident", m3d.PLAN_PERSISTENT: "streaming"}.get(
         ctx.get_option(m3d.OPT_ADJOINT_PLAN), "none")
     # the tangent year map (phi and phi' v in one pass), CUDA events
     v = torch.ones_like(y0)
     phi, jv = torch.empty_like(y0), torch.empty_like(y0)
     t_tan = timed(lambda: ctx.year_tangent(y0, v, u, phi, jv), reps)
+    progress("single-context tangent")
     tridiagonal = ctx.get_option(m3d.OPT_IMPLICIT_FORM) == m3d.IMPLICIT_TRIDIAGONAL
     ctx.close()
     _, flops_single = method_per_step(prob)
@@ -690,7 +699,9 @@ def run_scale_1deg(args):
                                      for _ in members])).cuda()
     Y1 = torch.empty_like(Y0)
     cpb, nw, ms = ens.autotune(Y0, nsteps=5)
+    progress("ensemble autotune")
     t_ens = timed(lambda: ens.year_map(Y0, Y1), reps)
+    progress("ensemble year map")
     # the ensemble's derivatives: one tangent-ensemble year map (phi and phi' v of all 16 members:
     # one Krylov iteration of all members' Newton-Krylov solves), the reverse sweep (checkpoint
     # every 480 steps), and a bounded batched Newton-Krylov run (tangent products) from a state
@@ -702,22 +713,26 @@ def run_scale_1deg(args):
         V = torch.from_numpy(np.random.default_rng(5).standard_normal(tuple(Y0.shape))).cuda()
         YV = torch.cat([Y0, V])
         t_etan = timed(lambda: tan.year_map(YV, torch.empty_like(YV)), 1)
+        progress("tangent-ensemble year map")
         Wb = torch.ones_like(Y0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ens.year_adjoint(Y0, Wb, torch.empty_like(Y0), ckpt_every=480)
         torch.cuda.synchronize()
         t_eadj = time.perf_counter() - t0
+        progress("ensemble reverse sweep")
         Ys = Y0.clone()
         for _ in range(args.scale_spinup_years):
             ens.year_map(Ys, Ys)
         torch.cuda.synchronize()
+        progress("spin-up")
         t0 = time.perf_counter()
         st, reps_n = ens.newton_solve(Ys, prob.vol, tangent_ensemble=tan, tol=1e-8, jv=m3d.JV_TANGENT,
                                       max_newton=args.scale_newton_steps, max_krylov=args.scale_krylov,
                                       restart=args.scale_krylov)
         torch.cuda.synchronize()
         t_newton = time.perf_counter() - t0
+        progress("ensemble Newton-Krylov")
         tan.close()
         deriv = {"tangent_year_map_s": t_etan, "tangent_over_forward": t_etan / t_ens,
                  "adjoint_s": t_eadj, "adjoint_over_forward": t_eadj / t_ens, "ckpt_every": 480,
