@@ -328,6 +328,9 @@ m3d_status metos3d_spinup(m3d_ctx *ctx, double *y, const double *u, int nyears, 
  * (I - phi'(y)) s = -F(y) is solved by restarted GMRES with modified Gram-Schmidt
  * orthogonalisation to the Eisenstat-Walker tolerance (choice 2: eta_0 = 0.3,
  * gamma = 0.9, alpha = (1+sqrt 5)/2, safeguarded, kept within [0.5 tol/||F||, 0.9]).
+ * A trial step whose residual is not finite (the state left the model's domain) is cut to a
+ * tenth and gives the interpolation no point; no step length below 1e-4 is tried: the solve
+ * then stops at its iterate (report->line_search_failed).
  * Jacobian-vector products are finite differences, J v = v - (phi(y + h v) - phi(y)) / h
  * with h = fd_eps ||y|| / ||v|| (M3D_JV_FD), or exact, J v = v - phi'(y) v by the tangent
  * year map (M3D_JV_TANGENT, see metos3d_year_tangent).  phi conserves the total mass, so I - phi' is singular and
@@ -369,6 +372,9 @@ typedef struct {
     int ntrial;                              /* entries of trial_lambdas */
     double trial_lambdas[M3D_NEWTON_MAX_TRIALS];  /* every step length tried, in order */
     double seconds;
+    int line_search_failed;     /* 1: the last step's line search found no decrease with a step
+                                   length of 1e-4 or more; the solve stopped at its iterate (that
+                                   step's lambda is 0) */
 } m3d_newton_report;
 
 void metos3d_newton_default_options(m3d_newton_opts *opts);

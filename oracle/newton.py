@@ -136,26 +136,35 @@ def cubic_backtrack(f0, slope, lam, f_lam, lam_prev, f_prev):
 
 
 def line_search(f, f0, slope, armijo=1e-4, lam_min=1e-4, lo=0.1, hi=0.5):
-    """Backtracking line search along a descent direction of f, with f(0) = f0, f'(0) = slope < 0.
+    """Backtracking line search along a descent direction of f, with f(0) = f0, f'(0) = slope < 0
+    (Dennis & Schnabel, Algorithm A6.3.1).
 
     Tries lam = 1 first and accepts the first lam with the Armijo decrease
-    f(lam) <= f0 + armijo lam slope (or lam below lam_min).  After a failed trial the next lam
-    is the minimiser of the quadratic model (first backtrack) or of the cubic model through
-    the last two trials (later backtracks), kept within [lo, hi] times the failed lam.
+    f(lam) <= f0 + armijo lam slope.  After a failed trial the next lam is the minimiser of the
+    quadratic model (first backtrack) or of the cubic model through the last two trials (later
+    backtracks), kept within [lo, hi] times the failed lam.  A trial whose f is not finite (the
+    model state left its domain) gives no model: the next lam is lo times it, and the next
+    finite failure starts from the quadratic model again.  A lam below lam_min is not tried:
+    the search fails and returns (0.0, f0, trials), no step.
     Returns (lam, f(lam), trials), trials the list of (lam, f(lam)) in the order tried.
     """
     lam, prev, trials = 1.0, None, []
-    while True:
+    while lam >= lam_min:
         fl = f(lam)
         trials.append((lam, fl))
-        if fl <= f0 + armijo * lam * slope or lam < lam_min:
+        if not math.isfinite(fl):
+            prev = None
+            lam = lo * lam
+            continue
+        if fl <= f0 + armijo * lam * slope:
             return lam, fl, trials
         if prev is None:
             lt = quadratic_backtrack(f0, slope, lam, fl)
         else:
             lt = cubic_backtrack(f0, slope, lam, fl, prev[0], prev[1])
         prev = (lam, fl)
-        lam = min(max(lt, lo * lam), hi * lam)
+        lam = min(max(lt, lo * lam), hi * lam) if math.isfinite(lt) else lo * lam
+    return 0.0, f0, trials
 
 
 def newton_krylov(P, y0, u, tol=1e-8, max_newton=40, restart=200, max_krylov=200, fd_eps=1e-8,
@@ -198,7 +207,8 @@ def newton_solve(phi, y0, tol=1e-8, max_newton=40, restart=200, max_krylov=200, 
     GMRES cycle, which restart >= max_krylov gives): the inexact step's own slope, not the
     -||F||^2 of an exact Newton step (with eta up to 0.9 the two differ by a factor up to 5).
     The report holds, per Newton step, eta, the GMRES iterations and residual rho, the slope,
-    the accepted lam and every lam tried; with record_steps, also the steps s and the states
+    the accepted lam (0 where the line search found no acceptable step: the solve then stops at
+    the current iterate with line_search_failed) and every lam tried; with record_steps, also the steps s and the states
     y they start from.
     """
     y = np.array(y0, dtype=np.float64)
@@ -206,7 +216,9 @@ def newton_solve(phi, y0, tol=1e-8, max_newton=40, restart=200, max_krylov=200, 
     F = y - py
     r = float(np.linalg.norm(F))
     rep = {"residuals": [r], "krylov": [], "year_maps": 1, "lambdas": [], "etas": [], "slopes": [],
-           "gmres_residuals": [], "trials": [], "converged": False}
+           "gmres_residuals": [], "trials": [], "converged": False, "line_search_failed": False}
+    if not math.isfinite(r):
+        return y, rep
     if record_steps:
         rep["steps"], rep["states"] = [], []
     eta_prev, r_prev = None, None
@@ -244,14 +256,19 @@ def newton_solve(phi, y0, tol=1e-8, max_newton=40, restart=200, max_krylov=200, 
         if record_steps:
             rep["steps"].append(s.copy())
             rep["states"].append(y.copy())
-        yn = y + lam * s
-        pyn = cache[lam]
         rep["krylov"].append(its)
         rep["etas"].append(eta)
         rep["gmres_residuals"].append(rho)
         rep["slopes"].append(slope)
         rep["lambdas"].append(lam)
         rep["trials"].append([t[0] for t in trials])
+        if lam == 0.0:
+            # no acceptable step along s: stop at the current iterate
+            rep["line_search_failed"] = True
+            rep["residuals"].append(r)
+            break
+        yn = y + lam * s
+        pyn = cache[lam]
         y, py, F = yn, pyn, yn - pyn
         r_prev, eta_prev = r, eta
         r = math.sqrt(2.0 * fn)

@@ -86,7 +86,8 @@ class NewtonReport(C.Structure):
                 ("krylov", C.c_int * NEWTON_MAX_HIST), ("lambdas", C.c_double * NEWTON_MAX_HIST),
                 ("etas", C.c_double * NEWTON_MAX_HIST), ("slopes", C.c_double * NEWTON_MAX_HIST),
                 ("trials", C.c_int * NEWTON_MAX_HIST), ("ntrial", C.c_int),
-                ("trial_lambdas", C.c_double * NEWTON_MAX_TRIALS), ("seconds", C.c_double)]
+                ("trial_lambdas", C.c_double * NEWTON_MAX_TRIALS), ("seconds", C.c_double),
+                ("line_search_failed", C.c_int)]
 
     def to_dict(self):
         k = self.newton_steps
@@ -101,7 +102,7 @@ class NewtonReport(C.Structure):
                 "residual": self.residual, "residuals": list(self.residuals[:k + 1]),
                 "krylov": list(self.krylov[:kk]), "lambdas": list(self.lambdas[:kk]),
                 "etas": list(self.etas[:kk]), "slopes": list(self.slopes[:kk]), "trials": per_step,
-                "seconds": self.seconds}
+                "seconds": self.seconds, "line_search_failed": bool(self.line_search_failed)}
 
 
 JV_FD = 0

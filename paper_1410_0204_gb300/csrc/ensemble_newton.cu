@@ -207,11 +207,12 @@ extern "C" m3d_status metos3d_ensemble_newton_solve(m3d_ensemble *ens, m3d_ensem
         for (double x : vh) vv += x * x;
         for (int m = 0; m < nm; m++) wsum[m] = vv * (off[m + 1] - off[m]);
     }
+    std::vector<char> stopped(nm, 0);         // members whose line search found no decrease
     for (int it = 0; it < o.max_newton; it++) {
         std::vector<char> act(nm, 0);
         bool any = false;
         for (int m = 0; m < nm; m++) {
-            act[m] = r[m] > o.tol && R[m].newton_steps < o.max_newton;
+            act[m] = !stopped[m] && r[m] > o.tol && std::isfinite(r[m]) && R[m].newton_steps < o.max_newton;
             any = any || act[m];
         }
         if (!any) break;
@@ -334,11 +335,23 @@ extern "C" m3d_status metos3d_ensemble_newton_solve(m3d_ensemble *ens, m3d_ensem
             R[m].etas[std::min(R[m].newton_steps, M3D_NEWTON_MAX_HIST - 1)] = eta[m];
             R[m].slopes[std::min(R[m].newton_steps, M3D_NEWTON_MAX_HIST - 1)] = slope[m];
         }
+        // each member backtracks as the single solve does: a trial whose residual is not finite
+        // gives no model and is cut to a tenth; no step below 1e-4 is tried, and a member whose
+        // search fails keeps its iterate (lambda 0) and stops
         int trials = 0;
+        std::vector<double> lam_eval(nm, -1.0);     // the step lengths of the last evaluated trial
         while (true) {
             bool anyls = false;
-            for (int m = 0; m < nm; m++) anyls = anyls || ls[m];
+            for (int m = 0; m < nm; m++) {
+                if (ls[m] && o.line_search && lam[m] < 1e-4) {
+                    ls[m] = 0;
+                    lam[m] = 0.0;
+                    stopped[m] = 1;
+                }
+                anyls = anyls || ls[m];
+            }
             if (!anyls) break;
+            lam_eval = lam;
             CK(axpby(Yt, one, Y, lam, S));
             ST(phi(Yt, PYt));
             CK(axpby(tmp, one, Yt, mone, PYt));
@@ -349,7 +362,16 @@ extern "C" m3d_status metos3d_ensemble_newton_solve(m3d_ensemble *ens, m3d_ensem
                 fn[m] = 0.5 * dv[m];
                 if (R[m].ntrial < M3D_NEWTON_MAX_TRIALS) R[m].trial_lambdas[R[m].ntrial++] = lam[m];
                 R[m].trials[std::min(R[m].newton_steps, M3D_NEWTON_MAX_HIST - 1)]++;
-                if (!o.line_search || fn[m] <= f0[m] + 1e-4 * lam[m] * slope[m] || lam[m] < 1e-4) {
+                if (!o.line_search) {
+                    ls[m] = 0;
+                    continue;
+                }
+                if (!std::isfinite(fn[m])) {
+                    lamp[m] = -1.0;
+                    lam[m] *= 0.1;
+                    continue;
+                }
+                if (fn[m] <= f0[m] + 1e-4 * lam[m] * slope[m]) {
                     ls[m] = 0;
                     continue;
                 }
@@ -357,14 +379,28 @@ extern "C" m3d_status metos3d_ensemble_newton_solve(m3d_ensemble *ens, m3d_ensem
                                                 : cubic_bt(f0[m], slope[m], lam[m], fn[m], lamp[m], fp[m]);
                 lamp[m] = lam[m];
                 fp[m] = fn[m];
-                lam[m] = std::min(std::max(lt, 0.1 * lam[m]), 0.5 * lam[m]);
+                lam[m] = std::isfinite(lt) ? std::min(std::max(lt, 0.1 * lam[m]), 0.5 * lam[m]) : 0.1 * lam[m];
             }
-            if (trials > 64) break;
+            if (trials > 64) {              // not reached: lambda falls below 1e-4 within 14 trials
+                for (int m = 0; m < nm; m++)
+                    if (ls[m]) {
+                        ls[m] = 0;
+                        lam[m] = 0.0;
+                        stopped[m] = 1;
+                    }
+                break;
+            }
         }
-        // accept: Y += lam S, phi(Y) from the last evaluation at the accepted lam (one more map
-        // when members accepted at different trials)
-        CK(axpby(Y, one, Y, lam, S));
-        ST(phi(Y, PY));
+        // accept: Y += lam S.  When the last trial evaluated every member at its accepted step
+        // length, that trial is the new iterate and its year map is phi(Y) (the same kernels on
+        // the same inputs, so the same bits); otherwise one more year map.
+        if (lam_eval == lam) {
+            CK(cudaMemcpyAsync(Y, Yt, sizeof(double) * len, cudaMemcpyDeviceToDevice, s0));
+            CK(cudaMemcpyAsync(PY, PYt, sizeof(double) * len, cudaMemcpyDeviceToDevice, s0));
+        } else {
+            CK(axpby(Y, one, Y, lam, S));
+            ST(phi(Y, PY));
+        }
         CK(axpby(F, one, Y, mone, PY));
         CK(member_dots(F, F, dv));
         for (int m = 0; m < nm; m++) {
@@ -373,6 +409,7 @@ extern "C" m3d_status metos3d_ensemble_newton_solve(m3d_ensemble *ens, m3d_ensem
             etaprev[m] = eta[m];
             r[m] = std::sqrt(dv[m]);
             R[m].lambdas[std::min(R[m].newton_steps, M3D_NEWTON_MAX_HIST - 1)] = lam[m];
+            if (stopped[m]) R[m].line_search_failed = 1;
             R[m].newton_steps++;
             R[m].residuals[std::min(R[m].newton_steps, M3D_NEWTON_MAX_HIST - 1)] = r[m];
         }

@@ -589,7 +589,7 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
     // the ensemble-backed models run their year as a graph of step launches, which does not
     // honour SyncParams::skip: their Krylov iterations are checked one at a time
     const int lag = c->ens ? 0 : 1;
-    while (R.newton_steps < o.max_newton && r > o.tol) {
+    while (R.newton_steps < o.max_newton && r > o.tol && std::isfinite(r)) {
         const int step = R.newton_steps, hs = std::min(step, M3D_NEWTON_MAX_HIST - 1);
         const double eta = forcing_term(step == 0, r, r_prev, eta_prev, o.tol);
         double ynorm = 0.0;
@@ -617,9 +617,17 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
         const double rho = res_rel * r;
         const double f0 = 0.5 * r * r, slope = -(r * r - rho * rho);
         R.slopes[hs] = slope;
+        // Backtracking (Dennis & Schnabel, Algorithm A6.3.1): a trial whose residual is not
+        // finite gives no model, the next one is a tenth of it; no step below 1e-4 is tried,
+        // and when the search fails the solve stops at its current iterate.
         double lam = 1.0, lam_prev = -1.0, f_prev = 0.0, fn = 0.0;
         int trials = 0;
+        bool failed = false;
         while (true) {
+            if (o.line_search && lam < 1e-4) {
+                failed = true;
+                break;
+            }
             TRY(S.axpby(W.yn, 1.0, W.y, lam, W.s));
             TRY(phi_rec(W.yn, W.pyn, W.fn_next));
             TRY(metos3d_sync(c));
@@ -629,12 +637,26 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
             fn = 0.5 * rn * rn;
             trials++;
             if (R.ntrial < M3D_NEWTON_MAX_TRIALS) R.trial_lambdas[R.ntrial++] = lam;
-            if (!o.line_search || fn <= f0 + 1e-4 * lam * slope || lam < 1e-4) break;
+            if (!o.line_search) break;
+            if (!std::isfinite(fn)) {
+                lam_prev = -1.0;
+                lam *= 0.1;
+                continue;
+            }
+            if (fn <= f0 + 1e-4 * lam * slope) break;
             const double lt = lam_prev < 0.0 ? quadratic_backtrack(f0, slope, lam, fn)
                                              : cubic_backtrack(f0, slope, lam, fn, lam_prev, f_prev);
             lam_prev = lam;
             f_prev = fn;
-            lam = std::min(std::max(lt, 0.1 * lam), 0.5 * lam);
+            lam = std::isfinite(lt) ? std::min(std::max(lt, 0.1 * lam), 0.5 * lam) : 0.1 * lam;
+        }
+        if (failed) {
+            R.newton_steps++;
+            R.residuals[std::min(R.newton_steps, M3D_NEWTON_MAX_HIST - 1)] = r;
+            R.lambdas[hs] = 0.0;
+            R.trials[hs] = trials;
+            R.line_search_failed = 1;
+            break;
         }
         std::swap(W.y, W.yn);
         std::swap(W.py, W.pyn);
@@ -654,7 +676,11 @@ m3d_status metos3d_newton_solve(m3d_ctx *c, double *y_io, const double *u, const
     CUDA_OR_FAIL(c, cudaMemcpyAsync(y_io, W.y, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     m3d_status out = R.converged ? M3D_OK : M3D_NOT_CONVERGED;
-    if (!R.converged) fail(c, M3D_NOT_CONVERGED, "Newton stopped at residual %.3e after %d steps", r, R.newton_steps);
+    if (R.line_search_failed)
+        fail(c, M3D_NOT_CONVERGED, "Newton stopped at residual %.3e: the line search of step %d found no "
+                                   "decrease (step lengths down to 1e-4)", r, R.newton_steps);
+    else if (!R.converged)
+        fail(c, M3D_NOT_CONVERGED, "Newton stopped at residual %.3e after %d steps", r, R.newton_steps);
     return finish(out);
 }
 

@@ -311,3 +311,40 @@ def test_ensemble_newton_every_member_periodic(m3d, jv):
     ens.close()
     if tan:
         tan.close()
+
+
+def test_ensemble_newton_line_search_through_trials_that_overflow(m3d):
+    """Two NPZD-DOP members in lockstep (phytoplankton x 10 and x 1 from the constant start,
+    three Krylov iterations per step, tangent products): full steps of both overflow the year
+    map and are cut to a tenth, each member on its own trials.  Every member's trials,
+    residuals and state match the oracle's Newton of that member alone."""
+    from oracle import newton as on
+    p, P = problem("tiny_6x4x4")
+    u = np.asarray(mi.default_params(mi.MODEL_NPZD), dtype=np.float64)
+    members = [mi.Member(mi.MODEL_NPZD, u), mi.Member(mi.MODEL_NPZD, u)]
+    ens = m3d.Ensemble.from_problem(p, members)
+    tan = m3d.Ensemble.from_problem(p, members, tangent=True)
+    base = mi.initial_state(p, 5, mi.model_initial_values(mi.MODEL_NPZD))
+    ys = [base * np.array((1.0, sp, 1.0, 1.0, 1.0))[:, None] for sp in (10.0, 1.0)]
+    Y = stack(ys)
+    st, reps = ens.newton_solve(Y, p.vol, tangent_ensemble=tan, tol=1e-8, jv=m3d.JV_TANGENT, max_newton=4,
+                                restart=3, max_krylov=3)
+    assert st == m3d.M3D_NOT_CONVERGED
+    got = split(ens, Y)
+
+    def tangent(yy, py, v):
+        return oracle.year_tangent(P, yy, v, u, model=mi.MODEL_NPZD)[1]
+
+    for m in range(2):
+        want, orep = on.newton_krylov(P, ys[m], u, tol=1e-8, max_newton=4, restart=3, max_krylov=3,
+                                      model=mi.MODEL_NPZD, jv=tangent)
+        assert orep["trials"][0][:2] == [1.0, 0.1], orep["trials"]     # the full step overflowed
+        assert not reps[m]["line_search_failed"]
+        assert reps[m]["krylov"] == orep["krylov"], m
+        assert [len(t) for t in reps[m]["trials"]] == [len(t) for t in orep["trials"]], m
+        for k in range(len(orep["trials"])):
+            assert np.allclose(reps[m]["trials"][k], orep["trials"][k], rtol=1e-6, atol=0), (m, k)
+        assert np.allclose(reps[m]["residuals"], orep["residuals"], rtol=1e-5, atol=0), m
+        assert np.isfinite(got[m]).all() and np.abs(got[m] - want).max() / np.abs(want).max() < 1e-5, m
+    ens.close()
+    tan.close()

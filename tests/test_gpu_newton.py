@@ -118,6 +118,50 @@ def test_newton_backtracking_matches_oracle_step_by_step(m3d):
     ctx.close()
 
 
+def npzd_far_start(p, scale_p):
+    """NPZD-DOP's constant start with the phytoplankton scaled: full Newton steps from it leave
+    the model's domain (negative zooplankton under quadratic mortality overflows within the year)."""
+    return mi.initial_state(p, 5, mi.model_initial_values(mi.MODEL_NPZD)) * \
+        np.array((1.0, scale_p, 1.0, 1.0, 1.0))[:, None]
+
+
+def oracle_npzd_newton(P, y0, u, steps, krylov):
+    def tan(yy, py, v):
+        return oracle.year_tangent(P, yy, v, u, model=mi.MODEL_NPZD)[1]
+    return on.newton_krylov(P, y0, u, tol=1e-8, max_newton=steps, restart=krylov, max_krylov=krylov,
+                            model=mi.MODEL_NPZD, jv=tan, record_steps=True)
+
+
+def test_newton_line_search_through_trials_that_overflow(m3d):
+    """NPZD-DOP (phytoplankton x 10, three Krylov iterations per step, tangent products): the
+    full step of the first Newton step and its tenth both overflow the year map, the third
+    trial decreases |F|; the third step's full step overflows again.  The GPU solve takes the
+    oracle's trials (a non-finite trial is cut to a tenth and gives no model), the same
+    residuals, and ends on a finite state."""
+    p = mi.make_problem("tiny_6x4x4")
+    P = oracle.Problem(p)
+    u = np.asarray(mi.default_params(mi.MODEL_NPZD), dtype=np.float64)
+    y0 = npzd_far_start(p, 10.0)
+    want, orep = oracle_npzd_newton(P, y0, u, 4, 3)
+    # the oracle's own trials at lambda = 1 and 0.1 of the first step overflow
+    s0 = orep["steps"][0].reshape(y0.shape)
+    for lam in (1.0, 0.1):
+        assert not np.isfinite(oracle.year_map(P, y0 + lam * s0, u, model=mi.MODEL_NPZD)).all()
+    assert orep["trials"][0] == [1.0, 0.1, 0.010000000000000002] and len(orep["trials"][2]) == 2
+    ctx = m3d.Context.from_problem(p, model=mi.MODEL_NPZD, ntracer=5, nparam=len(u))
+    y = cuda(y0)
+    st, rep = ctx.newton_solve(y, cuda(u), tol=1e-8, max_newton=4, restart=3, max_krylov=3, jv=m3d.JV_TANGENT)
+    assert st == m3d.M3D_NOT_CONVERGED and not rep["line_search_failed"]
+    assert rep["krylov"] == orep["krylov"]
+    assert [len(t) for t in rep["trials"]] == [len(t) for t in orep["trials"]]
+    for k in range(4):
+        assert np.allclose(rep["trials"][k], orep["trials"][k], rtol=1e-6, atol=0), (k, rep["trials"], orep["trials"])
+    assert np.allclose(rep["residuals"], orep["residuals"], rtol=1e-5, atol=0), (rep["residuals"], orep["residuals"])
+    got = y.cpu().numpy()
+    assert np.isfinite(got).all() and np.abs(got - want).max() / np.abs(want).max() < 1e-5
+    ctx.close()
+
+
 def test_newton_fd_backtracks_and_converges(m3d):
     """The same far start with finite-difference products: the line search backtracks and the
     solve reaches the oracle's periodic state."""

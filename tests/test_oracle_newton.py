@@ -173,6 +173,35 @@ def pins_line_search_bounds(m):
     assert trials[1][0] == 0.1 and lam < 0.1
 
 
+def pins_line_search_guards(m):
+    """Trials outside the function's domain (not finite) and a search that finds no decrease."""
+    f0, slope = 1.0, -2.0
+
+    def f(x):                       # not defined beyond 0.5; below it f = 1 - 2x + 40x^2
+        return math.nan if x > 0.5 else f0 + slope * x + 40.0 * x * x
+    lam, fl, trials = m.line_search(f, f0, slope)
+    # the NaN at 1 gives no model: the next trial is 0.1 of it; the failure there starts the
+    # quadratic model afresh, whose minimiser 0.025 (in [0.01, 0.05]) is accepted
+    assert [t[0] for t in trials][:2] == [1.0, 0.1] and math.isnan(trials[0][1]) and len(trials) == 3
+    assert math.isclose(lam, 0.025, rel_tol=1e-12) and fl == f(lam)
+    lam, fl, trials = m.line_search(lambda x: math.inf if x > 0.05 else f0 + slope * x, f0, slope)
+    assert len(trials) == 3 and math.isclose(lam, 0.01, rel_tol=1e-12)
+    # f increases along the direction: every step length down to 1e-4 fails, none below it is
+    # tried, and the search returns no step
+    lam, fl, trials = m.line_search(lambda x: f0 + x, f0, slope)
+    assert lam == 0.0 and fl == f0 and 4 <= len(trials) <= 14
+    assert min(t[0] for t in trials) >= 1e-4 and all(t[1] > f0 for t in trials)
+    # the driver stops at its iterate when the line search fails: phi = 0 with a wrong
+    # derivative (phi' = 2 I) makes the Newton step s = F an ascent direction of |F|
+    y0 = np.array([1.0, -2.0, 0.5])
+    y, rep = m.newton_solve(lambda y: np.zeros_like(y), y0, jv=lambda y, py, v: 2.0 * v)
+    assert rep["line_search_failed"] and not rep["converged"] and np.array_equal(y, y0)
+    assert rep["lambdas"] == [0.0] and rep["residuals"] == [float(np.linalg.norm(y0))] * 2
+    # a start whose residual is not finite takes no step
+    y, rep = m.newton_solve(lambda y: np.full_like(y, math.nan), y0)
+    assert not rep["converged"] and rep["krylov"] == [] and np.array_equal(y, y0)
+
+
 def pins_newton_driver(m):
     """The generic driver on F(y) = atan(A y - b) (componentwise, n = 6) from far away, where
     full Newton steps overshoot: exact Jacobian, every slope equal to F.J s computed directly,
@@ -224,6 +253,10 @@ def test_line_search_bounds_and_armijo_side():
 
 def test_newton_driver_slopes_and_forcing_on_a_small_map():
     pins_newton_driver(on)
+
+
+def test_line_search_outside_the_domain_and_when_it_finds_no_decrease():
+    pins_line_search_guards(on)
 
 
 def test_gmres_mgs_solves_a_small_system():
@@ -330,6 +363,11 @@ NEWTON_MUTANTS = {
     "armijo_sign": ("fl <= f0 + armijo * lam * slope", "fl <= f0 - armijo * lam * slope"),
     "slope_of_exact_newton": ("slope = -(r * r - rho * rho)", "slope = -r * r"),
     "models_swapped": ("if prev is None:\n            lt = quadratic", "if prev is not None:\n            lt = quadratic"),
+    "nonfinite_kept_as_model": ("prev = None\n            lam = lo * lam", "prev = (lam, fl)\n            lam = lo * lam"),
+    "nonfinite_not_caught": ("if not math.isfinite(fl):", "if False:"),
+    "failure_takes_the_last_step": ("return 0.0, f0, trials", "return trials[-1][0], trials[-1][1], trials"),
+    "failure_below_lam_min_tried": ("while lam >= lam_min:", "while lam >= 0.1 * lam_min:"),
+    "failure_not_stopping": ("if lam == 0.0:", "if False:"),
 }
 
 
@@ -350,10 +388,12 @@ def _mutant_module(name, tmp_path):
 def test_newton_pins_catch_mutant(name, tmp_path):
     mod = _mutant_module(name, tmp_path)
     caught = False
-    for pins in (pins_forcing_term, pins_backtracks, pins_line_search, pins_line_search_bounds, pins_newton_driver):
+    for pins in (pins_forcing_term, pins_backtracks, pins_line_search, pins_line_search_bounds,
+                 pins_line_search_guards, pins_newton_driver):
         try:
             pins(mod)
-        except (AssertionError, ValueError, TypeError, ZeroDivisionError, np.linalg.LinAlgError, RuntimeError):
+        except (AssertionError, ValueError, TypeError, ZeroDivisionError, KeyError, np.linalg.LinAlgError,
+                RuntimeError):
             caught = True
             break
     assert caught, "the Newton pins did not catch mutant %s" % name
