@@ -541,20 +541,12 @@ struct AdjointParams {
 //   euphotic: f = alpha' N/(N+K_N) I/(I+K_I), qN = -f + lambda D, qD = sigma f - lambda D
 //   E = (1 - sigma) sum f h;  aphotic: qN = E mfrac + lambda D, qD = -lambda D
 //   shallow column: the bottom layer also gets E / h.
-// SEP: run by nthr threads from tid0 (named barrier `bar` between the passes) while the other
-// threads apply A_j^T, writing the state cotangent's source part into dq (every cell) instead of
-// adding it to z; otherwise run by the whole CTA and added into z.
-template <int NTR, bool SEP = false>
+template <int NTR>
 __device__ __forceinline__ void ndop_source_adjoint_tile(const StepParams &P, const AdjointParams &A, const Tile &T,
                                                          int j, const double *__restrict__ y,
                                                          const double *__restrict__ zbar, const TileSmem &M,
-                                                         double *ub, int nthr = kThreads, int tid0 = 0, int bar = 0)
+                                                         double *ub)
 {
-    const int tid = (int)threadIdx.x - tid0;
-    auto sync = [&]() {
-        if (SEP) barrier_sub(bar);
-        else __syncthreads();
-    };
     const int zmax = P.zmax;
     const double alpha = __ldg(P.qpar + kQAlpha), sigma = __ldg(P.qpar + kQSigma);
     const double lambda = __ldg(P.qpar + kQLambda), KN = __ldg(P.qpar + kQKN);
@@ -565,7 +557,7 @@ __device__ __forceinline__ void ndop_source_adjoint_tile(const StepParams &P, co
     double *ehk = M.ek + zmax;         // [zmax] (1 - sigma) f h of euphotic cells
     double *Ebar = M.aux;              // per column, at its first cell
     // (a) forward production of the euphotic cells
-    for (int e = T.eu0 + tid; e < T.eu1; e += nthr) {
+    for (int e = T.eu0 + (int)threadIdx.x; e < T.eu1; e += blockDim.x) {
         const int i = __ldg(P.eu_list + e);
         const int cell = T.cell0 + i;
         const double I = __ldg(I0row + __ldg(P.cell_ulat + cell)) * __ldg(P.atten + cell);
@@ -574,10 +566,10 @@ __device__ __forceinline__ void ndop_source_adjoint_tile(const StepParams &P, co
         fk[i] = f;
         ehk[i] = oms * f * __ldg(P.h + cell);
     }
-    sync();
+    __syncthreads();
     // (b) per column: the cotangent of its export, and the Martin exponent's gradient
     const int c0 = __ldg(A.col_off + blockIdx.x), c1 = __ldg(A.col_off + blockIdx.x + 1);
-    for (int c = c0 + tid; c < c1; c += nthr) {
+    for (int c = c0 + (int)threadIdx.x; c < c1; c += blockDim.x) {
         const int pc = __ldg(A.col_list + c);
         const int cb = pc & 0xffff, L = pc >> 16;
         const int neu = L < kEuphotic ? L : kEuphotic;
@@ -601,21 +593,16 @@ __device__ __forceinline__ void ndop_source_adjoint_tile(const StepParams &P, co
         ub[6] += bb;
         ub[2] -= eb * sfh;                        // d E / d sigma = -sum f h
     }
-    sync();
+    __syncthreads();
     // (c) every cell: DOP remineralisation; euphotic cells: production
-    for (int i = tid; i < T.ncell; i += nthr) {
+    for (int i = threadIdx.x; i < T.ncell; i += blockDim.x) {
         const int cell = T.cell0 + i;
         const int k = __ldg(P.cell_kl + cell) & 0xff;
         const double qbN = ds * __ldcg(zbar + (size_t)cell * NTR);
         const double qbD = ds * __ldcg(zbar + (size_t)cell * NTR + 1);
         const double D = __ldcg(y + (size_t)cell * NTR + 1);
         const double dl = qbN - qbD;
-        if (SEP) {
-            M.dq[zmax + i] = lambda * dl;         // d q / d DOP
-            M.dq[i] = 0.0;
-        } else {
-            M.z[zmax + i] += lambda * dl;
-        }
+        M.z[zmax + i] += lambda * dl;            // d q / d DOP
         ub[3] += dl * D;                          // d q / d lambda
         if (k < kEuphotic) {
             const double N = __ldcg(y + (size_t)cell * NTR);
@@ -625,7 +612,7 @@ __device__ __forceinline__ void ndop_source_adjoint_tile(const StepParams &P, co
             ub[2] += qbD * f;
             const double NK = N + KN, IK = I + KI;
             const double Mm = N / NK, LF = I / IK;
-            (SEP ? M.dq[i] : M.z[i]) += fb * alpha * LF * (KN / (NK * NK));   // d f / d N
+            M.z[i] += fb * alpha * LF * (KN / (NK * NK));            // d f / d N
             ub[1] += fb * 360.0 * Mm * LF;                            // d f / d alpha (alpha per day)
             ub[4] += fb * alpha * LF * (-N / (NK * NK));              // d f / d K_N
             ub[5] += fb * alpha * Mm * (-I / (IK * IK));              // d f / d K_I
@@ -652,7 +639,6 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
     const Tile T = PT.tiles[tile];
     const ResidentTile RT = RTp.rt[tile];
     const int zmax = PT.zmax;
-    constexpr bool SEP = !STREAM;      // the source term's reverse on its own warps (needs dq)
     // STREAM: the operators are read from global memory where they lie (the month's slices of
     // the tile), only the tile's cotangent and the source term's scratch sit in shared memory,
     // and the implicit part uses the dense form (TRI must be false)
@@ -715,39 +701,17 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
         if (m != exp_month) {
             explicit_month(m);
             exp_month = m;
-            if (SEP) __syncthreads();
         }
-        if (SEP) {
-            // The source term's reverse needs only this tile's own cotangent (written by this CTA
-            // in the previous step) and y_j, so the last kQWarps warps run it at once into dq,
-            // while the explicit group waits for the neighbouring tiles and forms A_j^T zbar_j
-            // (as the forward step overlaps the source term with its explicit part).
-            if ((int)threadIdx.x >= kSpThreads) {
-                ndop_source_adjoint_tile<NTR, true>(PT, A, T, j, y, zb, M, ub, kQThreads, kSpThreads, 2);
-            } else {
-                if (threadIdx.x < 32) {
-                    bool ok = wait_neighbours(S, tile, s + 1, s);
-                    if (threadIdx.x == 0) abort_flag = ok ? 0 : 1;
-                }
-                barrier_sub(3);
-                if (!abort_flag)
-                    spmv_resident<NTR, false>(PT, T, __ldg(PT.wtab + j), zb, M, PT.sp_wlist_g, PT.sp_woff_g,
-                                              kSpThreads / 32, (int)(threadIdx.x >> 5));   // ybar_j = A_j^T zbar_j
-            }
-            __syncthreads();
-            if (abort_flag) { aborted = true; break; }
-        } else {
-            if (threadIdx.x < 32) {
-                bool ok = wait_neighbours(S, tile, s + 1, s);
-                if (threadIdx.x == 0) abort_flag = ok ? 0 : 1;
-            }
-            __syncthreads();
-            if (abort_flag) { aborted = true; break; }
-            spmv_resident<NTR, false>(PT, T, __ldg(PT.wtab + j), zb, M);       // ybar_j = A_j^T zbar_j
-            __syncthreads();
-            ndop_source_adjoint_tile<NTR>(PT, A, T, j, y, zb, M, ub);           // + (d dq/dy)^T zbar_j
-            __syncthreads();
+        if (threadIdx.x < 32) {
+            bool ok = wait_neighbours(S, tile, s + 1, s);
+            if (threadIdx.x == 0) abort_flag = ok ? 0 : 1;
         }
+        __syncthreads();
+        if (abort_flag) { aborted = true; break; }
+        spmv_resident<NTR, false>(PT, T, __ldg(PT.wtab + j), zb, M);       // ybar_j = A_j^T zbar_j
+        __syncthreads();
+        ndop_source_adjoint_tile<NTR>(PT, A, T, j, y, zb, M, ub);           // + (d dq/dy)^T zbar_j
+        __syncthreads();
         if (s + 1 < nsteps) {
             const int jm = (j + PT.nstep - 1) % PT.nstep;
             const int mm = __ldg(PT.m0tab + jm);
@@ -756,11 +720,11 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
                 imp_month = mm;
                 __syncthreads();
             }
-            implicit_resident<NTR, TRI, SEP>(PT, RTp, T, __ldg(PT.wtab + jm), M, zn);   // zbar_{j-1}
+            implicit_resident<NTR, TRI>(PT, RTp, T, __ldg(PT.wtab + jm), M, zn);   // zbar_{j-1}
         } else {
             for (int i = threadIdx.x; i < T.ncell; i += blockDim.x) {
                 double v[NTR];
-                for (int t = 0; t < NTR; t++) v[t] = SEP ? M.z[t * zmax + i] + M.dq[t * zmax + i] : M.z[t * zmax + i];
+                for (int t = 0; t < NTR; t++) v[t] = M.z[t * zmax + i];
                 store_cell<NTR>(out, T.cell0 + i, v);
             }
         }
