@@ -307,18 +307,35 @@ __device__ __forceinline__ void implicit_dense_resident(const StepParams &P, con
 // weights (1 - w)/d_k and w/d_k of every cell; one combining pass then writes
 // (1 - w)/d0_k u0_k + w/d1_k u1_k.  Equal to (B_m0 + w (B_m1 - B_m0)) z up to rounding,
 // because the monthly blocks are the inverses B_m = M_m^{-1}.
+// The tile's chain range and this thread's first chain descriptor: the same every step, so a
+// sweep loads them once (their loads would otherwise start every step's Thomas phase).
+struct ChainPre {
+    int ch0, ch1, pc0;
+};
+
+__device__ __forceinline__ ChainPre chain_pre(const ResidentParams &R)
+{
+    ChainPre C;
+    C.ch0 = __ldg(R.chain_off + blockIdx.x);
+    C.ch1 = __ldg(R.chain_off + blockIdx.x + 1);
+    const int c = C.ch0 + (int)threadIdx.x;
+    C.pc0 = c < C.ch1 ? __ldg(R.chains + c) : 0;
+    return C;
+}
+
 template <int NTR, bool ADD_DQ>
 __device__ __forceinline__ void implicit_tri_resident(const StepParams &P, const ResidentParams &R, const Tile &T,
-                                                      double w, const TileSmem &M, double *__restrict__ yn)
+                                                      double w, const TileSmem &M, double *__restrict__ yn,
+                                                      const ChainPre &CP)
 {
     const int zmax = P.zmax;
-    const int ch0 = __ldg(R.chain_off + blockIdx.x), ch1 = __ldg(R.chain_off + blockIdx.x + 1);
+    const int ch0 = CP.ch0, ch1 = CP.ch1;
     const int nthreads = (int)blockDim.x, tid = (int)threadIdx.x;
     const int chain_threads = min(nthreads, ((ch1 - ch0 + 31) / 32) * 32);
     double *c0 = M.ek, *c1 = M.ek + zmax;     // blend weights (the source term's scratch is free now)
     if (tid < chain_threads) {
         for (int c = ch0 + tid; c < ch1; c += chain_threads) {
-            const int pc = __ldg(R.chains + c);
+            const int pc = c == ch0 + tid ? CP.pc0 : __ldg(R.chains + c);
             const int cb = pc & 0xffff, L = (pc >> 16) & 0x7f, t = (pc >> 23) & 0xf, h = (pc >> 27) & 1;
             const double *nl = M.tl + (3 * h + 0) * zmax + cb;
             const double *ne = M.tl + (3 * h + 2) * zmax + cb;
@@ -381,10 +398,12 @@ __device__ __forceinline__ void implicit_tri_resident(const StepParams &P, const
 
 template <int NTR, bool TRI, bool ADD_DQ = false>
 __device__ __forceinline__ void implicit_resident(const StepParams &P, const ResidentParams &R, const Tile &T,
-                                                  double w, const TileSmem &M, double *__restrict__ yn)
+                                                  double w, const TileSmem &M, double *__restrict__ yn,
+                                                  const ChainPre *CP = nullptr)
 {
     if (TRI) {
-        implicit_tri_resident<NTR, ADD_DQ>(P, R, T, w, M, yn);
+        if (CP) implicit_tri_resident<NTR, ADD_DQ>(P, R, T, w, M, yn, *CP);
+        else implicit_tri_resident<NTR, ADD_DQ>(P, R, T, w, M, yn, chain_pre(R));
     } else {
         if (ADD_DQ) {           // the dense form reads z once per block entry: add the increment first
             const int nc = T.ncell, zmax = P.zmax;
@@ -438,6 +457,8 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
         fetch_operator(0);
     }
     copy_to_shared_int(M.si, P.sp_col + RT.sp_base, RT.sp_n);
+    ChainPre CP{0, 0, 0};
+    if (TRI) CP = chain_pre(R);
     __syncthreads();
     int cur_month = -1;
     for (int s = 0; s < nsteps; s++) {
@@ -509,7 +530,7 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
             return;
         }
         if (stepop && threadIdx.x == copier && s + 1 < nsteps) fetch_operator(s + 1);
-        implicit_resident<NTR, TRI, ModelTraits<MODEL>::has_q>(P, R, T, w, M, yn);
+        implicit_resident<NTR, TRI, ModelTraits<MODEL>::has_q>(P, R, T, w, M, yn, &CP);
         // the CTA barrier orders every thread's stores of y_{j+1} before thread 0's release (a
         // release by a source-term thread instead was measured 7% slower: its fence then delays
         // that group's next source term)
