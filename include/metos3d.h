@@ -276,6 +276,11 @@ m3d_status metos3d_sync(m3d_ctx *ctx);
  *       free device memory at init, else 0.  Setting 1 allocates and computes the array
  *       (synchronous; M3D_ERR_CUDA if the allocation fails, M3D_ERR_UNSUPPORTED without the
  *       resident plan); 0 frees it.  The derivative sweeps use it for their forward parts.
+ *       The first resident reverse sweep (metos3d_year_adjoint, metos3d_periodic_gradient)
+ *       of a context that keeps them also builds the transposed operator of every step,
+ *       A_j^T, the same size again, where it takes at most a quarter of the free device
+ *       memory (else the sweep interpolates in the kernel); it is kept until 0 is set or the
+ *       context is freed.
  *   M3D_OPT_STEP_OPERATOR_BYTES (read only): bytes held by the per-step operators (0 if none).
  *   M3D_OPT_TANGENT_FORM: how metos3d_year_tangent evaluates phi'(y) v.  M3D_TANGENT_DUAL
  *       (default): one sweep of the state and its perturbation together, the source term on

@@ -284,6 +284,8 @@ m3d_status adjoint_segment_stream(m3d_ctx *c, const double *traj, long long len,
 m3d_status adjoint_segment(m3d_ctx *c, bool tri, const double *traj, long long len, const double *ybar_in,
                            double *out, double *zb0, double *zb1, int j0, int ns)
 {
+    m3d_status st = m3d_adjoint_step_operators(c);
+    if (st != M3D_OK) return st;
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.flags, 0, sizeof(int) * c->ntiles, c->stream));
     CUDA_OR_FAIL(c, cudaMemsetAsync(c->S.status, 0, sizeof(int) * 4, c->stream));
     StepParams PT = c->PT;

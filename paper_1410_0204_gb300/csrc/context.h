@@ -63,6 +63,8 @@ struct m3d_ctx {
     double *sp_b = nullptr;             // per-step explicit operators [nstep][slot-lanes] (or null)
     int tri_stream_ok = 0;              // the streaming kernels can apply the Thomas form (<= 2 tracers)
     size_t sp_b_bytes = 0;
+    double *spT_b = nullptr;            // the transposed per-step operators of the reverse sweep (or null)
+    size_t spT_b_bytes = 0;
     size_t adj_smem_stream = 0;
     StepParams PT{};
     m3d::ResidentParams RTadj{};
@@ -130,6 +132,11 @@ m3d_status m3d_year_linear_device(m3d_ctx *c, const double *fn, const double *v,
 // One TMM step j in the caller's layout (the step kernel; parameters already in c->u_dev and
 // the per-call tables made).
 m3d_status m3d_step_device(m3d_ctx *c, int j, const double *y, double *yn);
+// Builds the reverse sweep's per-step transposed explicit operators (A_j^T for every step j,
+// in the transposed slices' layout) the first time a resident reverse sweep runs, where the
+// context keeps forward per-step operators and the device has room for a second array.
+// Synchronous.  Leaves them absent (the sweep then interpolates in the kernel) otherwise.
+m3d_status m3d_adjoint_step_operators(m3d_ctx *c);
 // An ensemble-backed context (N, PO4-DOP-PHY, NPZD-DOP): hand the parameters in c->u_dev to its
 // one-member ensemble (synchronous; nothing to do when they did not change).
 m3d_status m3d_ens_sync_params(m3d_ctx *c);

@@ -296,6 +296,8 @@ void release(m3d_ctx *c)
     if (c->year_graph) cudaGraphExecDestroy(c->year_graph);
     if (c->sp_b) cudaFree(c->sp_b);
     c->sp_b = nullptr;
+    if (c->spT_b) cudaFree(c->spT_b);
+    c->spT_b = nullptr;
     for (void *p : c->allocs) cudaFree(p);
     if (c->red_host) cudaFreeHost(c->red_host);
     if (c->status_host) cudaFreeHost(c->status_host);
@@ -307,13 +309,12 @@ void release(m3d_ctx *c)
 m3d_status set_step_operators(m3d_ctx *c, bool on)
 {
     if (!on) {
-        if (c->sp_b) {
-            CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
-            CUDA_OR_FAIL(c, cudaFree(c->sp_b));
-        }
-        c->sp_b = nullptr;
-        c->sp_b_bytes = 0;
-        c->R.sp_b = c->R_tan.sp_b = nullptr;
+        if (c->sp_b || c->spT_b) CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+        if (c->sp_b) CUDA_OR_FAIL(c, cudaFree(c->sp_b));
+        if (c->spT_b) CUDA_OR_FAIL(c, cudaFree(c->spT_b));
+        c->sp_b = c->spT_b = nullptr;
+        c->sp_b_bytes = c->spT_b_bytes = 0;
+        c->R.sp_b = c->R_tan.sp_b = c->RTadj.sp_b = nullptr;
         return M3D_OK;
     }
     if (c->sp_b) return M3D_OK;
@@ -338,6 +339,39 @@ m3d_status set_step_operators(m3d_ctx *c, bool on)
     c->R.sp_bstride = c->R_tan.sp_bstride = spn;
     return M3D_OK;
 }
+
+}  // namespace
+
+m3d_status m3d_adjoint_step_operators(m3d_ctx *c)
+{
+    if (!c->sp_b || c->spT_b || !c->adj_ok) return M3D_OK;
+    const long long spn = c->P.sp_mstride;
+    const size_t bytes = sizeof(double) * (size_t)spn * (size_t)c->nstep;
+    size_t free_b = 0, total_b = 0;
+    CUDA_OR_FAIL(c, cudaMemGetInfo(&free_b, &total_b));
+    if (bytes > free_b / 4) return M3D_OK;          // keep room for the sweep's trajectory
+    double *buf = nullptr;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return M3D_OK;
+    }
+    const int bx = (int)std::min<long long>((spn + 255) / 256, 64);
+    k_step_operators<<<dim3(bx, c->nstep), 256, 0, c->stream>>>(spn, c->PT.sp_a, c->PT.sp_d, c->P.m0tab, c->P.wtab,
+                                                                buf);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        return fail(c, M3D_ERR_CUDA, "transposed per-step operators: %s", cudaGetErrorString(e));
+    }
+    c->spT_b = buf;
+    c->spT_b_bytes = bytes;
+    c->RTadj.sp_b = buf;
+    c->RTadj.sp_bstride = spn;
+    return M3D_OK;
+}
+
+namespace {
 
 bool all_finite(const double *p, size_t count)
 {

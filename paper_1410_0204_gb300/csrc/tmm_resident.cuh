@@ -656,6 +656,7 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ int abort_flag;
     __shared__ double red[kThreads / 32][7];
+    __shared__ __align__(8) unsigned long long opbar[2];
     const int tile = blockIdx.x;
     const Tile T = PT.tiles[tile];
     const ResidentTile RT = RTp.rt[tile];
@@ -699,6 +700,25 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
         }
     };
     int exp_month = -1, imp_month = -1;
+    // With per-step transposed operators (RTp.sp_b): the explicit arrays become a double
+    // buffer, step s (j = j0 + nsteps - 1 - s) reads buffer s mod 2, and once every thread is
+    // past step s's explicit part a bulk copy brings step s+1's values into the other buffer,
+    // step s+2's being prefetched into L2 meanwhile (as in the forward sweep).
+    const bool stepop = !STREAM && RTp.sp_b != nullptr && nsteps > 0;
+    const unsigned opbytes = (unsigned)RT.sp_n * 8u;
+    auto op_src = [&](int s) {
+        return RTp.sp_b + (long long)((j0 + nsteps - 1 - s) % PT.nstep) * RTp.sp_bstride + RT.sp_base;
+    };
+    auto fetch_operator = [&](int s) {
+        bulk_copy_to_shared((s & 1) ? M.sd : M.sa, op_src(s), opbytes, &opbar[s & 1]);
+        if (s + 1 < nsteps) prefetch_l2(op_src(s + 1), opbytes);
+    };
+    if (stepop && threadIdx.x == 0) {
+        mbar_init(&opbar[0], 1);
+        mbar_init(&opbar[1], 1);
+        mbar_init_fence();
+        fetch_operator(0);
+    }
     // zbar_{last} = B_last^T ybar_in on the tile's own cells
     {
         const int j = (j0 + nsteps - 1) % PT.nstep;
@@ -719,7 +739,7 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
         double *zn = (s & 1) ? zb0 : zb1;
         const double *y = traj + (long long)(nsteps - 1 - s) * stride;
         const int m = __ldg(PT.m0tab + j);
-        if (m != exp_month) {
+        if (!stepop && m != exp_month) {
             explicit_month(m);
             exp_month = m;
         }
@@ -728,9 +748,38 @@ __device__ __forceinline__ void year_adjoint_resident(const StepParams &PT, cons
             if (threadIdx.x == 0) abort_flag = ok ? 0 : 1;
         }
         __syncthreads();
-        if (abort_flag) { aborted = true; break; }
-        spmv_resident<NTR, false>(PT, T, __ldg(PT.wtab + j), zb, M);       // ybar_j = A_j^T zbar_j
-        __syncthreads();
+        if (abort_flag) {
+            // step s's copy may be in flight; it depends on no other tile (status[3] if the bound
+            // runs out anyway)
+            if (stepop && threadIdx.x == 0 && !mbar_wait_bounded(&opbar[s & 1], (s >> 1) & 1, S.timeout_ns))
+                atomicExch(S.status + 3, 1);
+            aborted = true;
+            break;
+        }
+        if (stepop) {
+            // every reader observes the completed copy itself
+            if (mbar_wait_bounded(&opbar[s & 1], (s >> 1) & 1, S.timeout_ns)) {
+                spmv_resident<NTR, false, true>(PT, T, 0.0, zb, M, PT.sp_wlist, PT.sp_woff, (int)(blockDim.x >> 5),
+                                                (int)(threadIdx.x >> 5), (s & 1) * RTp.sp_max);   // A_j^T zbar_j
+            } else {
+                if (atomicCAS(S.status, 0, 1) == 0) {
+                    S.status[1] = tile;
+                    S.status[2] = s;
+                }
+                abort_flag = 1;
+            }
+            __syncthreads();
+            if (abort_flag) {
+                if (threadIdx.x == 0 && !mbar_wait_bounded(&opbar[s & 1], (s >> 1) & 1, S.timeout_ns))
+                    atomicExch(S.status + 3, 1);
+                aborted = true;
+                break;
+            }
+            if (threadIdx.x == kThreads - 32 && s + 1 < nsteps) fetch_operator(s + 1);
+        } else {
+            spmv_resident<NTR, false>(PT, T, __ldg(PT.wtab + j), zb, M);   // ybar_j = A_j^T zbar_j
+            __syncthreads();
+        }
         ndop_source_adjoint_tile<NTR>(PT, A, T, j, y, zb, M, ub);           // + (d dq/dy)^T zbar_j
         __syncthreads();
         if (s + 1 < nsteps) {
