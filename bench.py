@@ -58,9 +58,9 @@ def peaks():
 # (3,115,008,000). The traffic is the step operators read once plus a few tens of MB, so
 # it grows with the step-operator bytes, and is scaled to this workload's
 # 16,793,763,840 by that ratio.
-YEAR_KERNEL_REVISION = "chains-add-dq"
+YEAR_KERNEL_REVISION = "chain-descriptors-once"
 TRAFFIC_PER_LAUNCH = {
-    ("resident", True, True, "chains-add-dq"): (
+    ("resident", True, True, "chain-descriptors-once"): (
         round(16793763840 * (3125096000 + 8253184) / 3115008000),
         "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 64x32x8 grid, "
         "scaled by the step-operator bytes (16.79 GB here vs 3.12 GB there)"),

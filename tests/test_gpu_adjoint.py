@@ -223,3 +223,37 @@ def test_streaming_adjoint_matches_oracle(m3d, name):
     assert rel(ybar0.cpu().numpy(), ybar_r.cpu().numpy()) < 1e-11
     assert np.abs(ubar - ubar_r).max() <= 1e-10 * np.abs(ubar_r).max()
     ctx.close()
+
+
+def test_reverse_sweep_step_operators_bit_identical_and_abort(m3d):
+    """The reverse sweep streaming per-step transposed operators gives the bits of the sweep
+    that interpolates every entry in the kernel (both checkpoint intervals); a withheld tile
+    makes it time out (its bulk copies in flight land first) and the context works on."""
+    p = mi.make_problem("ndop_64x32x8")
+    u = cuda(mi.default_params_ndop())
+    y0 = cuda(mi.random_state(p))
+    wbar = cuda(mi.random_state(p, seed=8) - 1.0)
+    ctx = m3d.Context.from_problem(p)
+    assert ctx.get_option(m3d.OPT_STEP_OPERATORS) == 1
+    got = {}
+    for stepop in (1, 0):
+        ctx.set_option(m3d.OPT_STEP_OPERATORS, stepop)
+        for ckpt in (240, p.nstep):
+            yb = torch.empty_like(y0)
+            ub = ctx.year_adjoint(y0, u, wbar, yb, ckpt)
+            got[(stepop, ckpt)] = (yb.cpu().numpy(), ub)
+    for ckpt in (240, p.nstep):
+        assert np.array_equal(got[(1, ckpt)][0], got[(0, ckpt)][0]), ckpt
+        assert np.array_equal(got[(1, ckpt)][1], got[(0, ckpt)][1]), ckpt
+    ctx.set_option(m3d.OPT_STEP_OPERATORS, 1)
+    ctx.set_option(m3d.OPT_WAIT_TIMEOUT_NS, 50_000_000)      # 50 ms
+    ctx.set_option(m3d.OPT_TEST_WITHHOLD_TILE, 0)
+    with pytest.raises(m3d.Metos3dError) as e:
+        ctx.year_adjoint(y0, u, wbar, torch.empty_like(y0), 240)
+    assert e.value.status == m3d.M3D_ERR_TIMEOUT
+    ctx.set_option(m3d.OPT_TEST_WITHHOLD_TILE, -1)
+    ctx.set_option(m3d.OPT_WAIT_TIMEOUT_NS, 2_000_000_000)
+    yb = torch.empty_like(y0)
+    ub = ctx.year_adjoint(y0, u, wbar, yb, 240)
+    assert np.array_equal(yb.cpu().numpy(), got[(1, 240)][0]) and np.array_equal(ub, got[(1, 240)][1])
+    ctx.close()
