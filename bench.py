@@ -58,7 +58,7 @@ def peaks():
 # (3,115,008,000). The traffic is the step operators read once plus a few tens of MB, so
 # it grows with the step-operator bytes, and is scaled to this workload's
 # 16,793,763,840 by that ratio.
-YEAR_KERNEL_REVISION = "chain-descriptors-once"
+YEAR_KERNEL_REVISION = "per-warp-release"
 TRAFFIC_PER_LAUNCH = {
     ("resident", True, True, "chain-descriptors-once"): (
         round(16793763840 * (3127285000 + 4130304) / 3115008000),

@@ -637,6 +637,13 @@ __device__ __forceinline__ void store_release(int *p, int v)
     asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
+// Release-ordered add (gpu scope): the calling thread's earlier writes, and those ordered before
+// them by a barrier it took part in, are visible to whoever acquires the new value.
+__device__ __forceinline__ void add_release(int *p, int v)
+{
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
 // Warp 0 waits for the neighbours of `tile` to reach `target`; returns false on abort.
 __device__ __forceinline__ bool wait_neighbours(const SyncParams &S, int tile, int target, int step)
 {

@@ -417,6 +417,8 @@ __device__ __forceinline__ void implicit_resident(const StepParams &P, const Res
     }
 }
 
+constexpr int kWarpsPerTile = kThreads / 32;   // releases per tile and step of the resident year kernel
+
 // The year (or nsteps steps from step j0) with the tiles' months resident in shared memory.
 // State of step s (interleaved): base + (s mod period) * stride; period 2 is a ping-pong,
 // period nsteps + 1 keeps every state (the trajectory an adjoint sweep reads back).
@@ -491,7 +493,7 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
         } else {
             if (s > 0 || stepop) {
                 if (threadIdx.x < 32) {
-                    bool ok = s > 0 ? wait_neighbours(S, tile, s, s) : true;
+                    bool ok = s > 0 ? wait_neighbours(S, tile, kWarpsPerTile * s, s) : true;
                     if (ok && stepop && !mbar_wait_bounded(&opbar[s & 1], (s >> 1) & 1, S.timeout_ns)) {
                         if (atomicCAS(S.status, 0, 1) == 0) {
                             S.status[1] = tile;
@@ -531,11 +533,13 @@ __device__ __forceinline__ void year_resident(const StepParams &P, const Residen
         }
         if (stepop && threadIdx.x == copier && s + 1 < nsteps) fetch_operator(s + 1);
         implicit_resident<NTR, TRI, ModelTraits<MODEL>::has_q>(P, R, T, w, M, yn, &CP);
-        // the CTA barrier orders every thread's stores of y_{j+1} before thread 0's release (a
-        // release by a source-term thread instead was measured 7% slower: its fence then delays
-        // that group's next source term)
+        // Every warp publishes its own stores of y_{j+1} as soon as they are made: the tile's
+        // counter gains one per warp, and the neighbours wait for kWarpsPerTile (s + 1).  No
+        // CTA barrier stands before the release, and each warp's fence waits only for its own
+        // stores.  The barrier after it keeps the tile's own next step behind all of them.
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0 && tile != S.withhold_tile) add_release(S.flags + tile, 1);
         __syncthreads();
-        if (threadIdx.x == 0 && tile != S.withhold_tile) store_release(S.flags + tile, s + 1);
     }
 }
 
