@@ -404,8 +404,8 @@ m3d_status metos3d_newton_solve(m3d_ctx *ctx, double *y, const double *u, const 
  * ystar: device [ntracer][n], the periodic solution (e.g. from metos3d_newton_solve);
  * u: device [nparam]; g: device [ntracer][n]; lambda: device [ntracer][n] output (may be
  * NULL); ubar_host: host [nparam] output, (d ys / d u)^T g.  opts NULL for the defaults
- * (metos3d_gradient_default_options); report may be NULL.  PO4-DOP only, as
- * metos3d_year_adjoint.  Returns M3D_NOT_CONVERGED (results and report filled in) if the
+ * (metos3d_gradient_default_options); report may be NULL.  PO4-DOP contexts only (it drives their
+ * tiled reverse sweep; other models give M3D_ERR_UNSUPPORTED).  Returns M3D_NOT_CONVERGED (results and report filled in) if the
  * relative residual tolerance is not met within max_krylov iterations.  Synchronous;
  * allocates the Krylov basis ((restart + 11) state vectors) and the adjoint's trajectory
  * ((ckpt_every + 1) states; the default keeps the whole year, 2.4 GB for 52,749 cells and two
