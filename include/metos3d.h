@@ -211,8 +211,10 @@ m3d_status metos3d_bgc(int model_id, double t, double dt, double lat, double ins
  * || a - b ||_2 over len doubles (device arrays a, b), written to the device double
  * *norm_dev, without allocating anything.  The paper has no counterpart: this is the
  * metos3d_residual reduction for callers that cannot call cudaMalloc when they need the
- * norm (for example while a stream is being captured into a CUDA graph, or when another
- * allocator owns all device memory), and it needs no context.
+ * norm: a process whose device memory is all handed out by another allocator with a
+ * fixed budget (a framework's caching pool, a host application that sized its pools at
+ * start-up) has none left to give, and a caller without a library context has no
+ * context-owned scratch to lend.  It needs no context.
  * Its per-block partial sums live in one static device array of
  * M3D_RESIDUAL_STATIC_MAX_BLOCKS doubles (512 KiB), which every GPU that loads the
  * library keeps until the process exits; len may be at most

@@ -1,11 +1,11 @@
 // residual_static.cu -- || a - b ||_2 without any device allocation.
 //
 // The same quantity as metos3d_residual (the residual norm the spin-up and the Newton
-// solver report), for callers that cannot allocate device memory at call time: code that
-// runs while a stream is being captured into a CUDA graph (cudaMalloc is not allowed
-// there), processes whose device memory is owned by another allocator with a fixed
-// budget, and tools that must not create a library context.  The per-block partial sums
-// live in one file-scope device array of fixed size instead of in allocated scratch.
+// solver report), for callers that cannot allocate device memory at call time: processes
+// whose device memory is all owned by another allocator with a fixed budget, and callers
+// that hold no library context (the other reductions use scratch a context allocated).
+// The per-block partial sums live in one file-scope device array of fixed size instead of
+// in allocated scratch.
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -1,8 +1,9 @@
 """The allocation-free residual entry point, metos3d_residual_static.
 
 Some callers cannot allocate device memory at the moment they need the residual norm
-|| a - b ||_2: code running while a stream is captured into a CUDA graph (cudaMalloc is
-forbidden there), or a process whose device memory is all owned by another allocator.
+|| a - b ||_2: a process whose device memory is all owned by another allocator with a
+fixed budget has none to spare, and a caller without a library context has no
+context-owned scratch to use.
 metos3d_residual_static keeps its partial sums in a static device array instead.  Here it
 is called through the C ABI and compared with the context-based metos3d_residual, within
 the tolerance the other reduction tests use, on two calls in a row (the second call must
