@@ -45,6 +45,28 @@ MUTANTS = {
 }
 
 
+def _run_pins(source_text, tmp_path):
+    """Build `source_text` as the oracle library and run the forward pins against it."""
+    mutated = tmp_path / "tmm_oracle_mut.c"
+    mutated.write_text(source_text)
+    lib = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                           "-o", str(lib), str(mutated), "-lm"])
+    env = dict(os.environ, M3D_ORACLE_LIB=str(lib), M3D_ORACLE_THREADS="1",
+               OMP_NUM_THREADS="1", OMP_WAIT_POLICY="passive")
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                           os.path.join(ROOT, "tests", "test_oracle_models.py")],
+                          env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+
+
+@pytest.mark.slow
+def test_unmutated_copy_passes_the_pins(tmp_path):
+    """The control: the oracle's own source, built and loaded as the mutants are, passes."""
+    r = _run_pins(open(SRC).read(), tmp_path)
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_mutant(name, tmp_path):
@@ -52,15 +74,5 @@ def test_pins_catch_mutant(name, tmp_path):
     text = open(SRC).read()
     assert old in text, "mutation site not found: %s" % name
     # the first occurrence is in the forward model (its tangent and adjoint follow later)
-    mutated = tmp_path / "tmm_oracle_mut.c"
-    mutated.write_text(text.replace(old, new, 1))
-    lib = tmp_path / "liboracle_mut.so"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-                           "-o", str(lib), str(mutated), "-lm"])
-    env = dict(os.environ, M3D_ORACLE_LIB=str(lib), M3D_ORACLE_THREADS="1",
-               OMP_NUM_THREADS="1", OMP_WAIT_POLICY="passive")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_models.py")],
-                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    r = _run_pins(text.replace(old, new, 1), tmp_path)
     assert r.returncode != 0, "the pins did not catch mutant %s:\n%s" % (name, r.stdout[-2000:])

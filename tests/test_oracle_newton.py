@@ -372,16 +372,27 @@ NEWTON_MUTANTS = {
 
 
 def _mutant_module(name, tmp_path):
-    old, new = NEWTON_MUTANTS[name]
     src = open(os.path.join(ROOT, "oracle", "newton.py")).read()
-    assert src.count(old) >= 1, "mutation site not found: %s" % name
+    if name is not None:
+        old, new = NEWTON_MUTANTS[name]
+        assert src.count(old) >= 1, "mutation site not found: %s" % name
+        src = src.replace(old, new, 1)
+    name = name or "unmutated"
     path = tmp_path / ("newton_%s.py" % name)
-    path.write_text(src.replace(old, new, 1).replace("from . import MODEL_NDOP, year_map",
-                                                     "from oracle import MODEL_NDOP, year_map"))
+    path.write_text(src.replace("from . import MODEL_NDOP, year_map", "from oracle import MODEL_NDOP, year_map"))
     spec = importlib.util.spec_from_file_location("newton_mutant_" + name, str(path))
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     return mod
+
+
+def test_unmutated_copy_passes_the_newton_pins(tmp_path):
+    """The control: the solver's own source, copied and loaded as the mutants are, passes
+    every pin, so a mutant fails because of its mistake and not because of the copy."""
+    mod = _mutant_module(None, tmp_path)
+    for pins in (pins_forcing_term, pins_backtracks, pins_line_search, pins_line_search_bounds,
+                 pins_line_search_guards, pins_newton_driver):
+        pins(mod)
 
 
 @pytest.mark.parametrize("name", sorted(NEWTON_MUTANTS))
