@@ -69,3 +69,61 @@ def test_single_context_model_counts_are_checked_without_gpu_work(lib):
     with pytest.raises(m3d.Metos3dError) as ei:
         m3d.Context.from_problem(p, model=4, ntracer=4, nparam=4, stream=fake_stream)
     assert ei.value.status == m3d.M3D_ERR_UNSUPPORTED
+
+
+def test_every_entry_point_rejects_a_null_handle_without_gpu_work(lib):
+    """Each call that takes a context or an ensemble returns M3D_ERR_ARG (or its documented
+    sentinel) for a NULL handle, before any device work, and leaves a message behind."""
+    L = ctypes.CDLL(b.LIB)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    N = None
+    calls = {
+        "metos3d_set_stream": (N, N),
+        "metos3d_step": (N, i(0), N, N, N),
+        "metos3d_year_map": (N, N, N, N),
+        "metos3d_year_map_host": (N, N, N, N),
+        "metos3d_year_tangent": (N, N, N, N, N, N),
+        "metos3d_year_adjoint": (N, N, N, N, N, N, i(240)),
+        "metos3d_mass": (N, N, N),
+        "metos3d_residual": (N, N, N, N),
+        "metos3d_check_finite": (N, N),
+        "metos3d_sync": (N,),
+        "metos3d_set_option": (N, i(0), ll(0)),
+        "metos3d_spinup": (N, N, N, i(1), d(0.0), N, N),
+        "metos3d_newton_solve": (N, N, N, N, N),
+        "metos3d_periodic_gradient": (N, N, N, N, N, N, N, N),
+        "metos3d_info": (N, N, N, N, N),
+        "metos3d_ensemble_layout": (N, N, N, N, N, N),
+        "metos3d_ensemble_set_stream": (N, N),
+        "metos3d_ensemble_set_params": (N, i(0), N),
+        "metos3d_ensemble_steps": (N, i(0), i(1), N, N),
+        "metos3d_ensemble_year_map": (N, N, N),
+        "metos3d_ensemble_set_tiling": (N, i(1), i(4)),
+        "metos3d_ensemble_get_tiling": (N, N, N),
+        "metos3d_ensemble_autotune": (N, N, i(1), N, N, N),
+        "metos3d_ensemble_year_adjoint": (N, N, N, N, N, i(240)),
+        "metos3d_ensemble_newton_solve": (N, N, N, N, N, N),
+    }
+    assert set(calls) | {"metos3d_init", "metos3d_ensemble_init", "metos3d_ensemble_init_tangent", "metos3d_bgc",
+                         "metos3d_residual_static", "metos3d_residual_static_error", "metos3d_get_option",
+                         "metos3d_newton_default_options", "metos3d_gradient_default_options",
+                         "metos3d_ensemble_last_launch_count", "metos3d_ensemble_last_error",
+                         "metos3d_ensemble_free", "metos3d_last_launch_count", "metos3d_last_error",
+                         "metos3d_free"} == set(m3d.declared_symbols())
+    for name, args in calls.items():
+        f = getattr(L, name)
+        f.restype = ctypes.c_int
+        assert f(*args) == m3d.M3D_ERR_ARG, name
+    for name in ("metos3d_get_option",):
+        f = getattr(L, name)
+        f.restype = ll
+        assert f(N, i(0)) == -1
+    for name in ("metos3d_last_launch_count", "metos3d_ensemble_last_launch_count"):
+        f = getattr(L, name)
+        f.restype = ll
+        assert f(N) == -1, name
+    L.metos3d_last_error.restype = ctypes.c_char_p
+    L.metos3d_ensemble_last_error.restype = ctypes.c_char_p
+    assert L.metos3d_last_error(N) is not None and L.metos3d_ensemble_last_error(N) is not None
+    L.metos3d_free(N)
+    L.metos3d_ensemble_free(N)
