@@ -127,3 +127,31 @@ def test_every_entry_point_rejects_a_null_handle_without_gpu_work(lib):
     assert L.metos3d_last_error(N) is not None and L.metos3d_ensemble_last_error(N) is not None
     L.metos3d_free(N)
     L.metos3d_ensemble_free(N)
+
+
+def test_bgc_interface_checks_its_arguments_without_gpu_work(lib):
+    """The model interface of Section 5.2 rejects bad sizes and arrays before it touches the
+    device: no layers, too many layers, no internal step, the wrong tracer or parameter count
+    for PO4-DOP, a missing array; an unknown model is unsupported."""
+    L = m3d.load()
+    h = np.array([50.0, 70.0, 90.0])
+    d = np.cumsum(h) - 0.5 * h
+    y = np.full(6, 2.0)
+    out = np.zeros(6)
+    u = np.ones(7)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+
+    def call(model=m3d.MODEL_NDOP, ntr=2, nl=3, nparam=7, nsub=1, hh=h, uu=u):
+        return L.metos3d_bgc(model, 0.0, 1.0 / 2880, 0.0, 300.0, 0.5, 0.0, 0.0, ntr, nl,
+                             dp(hh) if hh is not None else None, dp(d), None, None, dp(y), dp(out),
+                             nparam, dp(uu) if uu is not None else None, nsub)
+
+    assert call(nl=0) == m3d.M3D_ERR_ARG
+    assert call(nl=100000) == m3d.M3D_ERR_ARG
+    assert call(nsub=0) == m3d.M3D_ERR_ARG
+    assert call(ntr=3) == m3d.M3D_ERR_ARG
+    assert call(nparam=6) == m3d.M3D_ERR_ARG
+    assert call(hh=None) == m3d.M3D_ERR_ARG
+    assert call(uu=None) == m3d.M3D_ERR_ARG
+    assert call(model=4) == m3d.M3D_ERR_UNSUPPORTED
+    assert np.all(out == 0.0)
