@@ -615,6 +615,8 @@ m3d_status m3d_validate_inputs(const m3d_grid *g, const m3d_matrices *mt, std::s
     if (rp[0] != 0 || rp[g->n] != mt->nnz) return bad("%s", "matrices: rowptr must run from 0 to nnz");
     for (int i = 0; i < g->n; i++) {
         if (rp[i + 1] < rp[i]) return bad("matrices: rowptr decreases at row %d", i);
+        // checked before the row's indices are read: an entry beyond nnz would read past them
+        if (rp[i + 1] > mt->nnz) return bad("matrices: rowptr exceeds nnz at row %d", i);
         for (int p = rp[i]; p < rp[i + 1]; p++) {
             if (ci[p] < 0 || ci[p] >= g->n) return bad("matrices: column index out of range in row %d", i);
             if (p > rp[i] && ci[p] <= ci[p - 1]) return bad("matrices: row %d is not sorted or has duplicates", i);

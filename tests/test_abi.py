@@ -155,3 +155,56 @@ def test_bgc_interface_checks_its_arguments_without_gpu_work(lib):
     assert call(uu=None) == m3d.M3D_ERR_ARG
     assert call(model=4) == m3d.M3D_ERR_UNSUPPORTED
     assert np.all(out == 0.0)
+
+
+def test_init_validates_every_input_rule_without_gpu_work(lib):
+    """metos3d_init checks the grid and the matrices on the host before it allocates or
+    launches anything (the problem statement of Section 3): each malformed input below is
+    rejected with M3D_ERR_ARG and a message naming the rule, never read out of bounds."""
+    import types
+    import m3d_inputs as mi
+    p = mi.make_problem("ndop_64x32x8")
+    fake_stream = types.SimpleNamespace(cuda_stream=0)
+    base = dict(col_start=p.col_start, h=p.h, zc=p.zc, vol=p.vol, lat=p.lat, exp_rowptr=p.exp_rowptr,
+                exp_colidx=p.exp_colidx, exp_val=p.exp_val, imp_blk=p.imp_blk)
+    rp, ci = np.asarray(p.exp_rowptr), np.asarray(p.exp_colidx)
+    r = int(np.argmax(np.diff(rp) >= 3))                 # a row with at least three entries
+    a = int(rp[r])
+
+    def changed(key, edit):
+        arr = np.array(base[key], copy=True)
+        edit(arr)
+        return dict(base, **{key: arr})
+
+    def shift(k):
+        def edit(cs):
+            cs[1] = k
+        return edit
+
+    cases = {
+        "col_start must run from 0 to n": changed("col_start", lambda cs: cs.__setitem__(0, 1)),
+        "layers (1..": changed("col_start", shift(0)),              # column 0 without layers
+        "latitude": changed("lat", lambda x: x.__setitem__(3, 91.0)),
+        "bad h, zc or vol": changed("h", lambda x: x.__setitem__(7, 0.0)),
+        "bad h, zc or vol ": changed("zc", lambda x: x.__setitem__(7, np.inf)),
+        "bad h, zc or vol  ": changed("vol", lambda x: x.__setitem__(7, np.nan)),
+        "s_imp": dict(base, imp_blk=np.ascontiguousarray(np.asarray(p.imp_blk)[:, :-1])),
+        "rowptr must run from 0 to nnz": changed("exp_rowptr", lambda x: x.__setitem__(0, 1)),
+        "rowptr decreases": changed("exp_rowptr", lambda x: x.__setitem__(r + 1, x[r] - 1)),
+        "rowptr exceeds nnz": changed("exp_rowptr", lambda x: x.__setitem__(1, p.nnz + 100000)),
+        "column index out of range": changed("exp_colidx", lambda x: x.__setitem__(a, -1)),
+        "column index out of range ": changed("exp_colidx", lambda x: x.__setitem__(a, p.n)),
+        "not sorted": changed("exp_colidx", lambda x: x.__setitem__(slice(a, a + 2), x[a:a + 2][::-1].copy())),
+        "not sorted ": changed("exp_colidx", lambda x: x.__setitem__(a + 1, x[a])),
+        "non-finite values": changed("exp_val", lambda x: x.__setitem__((5, 11), np.nan)),
+        "non-finite values ": changed("imp_blk", lambda x: x.__setitem__((11, 2), np.inf)),
+    }
+    cs = np.asarray(base["col_start"])
+    k = int(np.argmax(cs > 64))                               # merge columns 0..k-1 into one deeper than 64
+    cases["layers (1..%d allowed)" % 64] = dict(base, col_start=np.concatenate([[0], cs[k:]]).astype(np.int32),
+                                                lat=np.asarray(base["lat"])[k - 1:])
+    for rule, kw in cases.items():
+        with pytest.raises(m3d.Metos3dError) as ei:
+            m3d.Context(**kw, stream=fake_stream)
+        assert ei.value.status == m3d.M3D_ERR_ARG, rule
+        assert rule.strip() in str(ei.value), (rule, str(ei.value))
