@@ -1415,7 +1415,7 @@ m3d_status metos3d_ensemble_steps(m3d_ensemble *e, int j0, int nsteps, const dou
     if (!Y0 || !Y1 || nsteps < 0 || j0 < 0) return efail(e, M3D_ERR_ARG, "steps: null state or negative count");
     m3d_status st = pack(e, Y0, e->xbuf[0]);
     for (int s = 0; s < nsteps && st == M3D_OK; s++)
-        st = launch_step(e, (j0 + s) % e->nstep, e->xbuf[s & 1], e->xbuf[(s + 1) & 1]);
+        st = launch_step(e, (int)(((long long)j0 + s) % e->nstep), e->xbuf[s & 1], e->xbuf[(s + 1) & 1]);
     if (st == M3D_OK) st = unpack(e, e->xbuf[nsteps & 1], Y1);
     e->last_launches = nsteps + 2;
     return st;
